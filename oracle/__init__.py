@@ -1,0 +1,220 @@
+"""FP64 CPU oracle of dense membrane-probability inference (Sec. 2.1, Sec. 2.2).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py``; never by the library. It shares no code with the CUDA path; the
+only shared module is ``synth`` (seeded inputs).
+
+``liboracle.so`` is compiled on first use from ``oracle.c`` (gcc, OpenMP over output channels,
+no FMA contraction). Every function here marshals numpy arrays into that library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CONV, MAXF, HEAD = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-o", tmp, src, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            i64, p, d = ctypes.c_int64, ctypes.c_void_p, ctypes.c_double
+            ci = ctypes.c_int
+            sig = {
+                "oracle_reflect101": ([i64, i64], i64),
+                "oracle_conv": ([p, i64, i64, i64, p, p, i64, i64, ci, p], ci),
+                "oracle_maxfilter2": ([p, i64, i64, i64, p], ci),
+                "oracle_head_sigmoid": ([p, i64, i64, i64, p, d, p], ci),
+                "oracle_net_radius": ([p, ci], i64),
+                "oracle_param_count": ([p, ci], i64),
+                "oracle_pad_region": ([p, i64, i64, i64, i64, i64, i64, i64, i64, p], ci),
+                "oracle_run_layers": ([p, ci, p, p, i64, i64, p], ci),
+                "oracle_forward_region": ([p, ci, p, p, i64, i64, i64, i64, i64, i64, i64, p], ci),
+                "oracle_patch_pixel": ([p, ci, p, p, i64, i64, i64, i64, i64, p], ci),
+                "oracle_maxfilter_amax": ([p, ci, p, p, i64, i64, i64, i64, i64, i64, i64, p, i64], ci),
+                "oracle_student_loss_grad": ([p, ci, p, p, i64, i64, i64, i64, i64, p, p, p], ci),
+                "oracle_adam_step": ([p, p, p, p, i64, i64, d, d, d, d], ci),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _chk(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle: {what} failed with code {rc}")
+
+
+def _desc(layers) -> np.ndarray:
+    return np.ascontiguousarray(np.array(layers, dtype=np.int32).reshape(-1, 5))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _u8(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint8))
+
+
+def reflect101(t: int, n: int) -> int:
+    return int(_load().oracle_reflect101(t, n))
+
+
+def conv(x, W, b, relu: bool) -> np.ndarray:
+    """Valid cross-correlation of x [cin][h][w] with W [cout][cin][k][k] plus b, optional ReLU."""
+    x, W, b = _f64(x), _f64(W), _f64(b)
+    cin, h, w = x.shape
+    cout, cin2, k, k2 = W.shape
+    assert cin2 == cin and k == k2 and b.shape == (cout,)
+    y = np.empty((cout, h - k + 1, w - k + 1), dtype=np.float64)
+    _chk(_load().oracle_conv(x.ctypes.data, cin, h, w, W.ctypes.data, b.ctypes.data, cout, k, int(relu),
+                             y.ctypes.data), "conv")
+    return y
+
+
+def maxfilter2(x) -> np.ndarray:
+    x = _f64(x)
+    c, h, w = x.shape
+    y = np.empty((c, h - 1, w - 1), dtype=np.float64)
+    _chk(_load().oracle_maxfilter2(x.ctypes.data, c, h, w, y.ctypes.data), "maxfilter2")
+    return y
+
+
+def head_sigmoid(x, wv, b: float) -> np.ndarray:
+    x, wv = _f64(x), _f64(wv)
+    c, h, w = x.shape
+    p = np.empty((h, w), dtype=np.float64)
+    _chk(_load().oracle_head_sigmoid(x.ctypes.data, c, h, w, wv.ctypes.data, float(b), p.ctypes.data),
+         "head_sigmoid")
+    return p
+
+
+def net_radius(layers) -> int:
+    d = _desc(layers)
+    return int(_load().oracle_net_radius(d.ctypes.data, len(d)))
+
+
+def param_count(layers) -> int:
+    d = _desc(layers)
+    return int(_load().oracle_param_count(d.ctypes.data, len(d)))
+
+
+def pad_region(slice_u8, y0, x0, h, w, R) -> np.ndarray:
+    s = _u8(slice_u8)
+    H, W = s.shape
+    out = np.empty((h + 2 * R, w + 2 * R), dtype=np.float64)
+    _chk(_load().oracle_pad_region(s.ctypes.data, H, W, W, y0, x0, h, w, R, out.ctypes.data), "pad_region")
+    return out
+
+
+def run_layers(layers, params, xp) -> np.ndarray:
+    d, prm, xp = _desc(layers), _f64(params), _f64(xp)
+    s = 0
+    for kind, k, *_ in d:
+        s += int(k) - 1
+    ph, pw = xp.shape
+    p = np.empty((ph - s, pw - s), dtype=np.float64)
+    _chk(_load().oracle_run_layers(d.ctypes.data, len(d), prm.ctypes.data, xp.ctypes.data, ph, pw,
+                                   p.ctypes.data), "run_layers")
+    return p
+
+
+def forward_region(layers, params, slice_u8, y0=0, x0=0, h=None, w=None) -> np.ndarray:
+    """Dense probabilities of the region [y0, y0+h) x [x0, x0+w) of one slice (FP64)."""
+    d, prm, s = _desc(layers), _f64(params), _u8(slice_u8)
+    H, W = s.shape
+    h = H - y0 if h is None else h
+    w = W - x0 if w is None else w
+    p = np.empty((h, w), dtype=np.float64)
+    _chk(_load().oracle_forward_region(d.ctypes.data, len(d), prm.ctypes.data, s.ctypes.data, H, W, W,
+                                       y0, x0, h, w, p.ctypes.data), "forward_region")
+    return p
+
+
+def forward_volume(layers, params, vol_u8) -> np.ndarray:
+    return np.stack([forward_region(layers, params, s) for s in vol_u8])
+
+
+def patch_pixel(layers, params, slice_u8, i, j) -> float:
+    d, prm, s = _desc(layers), _f64(params), _u8(slice_u8)
+    H, W = s.shape
+    out = np.empty(1, dtype=np.float64)
+    _chk(_load().oracle_patch_pixel(d.ctypes.data, len(d), prm.ctypes.data, s.ctypes.data, H, W, W, i, j,
+                                    out.ctypes.data), "patch_pixel")
+    return float(out[0])
+
+
+def maxfilter_amax(layers, params, slice_u8, y0=0, x0=0, h=None, w=None, n_maxf=2, channels=32):
+    d, prm, s = _desc(layers), _f64(params), _u8(slice_u8)
+    H, W = s.shape
+    h = H - y0 if h is None else h
+    w = W - x0 if w is None else w
+    out = np.zeros(n_maxf * channels, dtype=np.float64)
+    _chk(_load().oracle_maxfilter_amax(d.ctypes.data, len(d), prm.ctypes.data, s.ctypes.data, H, W, W,
+                                       y0, x0, h, w, out.ctypes.data, out.size), "maxfilter_amax")
+    return out.reshape(n_maxf, channels)
+
+
+def student_loss_grad(layers, params, slices_u8, targets):
+    """Mean-squared-error loss of the student on n slices against target maps, and its gradient."""
+    d, prm = _desc(layers), _f64(params)
+    s = _u8(slices_u8)
+    t = _f64(targets)
+    n, H, W = s.shape
+    assert t.shape == (n, H, W)
+    grad = np.empty(prm.size, dtype=np.float64)
+    loss = np.empty(1, dtype=np.float64)
+    _chk(_load().oracle_student_loss_grad(d.ctypes.data, len(d), prm.ctypes.data, s.ctypes.data, n, H, W,
+                                          W, H * W, t.ctypes.data, loss.ctypes.data, grad.ctypes.data),
+         "student_loss_grad")
+    return float(loss[0]), grad
+
+
+def adam_step(w, m, v, g, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on FP64 arrays; returns (w, m, v)."""
+    w, m, v, g = _f64(w).copy(), _f64(m).copy(), _f64(v).copy(), _f64(g)
+    _chk(_load().oracle_adam_step(w.ctypes.data, m.ctypes.data, v.ctypes.data, g.ctypes.data, w.size, step,
+                                  lr, b1, b2, eps), "adam_step")
+    return w, m, v
+
+
+def metrics(p_gpu, p_ref) -> dict:
+    """max-abs, mean-abs (FP64 sum), binarised agreement at 0.5 (p >= 0.5 is membrane), and the
+    near-threshold mass: fraction of reference pixels with |p - 0.5| < max-abs."""
+    a = np.asarray(p_gpu, dtype=np.float64)
+    r = np.asarray(p_ref, dtype=np.float64)
+    diff = np.abs(a - r)
+    mx = float(diff.max()) if diff.size else 0.0
+    return {
+        "max_abs": mx,
+        "mean_abs": float(diff.sum() / max(diff.size, 1)),
+        "agreement": float(((a >= 0.5) == (r >= 0.5)).mean()) if diff.size else 1.0,
+        "near_threshold": float((np.abs(r - 0.5) < mx).mean()) if diff.size else 0.0,
+        "n": int(diff.size),
+    }

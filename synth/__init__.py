@@ -1,0 +1,161 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests and bench and by the oracle tests.
+
+Holds no arithmetic of the method: EM-like uint8 slices (stand-ins for the EM stacks of
+Sec. 2 / Sec. 2.2), He-normal parameters, seeded integer draws, and the two workload network
+descriptions as plain data (each side turns them into its own form).
+
+The C library ``libsynth.so`` is compiled on first use (gcc, OpenMP, no FMA contraction).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsynth.so")
+_lock = threading.Lock()
+_lib = None
+
+# Layer kinds of the workload descriptions (same numbering as the library's mb_layer_kind).
+CONV, MAXFILTER, HEAD_SIGMOID = 0, 1, 2
+
+# (kind, ksize, cin, cout, relu)
+# The measured stand-in network: conv5x5 1->32 ReLU, 2x2 stride-1 max-filter, conv5x5 32->32
+# ReLU, max-filter, conv5x5 32->32 ReLU, conv1x1 32->1 sigmoid (receptive field 15x15).
+TEACHER = (
+    (CONV, 5, 1, 32, 1),
+    (MAXFILTER, 2, 32, 32, 0),
+    (CONV, 5, 32, 32, 1),
+    (MAXFILTER, 2, 32, 32, 0),
+    (CONV, 5, 32, 32, 1),
+    (HEAD_SIGMOID, 1, 32, 1, 0),
+)
+# The distilled student: conv3x3 1->16 ReLU, conv3x3 16->16 ReLU, conv1x1 16->1 sigmoid.
+STUDENT = (
+    (CONV, 3, 1, 16, 1),
+    (CONV, 3, 16, 16, 1),
+    (HEAD_SIGMOID, 1, 16, 1, 0),
+)
+
+TEACHER_WEIGHT_SEED = 20161206
+STUDENT_WEIGHT_SEED = 20161207
+BASE_SEED = 1612021200  # + workload index
+
+
+def build(force: bool = False) -> str:
+    """Compile libsynth.so next to this file; returns its path."""
+    src = os.path.join(_HERE, "synth.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-o", tmp, src, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            u64, i64, p = ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p
+            lib.synth_default_cells.argtypes = [i64, i64]
+            lib.synth_default_cells.restype = i64
+            lib.synth_slice_seed.argtypes = [u64, u64, u64]
+            lib.synth_slice_seed.restype = u64
+            lib.synth_em_slice.argtypes = [u64, i64, i64, i64, p, i64]
+            lib.synth_em_volume.argtypes = [u64, u64, i64, i64, i64, i64, p, i64, i64]
+            lib.synth_he_normal.argtypes = [u64, i64, i64, p, i64, p, ctypes.c_double]
+            lib.synth_uniform_ints.argtypes = [u64, i64, i64, i64, p]
+            lib.synth_uniform_floats.argtypes = [u64, i64, ctypes.c_double, ctypes.c_double, p]
+            for f in ("synth_em_slice", "synth_em_volume", "synth_he_normal", "synth_uniform_ints",
+                      "synth_uniform_floats"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with code {rc}")
+
+
+def default_cells(h: int, w: int) -> int:
+    return int(_load().synth_default_cells(h, w))
+
+
+def slice_seed(base: int, block: int, z: int) -> int:
+    return int(_load().synth_slice_seed(base, block, z))
+
+
+def em_slice(seed: int, h: int, w: int, n_cells: int = 0) -> np.ndarray:
+    out = np.empty((h, w), dtype=np.uint8)
+    _check(_load().synth_em_slice(seed, h, w, n_cells, out.ctypes.data, w), "synth_em_slice")
+    return out
+
+
+def em_volume(base: int, z: int, h: int, w: int, block: int = 0, n_cells: int = 0,
+              out: np.ndarray | None = None) -> np.ndarray:
+    """z independent slices [z][h][w]; `out` may be a preallocated (pinned) uint8 array."""
+    if out is None:
+        out = np.empty((z, h, w), dtype=np.uint8)
+    assert out.dtype == np.uint8 and out.shape == (z, h, w) and out.flags.c_contiguous
+    _check(_load().synth_em_volume(base, block, z, h, w, n_cells, out.ctypes.data, w, h * w),
+           "synth_em_volume")
+    return out
+
+
+def he_normal(seed: int, fan_in: int, n_w: int, n_b: int, bias_std: float):
+    w = np.empty(n_w, dtype=np.float32)
+    b = np.empty(n_b, dtype=np.float32)
+    _check(_load().synth_he_normal(seed, fan_in, n_w, w.ctypes.data, n_b, b.ctypes.data, bias_std),
+           "synth_he_normal")
+    return w, b
+
+
+def uniform_ints(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.int64)
+    _check(_load().synth_uniform_ints(seed, n, lo, hi, out.ctypes.data), "synth_uniform_ints")
+    return out
+
+
+def uniform_floats(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    out = np.empty(n, dtype=np.float32)
+    _check(_load().synth_uniform_floats(seed, n, lo, hi, out.ctypes.data), "synth_uniform_floats")
+    return out
+
+
+def param_count(layers) -> int:
+    n = 0
+    for kind, k, cin, cout, _ in layers:
+        if kind in (CONV, HEAD_SIGMOID):
+            n += cout * cin * k * k + cout
+    return n
+
+
+def init_params(layers, seed: int, bias_std: float = 0.01) -> np.ndarray:
+    """He-normal FP32 parameters for `layers`, packed per parameterised layer as W[cout][cin][k][k]
+    then b[cout]; parameterised layer number l draws from seed + l. bias_std 0 gives zero biases."""
+    parts = []
+    l = 0
+    for kind, k, cin, cout, _ in layers:
+        if kind in (CONV, HEAD_SIGMOID):
+            w, b = he_normal(seed + l, cin * k * k, cout * cin * k * k, cout, bias_std)
+            parts += [w, b]
+            l += 1
+    return np.concatenate(parts).astype(np.float32)
+
+
+def block_shapes(seed: int, n_blocks: int, side_lo: int = 256, side_hi: int = 1536,
+                 depth_lo: int = 1, depth_hi: int = 16):
+    """Uneven block shapes (D, H, W): H and W independent integers in [side_lo, side_hi],
+    D in [depth_lo, depth_hi]."""
+    hs = uniform_ints(seed, n_blocks, side_lo, side_hi)
+    ws = uniform_ints(seed + 1, n_blocks, side_lo, side_hi)
+    ds = uniform_ints(seed + 2, n_blocks, depth_lo, depth_hi)
+    return [(int(d), int(h), int(w)) for d, h, w in zip(ds, hs, ws)]
