@@ -1,0 +1,214 @@
+/*
+ * membrane.h - C ABI of libmembrane: dense per-pixel membrane-probability inference by a
+ * shallow CNN over uint8 EM image stacks, on one GB300 (sm_103a).
+ *
+ * The operation (Sec. 2.1 "Membrane classification"; Sec. 2.2 "A lightweight network
+ * architecture" and "Accelerating dense computation"): every pixel of every slice gets the
+ * probability that it lies on a neuronal membrane, computed densely (all pixels in one pass,
+ * max-pooling replaced by stride-1 max-filtering) by a stack of valid cross-correlations with
+ * bias and ReLU, 2x2 stride-1 max-filters, and a 1x1 head with a sigmoid (for two classes the
+ * softmax of Sec. 2.2 equals the sigmoid of the logit difference). Each slice is mirror-padded
+ * (reflect-101: index -t for t < 0 and 2(n-1)-t for t > n-1) by the network's radius so the map
+ * has the slice's size; the input pixel value is u/255. Slices and blocks are independent
+ * (Sec. 2 "Block merging": the stack is split into blocks processed independently).
+ *
+ * Conventions of every call:
+ *  - Every call returns an mb_status; no C++ exception crosses this boundary. On failure,
+ *    mb_last_error() returns a thread-local message with the detail.
+ *  - The caller owns all input and output buffers. The library owns its weights, plans and
+ *    workspaces (released by mb_net_destroy).
+ *  - Pointers are device pointers unless a call says otherwise. Calls on device pointers are
+ *    asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream). Calls given
+ *    host pointers are synchronous on return.
+ *  - Sizes are element counts; pitches are in elements of the buffer's type.
+ *  - Slices need h >= 8 and w >= 8 so reflect-101 padding by 7 is defined; else MB_ERR_SHAPE.
+ *  - A net/precision combination without a kernel returns MB_ERR_UNSUPPORTED.
+ *  - Host-side fault injection for tests: environment MB_FAULT_OOM=1 makes every library
+ *    allocation fail with MB_ERR_OOM.
+ */
+#ifndef MEMBRANE_H
+#define MEMBRANE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mb_net mb_net; /* opaque, library-owned */
+
+typedef enum {
+    MB_OK = 0,
+    MB_ERR_INVALID_ARG = 1, /* null pointer, bad enum, inconsistent sizes */
+    MB_ERR_SHAPE = 2,       /* h or w below 8, or a size beyond a stated maximum */
+    MB_ERR_OOM = 3,         /* device or pinned-host allocation failed */
+    MB_ERR_CUDA = 4,        /* a CUDA runtime/driver call failed (detail in mb_last_error) */
+    MB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    MB_ERR_NOT_READY = 6,   /* weights not loaded, or FP8 net not calibrated */
+    MB_ERR_UNSUPPORTED = 7  /* no kernel for this net / precision / option */
+} mb_status;
+
+typedef enum { MB_PREC_FP32 = 0, MB_PREC_BF16 = 1, MB_PREC_FP8 = 2 } mb_precision;
+typedef enum { MB_OUT_F32 = 0, MB_OUT_U8 = 1 } mb_out_type;
+typedef enum { MB_CONV = 0, MB_MAXFILTER = 1, MB_HEAD_SIGMOID = 2 } mb_layer_kind;
+
+/*
+ * One layer of a network description (Sec. 2.2 describes the network in prose as alternating
+ * convolution / max-filter layers).
+ *   MB_CONV:         ksize x ksize valid cross-correlation cin -> cout, + bias, ReLU if relu.
+ *   MB_MAXFILTER:    ksize x ksize stride-1 max over each channel (cin == cout).
+ *   MB_HEAD_SIGMOID: 1x1 cin -> 1, + bias, sigmoid; must be the last layer.
+ * dilation must be 1 and maxout_groups 1 (0 is read as 1) in this version.
+ * Supported networks: the teacher (conv5x5 1->32 ReLU, maxfilter 2, conv5x5 32->32 ReLU,
+ * maxfilter 2, conv5x5 32->32 ReLU, head 32->1) in FP32, BF16 and FP8, and the student
+ * (conv3x3 1->16 ReLU, conv3x3 16->16 ReLU, head 16->1) in FP32 and BF16.
+ */
+typedef struct {
+    int32_t kind, ksize, dilation, cin, cout, relu, maxout_groups;
+} mb_layer_desc;
+
+/* One block of a batch: z slices of h x w. in[zi*in_slice_pitch + y*in_pitch + x] (uint8),
+ * out likewise with out_pitch / out_slice_pitch in elements of the output type. Device memory. */
+typedef struct {
+    const uint8_t* in;
+    int64_t z, h, w, in_pitch, in_slice_pitch;
+    void* out;
+    int64_t out_pitch, out_slice_pitch;
+} mb_block;
+
+/* Student training settings (Adam: Kingma and Ba, 2014). */
+typedef struct {
+    int32_t batch;      /* slices per step, sampled with replacement */
+    int32_t steps;      /* total optimiser steps of the run */
+    int32_t ckpt_every; /* write a checkpoint every this many steps (0: never) */
+    int32_t resume;     /* 1: continue from ckpt_path if it exists */
+    float lr, beta1, beta2, eps;
+    uint64_t seed; /* batch sampling */
+} mb_train_cfg;
+
+/* Create a net for `device` (a CUDA ordinal) from n_layers descriptions. Weights start
+ * unloaded. Errors: MB_ERR_INVALID_ARG (null out_net, bad enum), MB_ERR_UNSUPPORTED (layer
+ * stack or precision without a kernel), MB_ERR_CUDA, MB_ERR_OOM. */
+mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precision prec, int32_t device,
+                        mb_net** out_net);
+
+/* Release everything the net owns. NULL is a no-op. Synchronises the net's device. */
+mb_status mb_net_destroy(mb_net* net);
+
+/* Number of FP32 parameters of the net (layout of mb_load_weights). */
+mb_status mb_net_param_count(const mb_net* net, int64_t* n_params);
+
+/* Copy FP32 parameters from HOST memory (caller keeps ownership). Layout: for each
+ * parameterised layer in order, W[cout][cin][k][k] then b[cout]. BF16/FP8 nets round their
+ * own copies from these. An FP8 net needs mb_calibrate_fp8 afterwards. Synchronous.
+ * Errors: MB_ERR_INVALID_ARG when n_params differs from mb_net_param_count. */
+mb_status mb_load_weights(mb_net* net, const float* params, int64_t n_params);
+
+/* Copy the net's FP32 parameters (the master copy; after training, the trained ones) to HOST
+ * memory. Synchronous. */
+mb_status mb_get_weights(const mb_net* net, float* params, int64_t n_params);
+
+/*
+ * FP8 E4M3 calibration of a teacher net created with MB_PREC_FP8 (no counterpart in the
+ * paper, which states no number format): runs the FP32 path on n calibration slices (device,
+ * contiguous n x h x w uint8), takes the per-channel maximum of the activations entering the
+ * 2nd and 3rd convolutions, folds those activation scales into the next layer's weights, then
+ * quantises every output channel of those weights with its own scale (amax / 448) to E4M3
+ * (round to nearest even, saturating). Synchronises `stream` before returning.
+ * amax_out (HOST, may be NULL) receives the 2 x 32 activation maxima.
+ */
+mb_status mb_calibrate_fp8(mb_net* net, const uint8_t* slices, int64_t n, int64_t h, int64_t w,
+                           float* amax_out, void* stream);
+
+/*
+ * Probability maps of a contiguous volume in[z][h][w] (uint8) into out[z][h][w] (float32 or
+ * uint8 q = min(255, floor(255 p + 0.5))). Device pointers: asynchronous on `stream`.
+ * Pinned or pageable HOST pointers (both in and out on the host): the volume is streamed
+ * through the device in z-slabs with copies overlapped with compute; synchronous.
+ * Mixed host/device pointers: MB_ERR_INVALID_ARG.
+ */
+mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,
+                          mb_out_type out_type, void* stream);
+
+/*
+ * Output rows [y0, y0 + rows) and columns [x0, x0 + cols) of every slice of the volume
+ * in[z][h][w] into out[z][rows][cols], computed with the slice's true context (mirror padding
+ * only at the slice borders). Values equal the corresponding pixels of mb_infer_volume.
+ * Device pointers only.
+ */
+mb_status mb_infer_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,
+                          int64_t x0, int64_t rows, int64_t cols, void* out, mb_out_type out_type,
+                          void* stream);
+
+/*
+ * A batch of independent blocks of uneven size (Sec. 2: blocks are segmented independently).
+ * BF16/FP8 teacher nets: one persistent launch drains a device work queue of (block, slice,
+ * strip) items; the first call for a new batch geometry captures the launch in a CUDA graph
+ * that later calls with the same geometry replay. Other nets: one launch per block.
+ * Device pointers; asynchronous. Output of each block equals mb_infer_volume of that block.
+ */
+mb_status mb_infer_batch(mb_net* net, const mb_block* blocks, int32_t n_blocks, mb_out_type out_type,
+                         void* stream);
+
+/* The comparison path of mb_infer_batch: one mb_infer_volume-style launch per block. */
+mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t n_blocks,
+                                   mb_out_type out_type, void* stream);
+
+/*
+ * Autotuner of the persistent tensor-core kernel: times each candidate (strip rows per work
+ * item, accumulator stages) on a synthetic h x w x z workload on `stream`, keeps the fastest
+ * in the net, and records it in the JSON cache at cache_path (HOST string, may be NULL) keyed
+ * on GPU name, precision and shape. A cached entry is reused without timing. choice_out
+ * (HOST, may be NULL) receives {rows_per_item, stages, from_cache}. Synchronous.
+ */
+mb_status mb_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path,
+                      int32_t* choice_out, void* stream);
+
+/*
+ * Student loss and gradient on n slices (device, in[n][h][w] uint8; target[n][h][w] float32):
+ * loss = mean over all n*h*w pixels of (p - t)^2 (written to HOST *loss), gradient (device,
+ * float32, parameter layout) of that mean. Student nets only. Synchronous.
+ */
+mb_status mb_student_loss_grad(mb_net* student, const uint8_t* in, const float* target, int64_t n,
+                               int64_t h, int64_t w, double* loss, float* grad, void* stream);
+
+/*
+ * Train a student net in place on n slices (device in[n][h][w], target[n][h][w] float32 teacher
+ * maps): cfg->steps Adam steps on batches of cfg->batch slices sampled with replacement
+ * (seeded); FP32 master weights, m and v; the forward copy is rounded to BF16 for BF16 nets.
+ * loss_curve (HOST, may be NULL) receives one loss per step run. With ckpt_path (HOST string,
+ * may be NULL), a checkpoint {step, master weights, m, v, sampler state} is written every
+ * cfg->ckpt_every steps; with cfg->resume the run continues from it, bitwise as if never
+ * interrupted. Synchronous.
+ */
+mb_status mb_student_train(mb_net* student, const uint8_t* in, const float* target, int64_t n, int64_t h,
+                           int64_t w, const mb_train_cfg* cfg, const char* ckpt_path, float* loss_curve,
+                           void* stream);
+
+/*
+ * Multi-pass inference (Sec. 1: a fast pass everywhere, a slower pass only where errors are
+ * likely): the student maps the volume in[z][h][w] into out (float32); each tile x tile square
+ * (aligned at multiples of tile, clipped at the edges) whose count of student outputs with
+ * lo <= p <= hi exceeds max_frac of its pixels is recomputed by the teacher with its true
+ * context and overwritten. *fallback_rate (HOST) receives flagged tiles / all tiles;
+ * tile_flags (device, may be NULL) receives one byte per tile in [z][ty][tx] order.
+ * Device pointers; synchronous (the flag count is read back).
+ */
+mb_status mb_infer_cascade(mb_net* student, mb_net* teacher, const uint8_t* in, int64_t z, int64_t h,
+                           int64_t w, float* out, int32_t tile, float lo, float hi, float max_frac,
+                           double* fallback_rate, uint8_t* tile_flags, void* stream);
+
+/* Static string for a status code. */
+const char* mb_status_string(mb_status s);
+
+/* Thread-local detail of the last failing call on this thread ("" if none). */
+const char* mb_last_error(void);
+
+/* Number of kernel launches this library has issued since load (for launch accounting). */
+int64_t mb_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MEMBRANE_H */

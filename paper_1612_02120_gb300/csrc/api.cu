@@ -1,0 +1,679 @@
+// api.cu - the extern "C" boundary of libmembrane: argument checks, net lifecycle, dispatch to
+// the FP32 CUDA-core path or the tensor-core path, and host-memory slab streaming.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace mb {
+
+static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+void clear_error() { g_err.clear(); }
+
+mb_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    const char* base = strrchr(file, '/');
+    set_error("%s:%d: %s: %s (%s)", base ? base + 1 : file, line, what, cudaGetErrorString(e),
+              cudaGetErrorName(e));
+    if (e == cudaErrorMemoryAllocation) return MB_ERR_OOM;
+    return MB_ERR_CUDA;
+}
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool fault_oom() {
+    const char* v = getenv("MB_FAULT_OOM");
+    return v && v[0] == '1';
+}
+
+mb_status dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (fault_oom()) {
+        set_error("allocation of %zu bytes failed (MB_FAULT_OOM injected)", bytes);
+        return MB_ERR_OOM;
+    }
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MB_ERR_OOM : MB_ERR_CUDA;
+    }
+    return MB_OK;
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+mb_status Workspace::ensure(size_t need) {
+    if (need <= bytes && ptr) return MB_OK;
+    if (ptr) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize", __FILE__, __LINE__);
+        dev_free(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    MB_TRY(dev_alloc(&ptr, need));
+    bytes = need;
+    return MB_OK;
+}
+
+void Workspace::release() {
+    dev_free(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+// Makes `dev` current for the scope of an API call and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static bool same_layer(const mb_layer_desc& a, int kind, int k, int cin, int cout, int relu) {
+    const int dil = a.dilation == 0 ? 1 : a.dilation;
+    const int mo = a.maxout_groups == 0 ? 1 : a.maxout_groups;
+    return a.kind == kind && a.ksize == k && a.cin == cin && a.cout == cout && (a.relu != 0) == (relu != 0) &&
+           dil == 1 && mo == 1;
+}
+
+static int detect_family(const mb_layer_desc* L, int n) {
+    if (n == 6 && same_layer(L[0], MB_CONV, 5, 1, 32, 1) && same_layer(L[1], MB_MAXFILTER, 2, 32, 32, 0) &&
+        same_layer(L[2], MB_CONV, 5, 32, 32, 1) && same_layer(L[3], MB_MAXFILTER, 2, 32, 32, 0) &&
+        same_layer(L[4], MB_CONV, 5, 32, 32, 1) && same_layer(L[5], MB_HEAD_SIGMOID, 1, 32, 1, 0))
+        return FAMILY_TEACHER;
+    if (n == 3 && same_layer(L[0], MB_CONV, 3, 1, 16, 1) && same_layer(L[1], MB_CONV, 3, 16, 16, 1) &&
+        same_layer(L[2], MB_HEAD_SIGMOID, 1, 16, 1, 0))
+        return FAMILY_STUDENT;
+    return 0;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static mb_status check_ready(const mb_net* net) {
+    if (!net) {
+        set_error("net is NULL");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (!net->loaded) {
+        set_error("weights not loaded (call mb_load_weights first)");
+        return MB_ERR_NOT_READY;
+    }
+    if (net->prec == MB_PREC_FP8 && !net->calibrated) {
+        set_error("FP8 net not calibrated (call mb_calibrate_fp8 first)");
+        return MB_ERR_NOT_READY;
+    }
+    return MB_OK;
+}
+
+static mb_status check_slice(int64_t z, int64_t h, int64_t w) {
+    if (z < 0) {
+        set_error("negative slice count %lld", (long long)z);
+        return MB_ERR_INVALID_ARG;
+    }
+    if (h < 8 || w < 8) {
+        set_error("slice %lldx%lld: h and w must be >= 8 for reflect-101 padding by 7", (long long)h,
+                  (long long)w);
+        return MB_ERR_SHAPE;
+    }
+    if (h > (1 << 20) || w > (1 << 20)) {
+        set_error("slice %lldx%lld exceeds 2^20 per side", (long long)h, (long long)w);
+        return MB_ERR_SHAPE;
+    }
+    return MB_OK;
+}
+
+mb_status teacher_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+                         int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
+                         int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st) {
+    if (z == 0 || rows == 0 || cols == 0) return MB_OK;
+    if (net->prec == MB_PREC_FP32)
+        return simt_teacher_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch,
+                                   out_slice, ot, st);
+    mb_block b;
+    b.in = in;
+    b.z = z;
+    b.h = h;
+    b.w = w;
+    b.in_pitch = in_pitch;
+    b.in_slice_pitch = in_slice;
+    b.out = out;
+    b.out_pitch = out_pitch;
+    b.out_slice_pitch = out_slice;
+    return tc_infer_blocks(net, &b, 1, &y0, &x0, &rows, &cols, ot, st, false);
+}
+
+static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,
+                            int64_t x0, int64_t rows, int64_t cols, void* out, mb_out_type ot, cudaStream_t st) {
+    if (net->family == FAMILY_TEACHER)
+        return teacher_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
+    if (z == 0) return MB_OK;
+    return simt_student_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
+}
+
+// Host-memory volumes: z-slabs through double-buffered device slabs, H2D / compute / D2H on three
+// streams so copies overlap compute.
+static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,
+                                   mb_out_type ot) {
+    const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
+    const size_t in_slice = (size_t)h * w, out_slice = (size_t)h * w * osz;
+    int64_t slab = std::max<int64_t>(1, (int64_t)((256ull << 20) / (in_slice + out_slice)));
+    slab = std::min<int64_t>(slab, z);
+    if (z == 0) return MB_OK;
+    const int NB = 2;
+    void* dbuf[NB] = {nullptr, nullptr};
+    cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_in[NB] = {}, ev_comp[NB] = {}, ev_out[NB] = {};
+    mb_status rc = MB_OK;
+    auto fail = [&](cudaError_t e, const char* what) {
+        rc = cuda_fail(e, what, __FILE__, __LINE__);
+    };
+    for (int b = 0; b < NB && rc == MB_OK; ++b) rc = dev_alloc(&dbuf[b], (in_slice + out_slice) * slab);
+    for (int i = 0; i < 3 && rc == MB_OK; ++i) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
+        if (e != cudaSuccess) fail(e, "cudaStreamCreate");
+    }
+    for (int b = 0; b < NB && rc == MB_OK; ++b) {
+        cudaError_t e = cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_comp[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out[b], cudaEventDisableTiming);
+        if (e != cudaSuccess) fail(e, "cudaEventCreate");
+    }
+    const int64_t nslab = (z + slab - 1) / slab;
+    for (int64_t k = 0; k < nslab && rc == MB_OK; ++k) {
+        const int b = (int)(k % NB);
+        const int64_t z0 = k * slab, nz = std::min<int64_t>(slab, z - z0);
+        uint8_t* din = static_cast<uint8_t*>(dbuf[b]);
+        uint8_t* dout = din + in_slice * slab;
+        cudaError_t e = cudaSuccess;
+        if (k >= NB) e = cudaStreamWaitEvent(s[0], ev_comp[b], 0);  // input buffer free
+        if (e == cudaSuccess) e = cudaMemcpyAsync(din, in + z0 * in_slice, in_slice * nz, cudaMemcpyHostToDevice, s[0]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[b], s[0]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s[1], ev_in[b], 0);
+        if (e == cudaSuccess && k >= NB) e = cudaStreamWaitEvent(s[1], ev_out[b], 0);  // output buffer free
+        if (e != cudaSuccess) {
+            fail(e, "slab H2D");
+            break;
+        }
+        rc = net_region(net, din, nz, h, w, 0, 0, h, w, dout, ot, s[1]);
+        if (rc != MB_OK) break;
+        e = cudaEventRecord(ev_comp[b], s[1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s[2], ev_comp[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + z0 * out_slice, dout, out_slice * nz,
+                                cudaMemcpyDeviceToHost, s[2]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], s[2]);
+        if (e != cudaSuccess) fail(e, "slab D2H");
+    }
+    for (int i = 0; i < 3; ++i)
+        if (s[i]) {
+            cudaError_t e = cudaStreamSynchronize(s[i]);
+            if (e != cudaSuccess && rc == MB_OK) fail(e, "cudaStreamSynchronize");
+        }
+    for (int b = 0; b < NB; ++b) {
+        if (ev_in[b]) cudaEventDestroy(ev_in[b]);
+        if (ev_comp[b]) cudaEventDestroy(ev_comp[b]);
+        if (ev_out[b]) cudaEventDestroy(ev_out[b]);
+        dev_free(dbuf[b]);
+    }
+    for (int i = 0; i < 3; ++i)
+        if (s[i]) cudaStreamDestroy(s[i]);
+    return rc;
+}
+
+static uint16_t f32_to_bf16_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan passthrough
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;  // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_round(float f) {
+    uint32_t u = (uint32_t)f32_to_bf16_bits(f) << 16;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+}  // namespace mb
+
+using namespace mb;
+
+#define API_BEGIN clear_error();
+#define API_GUARD(net)                                                  \
+    DeviceGuard guard_((net)->device);                                  \
+    if (guard_.err != cudaSuccess) return cuda_fail(guard_.err, "cudaSetDevice", __FILE__, __LINE__);
+
+extern "C" {
+
+const char* mb_status_string(mb_status s) {
+    switch (s) {
+        case MB_OK: return "MB_OK";
+        case MB_ERR_INVALID_ARG: return "MB_ERR_INVALID_ARG";
+        case MB_ERR_SHAPE: return "MB_ERR_SHAPE";
+        case MB_ERR_OOM: return "MB_ERR_OOM";
+        case MB_ERR_CUDA: return "MB_ERR_CUDA";
+        case MB_ERR_TIMEOUT: return "MB_ERR_TIMEOUT";
+        case MB_ERR_NOT_READY: return "MB_ERR_NOT_READY";
+        case MB_ERR_UNSUPPORTED: return "MB_ERR_UNSUPPORTED";
+    }
+    return "MB_ERR_UNKNOWN";
+}
+
+const char* mb_last_error(void) { return g_err.c_str(); }
+
+int64_t mb_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precision prec, int32_t device,
+                        mb_net** out_net) {
+    API_BEGIN
+    if (!out_net || !layers || n_layers <= 0) {
+        set_error("mb_net_create: null argument or n_layers <= 0");
+        return MB_ERR_INVALID_ARG;
+    }
+    *out_net = nullptr;
+    if (prec != MB_PREC_FP32 && prec != MB_PREC_BF16 && prec != MB_PREC_FP8) {
+        set_error("mb_net_create: unknown precision %d", (int)prec);
+        return MB_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n_layers; ++i) {
+        const mb_layer_desc& L = layers[i];
+        if (L.kind < MB_CONV || L.kind > MB_HEAD_SIGMOID || L.ksize <= 0 || L.cin <= 0 || L.cout <= 0 ||
+            L.dilation < 0 || L.maxout_groups < 0) {
+            set_error("mb_net_create: layer %d is malformed", i);
+            return MB_ERR_INVALID_ARG;
+        }
+    }
+    const int fam = detect_family(layers, n_layers);
+    if (!fam) {
+        set_error("mb_net_create: no kernel for this layer stack (teacher 5x5/32 or student 3x3/16 only)");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (fam == FAMILY_STUDENT && prec == MB_PREC_FP8) {
+        set_error("mb_net_create: the student runs in FP32 or BF16");
+        return MB_ERR_UNSUPPORTED;
+    }
+    int ndev = 0;
+    MB_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) {
+        set_error("mb_net_create: device %d out of range (%d devices)", device, ndev);
+        return MB_ERR_INVALID_ARG;
+    }
+    mb_net* net = new (std::nothrow) mb_net();
+    if (!net) {
+        set_error("mb_net_create: host allocation failed");
+        return MB_ERR_OOM;
+    }
+    net->device = device;
+    net->family = fam;
+    net->prec = prec;
+    net->layers.assign(layers, layers + n_layers);
+    int64_t np = 0;
+    for (const auto& L : net->layers)
+        if (L.kind != MB_MAXFILTER) np += (int64_t)L.cout * L.cin * L.ksize * L.ksize + L.cout;
+    net->n_params = np;
+    {
+        DeviceGuard g(device);
+        mb_status s = g.err == cudaSuccess ? MB_OK : cuda_fail(g.err, "cudaSetDevice", __FILE__, __LINE__);
+        if (s == MB_OK) s = dev_alloc((void**)&net->d_queue, 64 * sizeof(int));
+        if (s == MB_OK) {
+            cudaError_t e = cudaMemset(net->d_queue, 0, 64 * sizeof(int));
+            if (e != cudaSuccess) s = cuda_fail(e, "cudaMemset", __FILE__, __LINE__);
+        }
+        if (s != MB_OK) {
+            dev_free(net->d_queue);
+            delete net;
+            return s;
+        }
+    }
+    *out_net = net;
+    return MB_OK;
+}
+
+mb_status mb_net_destroy(mb_net* net) {
+    API_BEGIN
+    if (!net) return MB_OK;
+    {
+        DeviceGuard g(net->device);
+        cudaDeviceSynchronize();
+        tc_release(net);
+        dev_free(net->d_params);
+        dev_free(net->d_simt);
+        dev_free(net->d_queue);
+        net->ws.release();
+        net->ws2.release();
+    }
+    delete net;
+    return MB_OK;
+}
+
+mb_status mb_net_param_count(const mb_net* net, int64_t* n_params) {
+    API_BEGIN
+    if (!net || !n_params) {
+        set_error("mb_net_param_count: null argument");
+        return MB_ERR_INVALID_ARG;
+    }
+    *n_params = net->n_params;
+    return MB_OK;
+}
+
+mb_status mb_load_weights(mb_net* net, const float* params, int64_t n_params) {
+    API_BEGIN
+    if (!net || !params) {
+        set_error("mb_load_weights: null argument");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (n_params != net->n_params) {
+        set_error("mb_load_weights: got %lld parameters, the net has %lld", (long long)n_params,
+                  (long long)net->n_params);
+        return MB_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < n_params; ++i)
+        if (!(params[i] == params[i]) || params[i] > 3.0e38f || params[i] < -3.0e38f) {
+            set_error("mb_load_weights: parameter %lld is not finite", (long long)i);
+            return MB_ERR_INVALID_ARG;
+        }
+    API_GUARD(net)
+    net->host_params.assign(params, params + n_params);
+    std::vector<float> fwd(params, params + n_params);
+    if (net->family == FAMILY_STUDENT && net->prec == MB_PREC_BF16)
+        for (auto& v : fwd) v = bf16_round(v);
+    std::vector<float> packed;
+    simt_pack(net, fwd.data(), packed);
+    if (!net->d_params) MB_TRY(dev_alloc((void**)&net->d_params, sizeof(float) * n_params));
+    if (!net->d_simt) MB_TRY(dev_alloc((void**)&net->d_simt, sizeof(float) * packed.size()));
+    net->simt_floats = packed.size();
+    MB_CUDA(cudaMemcpy(net->d_params, params, sizeof(float) * n_params, cudaMemcpyHostToDevice));
+    MB_CUDA(cudaMemcpy(net->d_simt, packed.data(), sizeof(float) * packed.size(), cudaMemcpyHostToDevice));
+    net->calibrated = false;
+    net->loaded = true;
+    if (net->family == FAMILY_TEACHER && net->prec == MB_PREC_BF16) MB_TRY(tc_prepare(net));
+    return MB_OK;
+}
+
+mb_status mb_get_weights(const mb_net* net, float* params, int64_t n_params) {
+    API_BEGIN
+    if (!net || !params) {
+        set_error("mb_get_weights: null argument");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (n_params != net->n_params) {
+        set_error("mb_get_weights: got %lld parameters, the net has %lld", (long long)n_params,
+                  (long long)net->n_params);
+        return MB_ERR_INVALID_ARG;
+    }
+    if (!net->loaded) {
+        set_error("mb_get_weights: weights not loaded");
+        return MB_ERR_NOT_READY;
+    }
+    API_GUARD(net)
+    MB_CUDA(cudaMemcpy(params, net->d_params, sizeof(float) * n_params, cudaMemcpyDeviceToHost));
+    return MB_OK;
+}
+
+mb_status mb_calibrate_fp8(mb_net* net, const uint8_t* slices, int64_t n, int64_t h, int64_t w, float* amax_out,
+                           void* stream) {
+    API_BEGIN
+    if (!net || !slices || n <= 0) {
+        set_error("mb_calibrate_fp8: null argument or n <= 0");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (net->family != FAMILY_TEACHER || net->prec != MB_PREC_FP8) {
+        set_error("mb_calibrate_fp8: only FP8 teacher nets are calibrated");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (!net->loaded) {
+        set_error("mb_calibrate_fp8: weights not loaded");
+        return MB_ERR_NOT_READY;
+    }
+    MB_TRY(check_slice(n, h, w));
+    API_GUARD(net)
+    if (!is_device_ptr(slices)) {
+        set_error("mb_calibrate_fp8: slices must be device memory");
+        return MB_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    float* d_amax = nullptr;
+    MB_TRY(dev_alloc((void**)&d_amax, 64 * sizeof(float)));
+    mb_status s = simt_teacher_amax(net, slices, n, h, w, d_amax, st);
+    float host[64];
+    if (s == MB_OK) {
+        cudaError_t e = cudaMemcpyAsync(host, d_amax, sizeof(host), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "amax readback", __FILE__, __LINE__);
+    }
+    dev_free(d_amax);
+    if (s != MB_OK) return s;
+    for (int m = 0; m < 2; ++m)
+        for (int c = 0; c < 32; ++c) net->fp8_amax[m][c] = host[m * 32 + c];
+    if (amax_out) memcpy(amax_out, host, sizeof(host));
+    MB_TRY(tc_prepare(net));
+    net->calibrated = true;
+    return MB_OK;
+}
+
+mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,
+                          mb_out_type out_type, void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(net));
+    if ((!in || !out) && z > 0) {
+        set_error("mb_infer_volume: null buffer");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (out_type != MB_OUT_F32 && out_type != MB_OUT_U8) {
+        set_error("mb_infer_volume: unknown output type %d", (int)out_type);
+        return MB_ERR_INVALID_ARG;
+    }
+    MB_TRY(check_slice(z, h, w));
+    if (z == 0) return MB_OK;
+    API_GUARD(net)
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    if (din != dout) {
+        set_error("mb_infer_volume: in and out must both be device or both host memory");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (!din) return infer_host_volume(net, in, z, h, w, out, out_type);
+    return net_region(net, in, z, h, w, 0, 0, h, w, out, out_type, (cudaStream_t)stream);
+}
+
+mb_status mb_infer_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,
+                          int64_t x0, int64_t rows, int64_t cols, void* out, mb_out_type out_type, void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(net));
+    if ((!in || !out) && z > 0) {
+        set_error("mb_infer_region: null buffer");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (out_type != MB_OUT_F32 && out_type != MB_OUT_U8) {
+        set_error("mb_infer_region: unknown output type");
+        return MB_ERR_INVALID_ARG;
+    }
+    MB_TRY(check_slice(z, h, w));
+    if (y0 < 0 || x0 < 0 || rows < 0 || cols < 0 || y0 + rows > h || x0 + cols > w) {
+        set_error("mb_infer_region: region [%lld,+%lld) x [%lld,+%lld) outside the %lldx%lld slice",
+                  (long long)y0, (long long)rows, (long long)x0, (long long)cols, (long long)h, (long long)w);
+        return MB_ERR_SHAPE;
+    }
+    if (z == 0 || rows == 0 || cols == 0) return MB_OK;
+    API_GUARD(net)
+    if (!is_device_ptr(in) || !is_device_ptr(out)) {
+        set_error("mb_infer_region: device pointers only");
+        return MB_ERR_INVALID_ARG;
+    }
+    return net_region(net, in, z, h, w, y0, x0, rows, cols, out, out_type, (cudaStream_t)stream);
+}
+
+static mb_status check_blocks(const mb_net* net, const mb_block* blocks, int32_t n, mb_out_type ot) {
+    if (!blocks && n > 0) {
+        set_error("blocks is NULL");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (n < 0) {
+        set_error("n_blocks < 0");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (ot != MB_OUT_F32 && ot != MB_OUT_U8) {
+        set_error("unknown output type");
+        return MB_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i) {
+        const mb_block& b = blocks[i];
+        mb_status s = check_slice(b.z, b.h, b.w);
+        if (s != MB_OK) {
+            set_error("block %d: %s", i, mb_last_error());
+            return s;
+        }
+        if (b.z > 0 && (!b.in || !b.out)) {
+            set_error("block %d: null buffer", i);
+            return MB_ERR_INVALID_ARG;
+        }
+        if (b.in_pitch < b.w || b.in_slice_pitch < b.in_pitch * b.h || b.out_pitch < b.w ||
+            b.out_slice_pitch < b.out_pitch * b.h) {
+            set_error("block %d: pitches smaller than the block", i);
+            return MB_ERR_INVALID_ARG;
+        }
+    }
+    (void)net;
+    return MB_OK;
+}
+
+mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t n_blocks, mb_out_type out_type,
+                                   void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(net));
+    MB_TRY(check_blocks(net, blocks, n_blocks, out_type));
+    API_GUARD(net)
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n_blocks; ++i) {
+        const mb_block& b = blocks[i];
+        if (net->family == FAMILY_TEACHER) {
+            MB_TRY(teacher_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w, b.out,
+                                  b.out_pitch, b.out_slice_pitch, out_type, st));
+        } else if (b.z > 0) {
+            MB_TRY(simt_student_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w,
+                                       b.out, b.out_pitch, b.out_slice_pitch, out_type, st));
+        }
+    }
+    return MB_OK;
+}
+
+mb_status mb_infer_batch(mb_net* net, const mb_block* blocks, int32_t n_blocks, mb_out_type out_type,
+                         void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(net));
+    MB_TRY(check_blocks(net, blocks, n_blocks, out_type));
+    if (n_blocks == 0) return MB_OK;
+    if (net->family != FAMILY_TEACHER || net->prec == MB_PREC_FP32)
+        return mb_infer_batch_per_block(net, blocks, n_blocks, out_type, stream);
+    API_GUARD(net)
+    std::vector<int64_t> y0(n_blocks, 0), x0(n_blocks, 0), rows(n_blocks), cols(n_blocks);
+    for (int i = 0; i < n_blocks; ++i) {
+        rows[i] = blocks[i].h;
+        cols[i] = blocks[i].w;
+    }
+    return tc_infer_blocks(net, blocks, n_blocks, y0.data(), x0.data(), rows.data(), cols.data(), out_type,
+                           (cudaStream_t)stream, true);
+}
+
+mb_status mb_student_loss_grad(mb_net* student, const uint8_t* in, const float* target, int64_t n, int64_t h,
+                               int64_t w, double* loss, float* grad, void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(student));
+    if (student->family != FAMILY_STUDENT) {
+        set_error("mb_student_loss_grad: not a student net");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (!in || !target || !loss || !grad || n <= 0) {
+        set_error("mb_student_loss_grad: null argument or n <= 0");
+        return MB_ERR_INVALID_ARG;
+    }
+    MB_TRY(check_slice(n, h, w));
+    API_GUARD(student)
+    return student_loss_grad(student, in, target, n, h, w, loss, grad, (cudaStream_t)stream);
+}
+
+mb_status mb_student_train(mb_net* student, const uint8_t* in, const float* target, int64_t n, int64_t h,
+                           int64_t w, const mb_train_cfg* cfg, const char* ckpt_path, float* loss_curve,
+                           void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(student));
+    if (student->family != FAMILY_STUDENT) {
+        set_error("mb_student_train: not a student net");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (!in || !target || !cfg || n <= 0 || cfg->batch <= 0 || cfg->steps < 0 || cfg->ckpt_every < 0 ||
+        !(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) ||
+        !(cfg->eps > 0.f)) {
+        set_error("mb_student_train: bad arguments");
+        return MB_ERR_INVALID_ARG;
+    }
+    MB_TRY(check_slice(n, h, w));
+    API_GUARD(student)
+    return student_train(student, in, target, n, h, w, cfg, ckpt_path, loss_curve, (cudaStream_t)stream);
+}
+
+mb_status mb_infer_cascade(mb_net* student, mb_net* teacher, const uint8_t* in, int64_t z, int64_t h, int64_t w,
+                           float* out, int32_t tile, float lo, float hi, float max_frac, double* fallback_rate,
+                           uint8_t* tile_flags, void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(student));
+    MB_TRY(check_ready(teacher));
+    if (student->family != FAMILY_STUDENT || teacher->family != FAMILY_TEACHER) {
+        set_error("mb_infer_cascade: needs a student net and a teacher net");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (student->device != teacher->device) {
+        set_error("mb_infer_cascade: student and teacher on different devices");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (!in || !out || !fallback_rate || tile < 8 || !(lo <= hi) || !(max_frac >= 0.f)) {
+        set_error("mb_infer_cascade: bad arguments");
+        return MB_ERR_INVALID_ARG;
+    }
+    MB_TRY(check_slice(z, h, w));
+    API_GUARD(student)
+    return cascade(student, teacher, in, z, h, w, out, tile, lo, hi, max_frac, fallback_rate, tile_flags,
+                   (cudaStream_t)stream);
+}
+
+}  // extern "C"

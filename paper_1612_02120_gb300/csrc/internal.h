@@ -1,0 +1,128 @@
+// internal.h - host-side internals shared by the translation units of libmembrane.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/membrane.h"
+
+namespace mb {
+
+enum Family { FAMILY_TEACHER = 1, FAMILY_STUDENT = 2 };
+
+// Teacher geometry: conv5x5 x3 with two 2x2 max-filters -> receptive radius 7.
+constexpr int kTeacherRadius = 7;
+constexpr int kTeacherC = 32;
+// Student geometry: conv3x3 x2 -> radius 2.
+constexpr int kStudentRadius = 2;
+constexpr int kStudentC = 16;
+
+void set_error(const char* fmt, ...);
+void clear_error();
+mb_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+void count_launch(int n = 1);
+bool fault_oom();
+
+#define MB_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return ::mb::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define MB_TRY(call)                      \
+    do {                                  \
+        mb_status s_ = (call);            \
+        if (s_ != MB_OK) return s_;       \
+    } while (0)
+
+mb_status dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+
+// A growable device scratch buffer owned by a net.
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    mb_status ensure(size_t need);
+    void release();
+};
+
+// Tensor-core (tcgen05) teacher weights, packed for the UMMA operand layout.
+struct TcWeights {
+    void* packed = nullptr;     // L2 and L3 B operands (BF16 or E4M3), see tc_conv.cu
+    float* epi = nullptr;       // per-channel epilogue constants (bias, scales), FP32
+    size_t packed_bytes = 0;
+};
+
+struct GraphCacheEntry;
+
+}  // namespace mb
+
+struct mb_net {
+    int device = 0;
+    int family = 0;
+    mb_precision prec = MB_PREC_FP32;
+    std::vector<mb_layer_desc> layers;
+    int64_t n_params = 0;
+    std::vector<float> host_params;  // FP32 master copy on the host
+    bool loaded = false;
+    bool calibrated = false;
+    float* d_params = nullptr;   // FP32 parameters, API layout (student: the master copy)
+    float* d_simt = nullptr;     // SIMT layout: per conv layer Wt[ci][ky][kx][co], b[co]; head w, b
+    size_t simt_floats = 0;
+    mb::TcWeights tc;
+    float fp8_amax[2][32] = {};
+    mb::Workspace ws;            // layered FP32 path activations
+    mb::Workspace ws2;           // student training / cascade scratch
+    // persistent kernel tuning
+    int rows_per_item = 64;
+    int stages = 2;
+    bool tuned = false;
+    // batch graph cache
+    std::vector<mb::GraphCacheEntry*> graphs;
+    int* d_queue = nullptr;      // work-queue counter + error word (device)
+};
+
+namespace mb {
+
+// SIMT (FP32 arithmetic) layered path: conv kernels with activations in a workspace.
+mb_status simt_teacher_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
+                              int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
+                              int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
+                              mb_out_type ot, cudaStream_t st);
+mb_status simt_student_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
+                              int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
+                              int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
+                              mb_out_type ot, cudaStream_t st);
+// FP32 teacher activations after the two max-filters: per-channel amax over n slices (device out[64]).
+mb_status simt_teacher_amax(mb_net* net, const uint8_t* in, int64_t n, int64_t h, int64_t w, float* d_amax,
+                            cudaStream_t st);
+// Pack the SIMT weight layout from the FP32 API layout (host side).
+void simt_pack(const mb_net* net, const float* params, std::vector<float>& out);
+
+// Tensor-core fused path.
+mb_status tc_prepare(mb_net* net);   // pack BF16 / FP8 weights from host_params (+ calibration)
+void tc_release(mb_net* net);
+struct TcItem;                       // work item (device layout in tc_conv.cu)
+mb_status tc_infer_blocks(mb_net* net, const mb_block* blocks, int n_blocks, const int64_t* y0,
+                          const int64_t* x0, const int64_t* rows, const int64_t* cols, mb_out_type ot,
+                          cudaStream_t st, bool use_graph);
+
+// Student training and cascade.
+mb_status student_loss_grad(mb_net* s, const uint8_t* in, const float* tgt, int64_t n, int64_t h, int64_t w,
+                            double* loss, float* grad, cudaStream_t st);
+mb_status student_train(mb_net* s, const uint8_t* in, const float* tgt, int64_t n, int64_t h, int64_t w,
+                        const mb_train_cfg* cfg, const char* ckpt, float* curve, cudaStream_t st);
+mb_status cascade(mb_net* s, mb_net* t, const uint8_t* in, int64_t z, int64_t h, int64_t w, float* out,
+                  int tile, float lo, float hi, float max_frac, double* rate, uint8_t* flags,
+                  cudaStream_t st);
+
+// Teacher dispatch used by the API, the batch comparison path and the cascade.
+mb_status teacher_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+                         int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
+                         int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st);
+
+}  // namespace mb
