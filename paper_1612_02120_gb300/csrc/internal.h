@@ -50,13 +50,6 @@ struct Workspace {
     void release();
 };
 
-// Tensor-core (tcgen05) teacher weights, packed for the UMMA operand layout.
-struct TcWeights {
-    void* packed = nullptr;     // L2 and L3 B operands (BF16 or E4M3), see tc_conv.cu
-    float* epi = nullptr;       // per-channel epilogue constants (bias, scales), FP32
-    size_t packed_bytes = 0;
-};
-
 struct GraphCacheEntry;
 
 }  // namespace mb
@@ -73,7 +66,7 @@ struct mb_net {
     float* d_params = nullptr;   // FP32 parameters, API layout (student: the master copy)
     float* d_simt = nullptr;     // SIMT layout: per conv layer Wt[ci][ky][kx][co], b[co]; head w, b
     size_t simt_floats = 0;
-    mb::TcWeights tc;
+    void* tc_state = nullptr;    // tensor-core path state (packed operands, constants), tc_conv.cu
     float fp8_amax[2][32] = {};
     mb::Workspace ws;            // layered FP32 path activations
     mb::Workspace ws2;           // student training / cascade scratch
@@ -106,6 +99,7 @@ void simt_pack(const mb_net* net, const float* params, std::vector<float>& out);
 // Tensor-core fused path.
 mb_status tc_prepare(mb_net* net);   // pack BF16 / FP8 weights from host_params (+ calibration)
 void tc_release(mb_net* net);
+mb_status tc_poll_error(mb_net* net);  // MB_ERR_TIMEOUT if a launch recorded a timed-out wait
 struct TcItem;                       // work item (device layout in tc_conv.cu)
 mb_status tc_infer_blocks(mb_net* net, const mb_block* blocks, int n_blocks, const int64_t* y0,
                           const int64_t* x0, const int64_t* rows, const int64_t* cols, mb_out_type ot,

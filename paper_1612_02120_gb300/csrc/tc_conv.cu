@@ -1,14 +1,860 @@
-// tc_conv.cu - tensor-core (tcgen05) fused teacher path. (in progress)
+// tc_conv.cu - fused teacher inference on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// The whole network of Sec. 2.2 (dense computation with stride-1 max-filtering) runs in one
+// persistent kernel; intermediates never leave the SM:
+//   layer 1   conv5x5 1->32 + bias + ReLU    FP32 on CUDA cores (weights are kernel constants)
+//   maxfilter 2x2 stride 1                    fused into the layer-1 producer
+//   layer 2   conv5x5 32->32                  tcgen05.mma, BF16 or E4M3 operands, FP32 in TMEM
+//   + bias + ReLU + maxfilter                 fused into the layer-2 epilogue (TMEM -> regs)
+//   layer 3   conv5x5 32->32                  tcgen05.mma
+//   + bias + ReLU + head 1x1 + sigmoid        fused into the layer-3 epilogue, stored to HBM
+//
+// Work item: one slice, a strip of 118 output columns, a chunk of output rows. Each CTA walks
+// its items row by row. The layer-2/3 implicit GEMM per input row r:
+//   M = 128 pixels of the row, K = 32 channels (x 5 column taps dx), N = 5 row taps x 32 outputs.
+// The five row taps dy are stacked along N, so one input row is multiplied once and its five
+// 32-column result blocks accumulate into the TMEM accumulators of output rows r-4 .. r (a ring
+// of 8 row accumulators per layer); the column tap dx is a 16-byte shift of the A descriptor's
+// start address in the no-swizzle K-major layout [channel chunk][pixel][16 B].
+//
+// Warp roles (512 threads): warp 0 issues MMAs (one thread) and owns TMEM; warp 1 loads uint8
+// input rows (reflect-101 mirror padding, /255); warps 4-7 drain layer-2 accumulators; warps
+// 8-11 drain layer-3 accumulators; warps 12-15 compute layer 1. Hand-offs are mbarriers; every
+// wait is bounded by a 4 s global-timer limit after which the CTA records MB_ERR_TIMEOUT, stops
+// issuing work and leaves cleanly (TMEM is always freed).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace mb {
-mb_status tc_prepare(mb_net*) { return MB_OK; }
-void tc_release(mb_net*) {}
-mb_status tc_infer_blocks(mb_net*, const mb_block*, int, const int64_t*, const int64_t*, const int64_t*,
-                          const int64_t*, mb_out_type, cudaStream_t, bool) {
-    set_error("tensor-core path not built yet");
-    return MB_ERR_UNSUPPORTED;
+
+constexpr int kThreads = 512;
+constexpr int kPitch = 136;          // pixels per ring row (128 used + dx overrun)
+constexpr int kStrip = 118;          // valid output columns per 128-pixel strip
+constexpr int kInCols = 132;         // input columns read per row
+constexpr int kInRing = 8;           // input row ring
+constexpr int kRing = 4;             // mf1 / mf2 ring slots
+constexpr int kAccRing = 8;          // TMEM row accumulators per layer
+constexpr int kMaxBlocks = 64;       // blocks per launch (kernel-parameter table)
+constexpr int kGroupBytes = 5120;    // one B group: 2 chunks x 160 rows x 16 B
+constexpr uint64_t kWaitNs = 4000000000ull;
+
+struct TcBlockDesc {
+    const uint8_t* in;
+    void* out;
+    int64_t in_pitch, in_slice, out_pitch, out_slice;
+    int h, w;               // source slice size (mirror padding range)
+    int ry0, rx0, rh, rw;   // output region
+    int z, n_strips, n_chunks, item_start;
+};
+
+struct TcParams {
+    float w1[32][25];
+    float b1[32];
+    float ep2_scale[32], ep2_bias[32];
+    float ep3_scale[32], ep3_bias[32];
+    float q1[32], q2[32];   // activation quantisation multipliers (FP8), 1 for BF16
+    float hw[32];
+    float hb;
+    const uint8_t* wpack;   // packed B operands (global), layer 2 then layer 3
+    int* err;               // error word (MB_ERR_TIMEOUT on a timed-out wait)
+    int n_blocks, n_items, rows_per_item, lag, out_u8;
+    TcBlockDesc blk[kMaxBlocks];
+};
+
+template <bool FP8>
+struct Cfg {
+    static constexpr int kChunks = FP8 ? 2 : 4;                 // 16-byte channel chunks per pixel
+    static constexpr int kSlotBytes = kChunks * kPitch * 16;
+    static constexpr int kGroups = FP8 ? 5 : 10;                // MMAs per (layer, input row, run)
+    static constexpr int kLayerB = kGroups * kGroupBytes;
+    // shared memory map
+    static constexpr int oB = 0;
+    static constexpr int oR1 = oB + 2 * kLayerB;
+    static constexpr int oR2 = oR1 + kRing * kSlotBytes;
+    static constexpr int oIn = oR2 + kRing * kSlotBytes;
+    static constexpr int oSt1 = oIn + kInRing * kPitch * 4;
+    static constexpr int oSt2 = oSt1 + 2 * 4 * 32 * 4;
+    static constexpr int oBar = oSt2 + 2 * 4 * 32 * 4;
+    static constexpr int kBars = 2 * kInRing + 4 * kRing + 4 * kAccRing + 1;
+    static constexpr int oMisc = oBar + kBars * 8;
+    static constexpr int kSmem = oMisc + 16;
+};
+
+struct Bars {
+    uint64_t* in_full;
+    uint64_t* in_empty;
+    uint64_t* m1_full;
+    uint64_t* m1_empty;
+    uint64_t* m2_full;
+    uint64_t* m2_empty;
+    uint64_t* a2_full;
+    uint64_t* a2_free;
+    uint64_t* a3_full;
+    uint64_t* a3_free;
+    uint64_t* fin;
+};
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
+
+// Bounded wait. Returns false (and raises the CTA-wide abort flag) when the phase did not
+// complete within kWaitNs, or immediately once the CTA is aborting.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                           int* err) {
+    if (*abort_flag) return false;
+    if (ptx::mbar_test(bar, parity)) return true;
+    const uint64_t t0 = gtime();
+    uint32_t n = 0;
+    while (!ptx::mbar_test(bar, parity)) {
+        if ((++n & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (gtime() - t0 > kWaitNs) {
+                *abort_flag = 1;
+                *(volatile int*)err = MB_ERR_TIMEOUT;
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ int refl_clamp(int t, int n) {
+    t = t < 0 ? -t : t;
+    t = t >= n ? 2 * (n - 1) - t : t;
+    return t < 0 ? 0 : (t >= n ? n - 1 : t);
+}
+
+struct ItemInfo {
+    int b, zi, x0, y0, rows;
+};
+
+__device__ __forceinline__ ItemInfo decode_item(const TcParams& p, int k) {
+    int b = 0;
+    while (b + 1 < p.n_blocks && p.blk[b + 1].item_start <= k) ++b;
+    const TcBlockDesc& d = p.blk[b];
+    int r = k - d.item_start;
+    const int chunk = r % d.n_chunks;
+    r /= d.n_chunks;
+    const int strip = r % d.n_strips;
+    const int zi = r / d.n_strips;
+    ItemInfo it;
+    it.b = b;
+    it.zi = zi;
+    it.x0 = strip * kStrip;
+    it.y0 = chunk * p.rows_per_item;
+    it.rows = min(p.rows_per_item, d.rh - it.y0);
+    return it;
+}
+
+// Pack 8 consecutive channels (BF16) or 16 (E4M3) of one pixel into a 16-byte ring row.
+template <bool FP8>
+__device__ __forceinline__ void store_pixel(uint8_t* slot, int c, const float (&m)[32], const float* q) {
+    if (!FP8) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint4 u;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(m[8 * k + 0], m[8 * k + 1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(m[8 * k + 2], m[8 * k + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(m[8 * k + 4], m[8 * k + 5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(m[8 * k + 6], m[8 * k + 7]);
+            u.x = *reinterpret_cast<uint32_t*>(&h0);
+            u.y = *reinterpret_cast<uint32_t*>(&h1);
+            u.z = *reinterpret_cast<uint32_t*>(&h2);
+            u.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(slot + (k * kPitch + c) * 16) = u;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int ch = 16 * k + 4 * j;
+                __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+                    make_float2(m[ch] * q[ch], m[ch + 1] * q[ch + 1]), __NV_SATFINITE, __NV_E4M3);
+                __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                    make_float2(m[ch + 2] * q[ch + 2], m[ch + 3] * q[ch + 3]), __NV_SATFINITE, __NV_E4M3);
+                w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+            *reinterpret_cast<uint4*>(slot + (k * kPitch + c) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Issue the MMAs of one input row for one layer: output rows j = r-4+i of the layer for the
+// valid blocks i (0 <= j < n_out), split into runs of contiguous TMEM ring slots. Block 4 (row
+// j = r) is overwritten by the first group and accumulated by the others.
+template <bool FP8>
+__device__ __forceinline__ void issue_row(uint32_t tcol0, uint32_t acc_base_seq, int r, int n_out,
+                                          uint32_t a_slot_addr, uint32_t b_layer_addr) {
+    constexpr int G = Cfg<FP8>::kGroups;
+    const int ilo = max(0, 4 - r);
+    const int ihi = min(4, n_out - 1 - r + 4);
+    if (ilo > ihi) return;
+#pragma unroll 1
+    for (int g = 0; g < G; ++g) {
+        const int dx = FP8 ? g : (g >> 1);
+        const int hk = FP8 ? 0 : (g & 1);
+        const uint32_t a_addr = a_slot_addr + (uint32_t)(hk * 2 * kPitch * 16 + dx * 16);
+        const uint64_t adesc = ptx::smem_desc(a_addr, kPitch * 16, 128);
+        int i = ilo;
+        while (i <= ihi) {
+            const uint32_t slot0 = (acc_base_seq + (uint32_t)(r - 4 + i)) % kAccRing;
+            int i1 = i;
+            // extend the run while slots stay contiguous; block 4 of group 0 stands alone
+            while (i1 + 1 <= ihi && (slot0 + (uint32_t)(i1 + 1 - i)) < kAccRing && !(g == 0 && i1 + 1 == 4)) ++i1;
+            const int nb = i1 - i + 1;
+            const uint32_t d = tcol0 + 32u * slot0;
+            const uint64_t bdesc = ptx::smem_desc(b_layer_addr + (uint32_t)(g * kGroupBytes + i * 512), 160 * 16, 128);
+            const uint32_t acc = (g == 0 && i == 4) ? 0u : 1u;
+            if (FP8)
+                ptx::mma_e4m3(d, adesc, bdesc, ptx::idesc_f32acc(ptx::kFmtE4M3, 128, 32 * nb), acc);
+            else
+                ptx::mma_bf16(d, adesc, bdesc, ptx::idesc_f32acc(ptx::kFmtBF16, 128, 32 * nb), acc);
+            i = i1 + 1;
+        }
+    }
+}
+
+template <bool FP8>
+__global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_constant__ TcParams p) {
+    using C = Cfg<FP8>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* barmem = reinterpret_cast<uint64_t*>(smem + C::oBar);
+    Bars B;
+    B.in_full = barmem;
+    B.in_empty = B.in_full + kInRing;
+    B.m1_full = B.in_empty + kInRing;
+    B.m1_empty = B.m1_full + kRing;
+    B.m2_full = B.m1_empty + kRing;
+    B.m2_empty = B.m2_full + kRing;
+    B.a2_full = B.m2_empty + kRing;
+    B.a2_free = B.a2_full + kAccRing;
+    B.a3_full = B.a2_free + kAccRing;
+    B.a3_free = B.a3_full + kAccRing;
+    B.fin = B.a3_free + kAccRing;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::oMisc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::oMisc + 4);
+    float* in_ring = reinterpret_cast<float*>(smem + C::oIn);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    // ---- set-up: barriers, B operands, ring padding, TMEM ------------------------------------
+    if (tid == 0) {
+        for (int i = 0; i < kInRing; ++i) {
+            ptx::mbar_init(&B.in_full[i], 32);
+            ptx::mbar_init(&B.in_empty[i], 128);
+        }
+        for (int i = 0; i < kRing; ++i) {
+            ptx::mbar_init(&B.m1_full[i], 128);
+            ptx::mbar_init(&B.m1_empty[i], 1);
+            ptx::mbar_init(&B.m2_full[i], 128);
+            ptx::mbar_init(&B.m2_empty[i], 1);
+        }
+        for (int i = 0; i < kAccRing; ++i) {
+            ptx::mbar_init(&B.a2_full[i], 1);
+            ptx::mbar_init(&B.a2_free[i], 128);
+            ptx::mbar_init(&B.a3_full[i], 1);
+            ptx::mbar_init(&B.a3_free[i], 128);
+        }
+        ptx::mbar_init(B.fin, 1);
+        *abort_flag = 0;
+        ptx::mbar_fence_init();
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(p.wpack);
+        uint4* dst = reinterpret_cast<uint4*>(smem + C::oB);
+        for (int i = tid; i < 2 * C::kLayerB / 16; i += kThreads) dst[i] = __ldg(src + i);
+        // zero the whole A rings once (the dx overrun pixels 128..135 are read but never written)
+        uint4* r = reinterpret_cast<uint4*>(smem + C::oR1);
+        for (int i = tid; i < 2 * kRing * C::kSlotBytes / 16; i += kThreads) r[i] = make_uint4(0, 0, 0, 0);
+    }
+    if (warp == 0) {
+        ptx::tmem_alloc(tmem_slot, 512);
+        ptx::tmem_relinquish();
+    }
+    ptx::fence_proxy_async_smem();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const uint32_t smem_base = ptx::smem_u32(smem);
+
+    if (warp == 0) {
+        // ================= MMA issuer ========================================================
+        if (lane == 0) {
+            uint32_t m1_seq = 0, m2_seq = 0, a2_seq = 0, a3_seq = 0;
+            bool ok = true;
+            for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+                const ItemInfo it = decode_item(p, k);
+                const int NR = it.rows;
+                const int M1 = NR + 9, N2 = NR + 5, M2 = NR + 4;
+                for (int r = 0; r < M1 + p.lag; ++r) {
+                    if (r < M1) {
+                        const uint32_t q = m1_seq + r, s = q % kRing;
+                        ok = ok && wait_phase(&B.m1_full[s], (q / kRing) & 1, abort_flag, p.err);
+                        if (r < N2) {
+                            const uint32_t qa = a2_seq + r;
+                            ok = ok && wait_phase(&B.a2_free[qa % kAccRing], ((qa / kAccRing) & 1) ^ 1, abort_flag,
+                                                  p.err);
+                        }
+                        ptx::tc_fence_after();
+                        if (ok)
+                            issue_row<FP8>(tbase, a2_seq, r, N2, smem_base + C::oR1 + s * C::kSlotBytes,
+                                           smem_base + C::oB);
+                        ptx::mma_commit(&B.m1_empty[s]);
+                        if (r >= 4 && r - 4 < N2) ptx::mma_commit(&B.a2_full[(a2_seq + r - 4) % kAccRing]);
+                    }
+                    const int sr = r - 5 - p.lag;
+                    if (sr >= 0 && sr < M2) {
+                        const uint32_t q = m2_seq + sr, s = q % kRing;
+                        ok = ok && wait_phase(&B.m2_full[s], (q / kRing) & 1, abort_flag, p.err);
+                        if (sr < NR) {
+                            const uint32_t qa = a3_seq + sr;
+                            ok = ok && wait_phase(&B.a3_free[qa % kAccRing], ((qa / kAccRing) & 1) ^ 1, abort_flag,
+                                                  p.err);
+                        }
+                        ptx::tc_fence_after();
+                        if (ok)
+                            issue_row<FP8>(tbase + 256, a3_seq, sr, NR, smem_base + C::oR2 + s * C::kSlotBytes,
+                                           smem_base + C::oB + C::kLayerB);
+                        ptx::mma_commit(&B.m2_empty[s]);
+                        if (sr >= 4 && sr - 4 < NR) ptx::mma_commit(&B.a3_full[(a3_seq + sr - 4) % kAccRing]);
+                    }
+                }
+                m1_seq += M1;
+                m2_seq += M2;
+                a2_seq += N2;
+                a3_seq += NR;
+            }
+            // drain: all MMAs complete before TMEM is released
+            ptx::mma_commit(B.fin);
+            uint64_t t0 = gtime();
+            while (!ptx::mbar_test(B.fin, 0)) {
+                if (gtime() - t0 > kWaitNs) {
+                    *(volatile int*)p.err = MB_ERR_TIMEOUT;
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ================= input loader ======================================================
+        uint32_t in_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const ItemInfo it = decode_item(p, k);
+            const TcBlockDesc& d = p.blk[it.b];
+            const uint8_t* src = d.in + (int64_t)it.zi * d.in_slice;
+            const int nrows = it.rows + 14;
+            for (int u = 0; u < nrows; ++u) {
+                const uint32_t q = in_seq + u, s = q % kInRing;
+                wait_phase(&B.in_empty[s], ((q / kInRing) & 1) ^ 1, abort_flag, p.err);
+                const int sy = refl_clamp(d.ry0 + it.y0 - 7 + u, d.h);
+                const uint8_t* row = src + (int64_t)sy * d.in_pitch;
+                float* dst = in_ring + s * kPitch;
+                for (int c = lane; c < kInCols; c += 32) {
+                    const int sx = refl_clamp(d.rx0 + it.x0 - 7 + c, d.w);
+                    dst[c] = (float)__ldg(row + sx) / 255.0f;
+                }
+                ptx::mbar_arrive(&B.in_full[s]);
+            }
+            in_seq += nrows;
+        }
+    } else if (warp >= 12) {
+        // ================= layer 1 + max-filter producer ======================================
+        const int c = tid - 384;  // pixel column 0..127
+        const int pw = warp - 12;
+        float* stage = reinterpret_cast<float*>(smem + C::oSt1);
+        uint32_t in_seq = 0, m1_seq = 0;
+        float prev[32], cur[32];
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const ItemInfo it = decode_item(p, k);
+            const int NR = it.rows;
+            auto layer1 = [&](int row, float (&o)[32]) {
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) o[ch] = p.b1[ch];
+#pragma unroll
+                for (int ky = 0; ky < 5; ++ky) {
+                    const float* ir = in_ring + ((in_seq + row + ky) % kInRing) * kPitch + c;
+#pragma unroll
+                    for (int kx = 0; kx < 5; ++kx) {
+                        const float x = ir[kx];
+#pragma unroll
+                        for (int ch = 0; ch < 32; ++ch) o[ch] = fmaf(p.w1[ch][ky * 5 + kx], x, o[ch]);
+                    }
+                }
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) o[ch] = fmaxf(o[ch], 0.f);
+            };
+            for (int u = 0; u < 5; ++u) {
+                const uint32_t q = in_seq + u;
+                wait_phase(&B.in_full[q % kInRing], (q / kInRing) & 1, abort_flag, p.err);
+            }
+            layer1(0, prev);
+            ptx::mbar_arrive(&B.in_empty[in_seq % kInRing]);
+            const int M1 = NR + 9;
+            for (int t = 0; t < M1; ++t) {
+                const uint32_t qi = in_seq + t + 5;
+                wait_phase(&B.in_full[qi % kInRing], (qi / kInRing) & 1, abort_flag, p.err);
+                layer1(t + 1, cur);
+                ptx::mbar_arrive(&B.in_empty[(in_seq + t + 1) % kInRing]);
+                float m[32];
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], cur[ch]);
+                // horizontal neighbour c+1: shuffle inside the warp, staging across warps
+                float* st = stage + (t & 1) * 128;
+                if (lane == 0)
+#pragma unroll
+                    for (int ch = 0; ch < 32; ++ch) st[pw * 32 + ch] = m[ch];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) {
+                    float nb = __shfl_down_sync(0xffffffffu, m[ch], 1);
+                    if (lane == 31) nb = pw < 3 ? st[(pw + 1) * 32 + ch] : m[ch];
+                    m[ch] = fmaxf(m[ch], nb);
+                }
+                const uint32_t q = m1_seq + t, s = q % kRing;
+                wait_phase(&B.m1_empty[s], ((q / kRing) & 1) ^ 1, abort_flag, p.err);
+                store_pixel<FP8>(smem + C::oR1 + s * C::kSlotBytes, c, m, p.q1);
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&B.m1_full[s]);
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) prev[ch] = cur[ch];
+            }
+            for (int u = M1 + 1; u < NR + 14; ++u) ptx::mbar_arrive(&B.in_empty[(in_seq + u) % kInRing]);
+            in_seq += NR + 14;
+            m1_seq += M1;
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ================= layer-2 epilogue: bias, ReLU, max-filter -> A ring of layer 3 =======
+        const int c = tid - 128;
+        const int pw = warp - 4;
+        float* stage = reinterpret_cast<float*>(smem + C::oSt2);
+        uint32_t a2_seq = 0, m2_seq = 0;
+        float prev[32];
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const ItemInfo it = decode_item(p, k);
+            const int N2 = it.rows + 5;
+            for (int j = 0; j < N2; ++j) {
+                const uint32_t q = a2_seq + j, s = q % kAccRing;
+                wait_phase(&B.a2_full[s], (q / kAccRing) & 1, abort_flag, p.err);
+                ptx::tc_fence_after();
+                float v[32];
+                ptx::tmem_ld32(tbase + ((uint32_t)(32 * pw) << 16) + 32u * s, v);
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&B.a2_free[s]);
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) v[ch] = fmaxf(fmaf(v[ch], p.ep2_scale[ch], p.ep2_bias[ch]), 0.f);
+                if (j > 0) {
+                    float m[32];
+#pragma unroll
+                    for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], v[ch]);
+                    float* st = stage + (j & 1) * 128;
+                    if (lane == 0)
+#pragma unroll
+                        for (int ch = 0; ch < 32; ++ch) st[pw * 32 + ch] = m[ch];
+                    asm volatile("bar.sync 2, 128;" ::: "memory");
+#pragma unroll
+                    for (int ch = 0; ch < 32; ++ch) {
+                        float nb = __shfl_down_sync(0xffffffffu, m[ch], 1);
+                        if (lane == 31) nb = pw < 3 ? st[(pw + 1) * 32 + ch] : m[ch];
+                        m[ch] = fmaxf(m[ch], nb);
+                    }
+                    const uint32_t q2 = m2_seq + j - 1, s2 = q2 % kRing;
+                    wait_phase(&B.m2_empty[s2], ((q2 / kRing) & 1) ^ 1, abort_flag, p.err);
+                    store_pixel<FP8>(smem + C::oR2 + s2 * C::kSlotBytes, c, m, p.q2);
+                    ptx::fence_proxy_async_smem();
+                    ptx::mbar_arrive(&B.m2_full[s2]);
+                }
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) prev[ch] = v[ch];
+            }
+            a2_seq += N2;
+            m2_seq += N2 - 1;
+        }
+    } else if (warp >= 8 && warp < 12) {
+        // ================= layer-3 epilogue: bias, ReLU, head, sigmoid, store ==================
+        const int c = tid - 256;
+        const int pw = warp - 8;
+        uint32_t a3_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const ItemInfo it = decode_item(p, k);
+            const TcBlockDesc& d = p.blk[it.b];
+            const int NR = it.rows;
+            const bool col_ok = c < kStrip && it.x0 + c < d.rw;
+            for (int y = 0; y < NR; ++y) {
+                const uint32_t q = a3_seq + y, s = q % kAccRing;
+                wait_phase(&B.a3_full[s], (q / kAccRing) & 1, abort_flag, p.err);
+                ptx::tc_fence_after();
+                float v[32];
+                ptx::tmem_ld32(tbase + 256u + ((uint32_t)(32 * pw) << 16) + 32u * s, v);
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&B.a3_free[s]);
+                float z = p.hb;
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch)
+                    z = fmaf(p.hw[ch], fmaxf(fmaf(v[ch], p.ep3_scale[ch], p.ep3_bias[ch]), 0.f), z);
+                const float prob = 1.0f / (1.0f + expf(-z));
+                if (col_ok && !*abort_flag) {
+                    const int64_t idx = (int64_t)it.zi * d.out_slice + (int64_t)(it.y0 + y) * d.out_pitch + it.x0 + c;
+                    if (p.out_u8)
+                        static_cast<uint8_t*>(d.out)[idx] = (uint8_t)fminf(floorf(255.0f * prob + 0.5f), 255.0f);
+                    else
+                        static_cast<float*>(d.out)[idx] = prob;
+                }
+            }
+            a3_seq += NR;
+        }
+    }
+    // warps 2 and 3 have no role
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 0) ptx::tmem_dealloc(tbase, 512);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+
+static uint16_t bf16_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// Pack one 5x5 32->32 layer's weights W[co][ci][dy][dx] (already scaled) as the B operand groups.
+static void pack_layer(const float* W, bool fp8, const float* wscale_inv, uint8_t* out) {
+    for (int dx = 0; dx < 5; ++dx)
+        for (int i = 0; i < 5; ++i) {
+            const int dy = 4 - i;
+            for (int co = 0; co < 32; ++co) {
+                const int n = i * 32 + co;
+                for (int ci = 0; ci < 32; ++ci) {
+                    const float w = W[((co * 32 + ci) * 5 + dy) * 5 + dx];
+                    if (!fp8) {
+                        const int g = dx * 2 + ci / 16, kc = (ci % 16) / 8;
+                        uint16_t b = bf16_bits(w);
+                        memcpy(out + g * kGroupBytes + kc * 2560 + n * 16 + (ci % 8) * 2, &b, 2);
+                    } else {
+                        const int g = dx, kc = ci / 16;
+                        __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(w * wscale_inv[co], __NV_SATFINITE, __NV_E4M3);
+                        out[g * kGroupBytes + kc * 2560 + n * 16 + (ci % 16)] = q;
+                    }
+                }
+            }
+        }
+}
+
+struct TcState {
+    TcParams base;             // weights and epilogue constants (blocks filled per launch)
+    uint8_t* d_wpack = nullptr;
+    int* h_err = nullptr;      // mapped pinned host word the kernel writes on a timed-out wait
+    int* d_err = nullptr;      // its device alias
+};
+
+struct GraphCacheEntry {
+    std::vector<mb_block> blocks;
+    mb_out_type ot;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static TcState* state_of(mb_net* net) { return reinterpret_cast<TcState*>(net->tc_state); }
+
+mb_status tc_prepare(mb_net* net) {
+    const bool fp8 = net->prec == MB_PREC_FP8;
+    if (fp8 && !net->calibrated) {
+        // calibration provides the activation scales; until then only the FP32 pieces exist
+    }
+    TcState* S = state_of(net);
+    if (!S) {
+        S = new (std::nothrow) TcState();
+        if (!S) {
+            set_error("host allocation failed");
+            return MB_ERR_OOM;
+        }
+        memset(&S->base, 0, sizeof(S->base));
+        net->tc_state = S;
+    }
+    const float* P = net->host_params.data();
+    const float* W1 = P;
+    const float* B1 = W1 + 800;
+    const float* W2 = B1 + 32;
+    const float* B2 = W2 + 25600;
+    const float* W3 = B2 + 32;
+    const float* B3 = W3 + 25600;
+    const float* HW = B3 + 32;
+    TcParams& q = S->base;
+    for (int co = 0; co < 32; ++co) {
+        for (int k = 0; k < 25; ++k) q.w1[co][k] = W1[co * 25 + k];
+        q.b1[co] = B1[co];
+        q.hw[co] = HW[co];
+    }
+    q.hb = HW[32];
+    const size_t layer_bytes = (size_t)(fp8 ? 5 : 10) * kGroupBytes;
+    std::vector<uint8_t> pack(2 * layer_bytes, 0);
+    if (!fp8) {
+        for (int c = 0; c < 32; ++c) {
+            q.ep2_scale[c] = 1.f;
+            q.ep2_bias[c] = B2[c];
+            q.ep3_scale[c] = 1.f;
+            q.ep3_bias[c] = B3[c];
+            q.q1[c] = 1.f;
+            q.q2[c] = 1.f;
+        }
+        pack_layer(W2, false, nullptr, pack.data());
+        pack_layer(W3, false, nullptr, pack.data() + layer_bytes);
+    } else {
+        // activation scale s_a = amax / 448 per input channel, folded into the next layer's
+        // weights; then a per-output-channel weight scale s_w = amax|W'| / 448.
+        const float* Ws[2] = {W2, W3};
+        const float* Bs[2] = {B2, B3};
+        for (int l = 0; l < 2; ++l) {
+            float sa[32];
+            for (int ci = 0; ci < 32; ++ci) {
+                const float a = net->fp8_amax[l][ci];
+                sa[ci] = a > 0.f ? a / 448.f : 1.f;
+                (l == 0 ? q.q1 : q.q2)[ci] = 1.f / sa[ci];
+            }
+            std::vector<float> Wp(25600);
+            float inv[32];
+            for (int co = 0; co < 32; ++co) {
+                float amax = 0.f;
+                for (int ci = 0; ci < 32; ++ci)
+                    for (int t = 0; t < 25; ++t) {
+                        const float v = Ws[l][(co * 32 + ci) * 25 + t] * sa[ci];
+                        Wp[(co * 32 + ci) * 25 + t] = v;
+                        amax = std::max(amax, std::fabs(v));
+                    }
+                const float sw = amax > 0.f ? amax / 448.f : 1.f;
+                inv[co] = 1.f / sw;
+                (l == 0 ? q.ep2_scale : q.ep3_scale)[co] = sw;
+                (l == 0 ? q.ep2_bias : q.ep3_bias)[co] = Bs[l][co];
+            }
+            pack_layer(Wp.data(), true, inv, pack.data() + l * layer_bytes);
+        }
+    }
+    if (!S->d_wpack) MB_TRY(dev_alloc((void**)&S->d_wpack, 2 * 10 * kGroupBytes));
+    if (!S->h_err) {
+        if (fault_oom()) {
+            set_error("pinned allocation failed (MB_FAULT_OOM injected)");
+            return MB_ERR_OOM;
+        }
+        MB_CUDA(cudaHostAlloc((void**)&S->h_err, sizeof(int), cudaHostAllocMapped));
+        *S->h_err = 0;
+        MB_CUDA(cudaHostGetDevicePointer((void**)&S->d_err, S->h_err, 0));
+    }
+    MB_CUDA(cudaMemcpy(S->d_wpack, pack.data(), pack.size(), cudaMemcpyHostToDevice));
+    q.wpack = S->d_wpack;
+    q.err = S->d_err;
+    return MB_OK;
+}
+
+static void drop_graphs(mb_net* net) {
+    for (GraphCacheEntry* g : net->graphs) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+    }
+    net->graphs.clear();
+}
+
+void tc_release(mb_net* net) {
+    drop_graphs(net);
+    TcState* S = state_of(net);
+    if (S) {
+        dev_free(S->d_wpack);
+        if (S->h_err) cudaFreeHost(S->h_err);
+        delete S;
+        net->tc_state = nullptr;
+    }
+}
+
+static int g_num_sms = 0;
+
+static mb_status launch_tc(mb_net* net, TcParams& prm, cudaStream_t st) {
+    const bool fp8 = net->prec == MB_PREC_FP8;
+    if (g_num_sms == 0) {
+        int dev = 0;
+        MB_CUDA(cudaGetDevice(&dev));
+        MB_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int smem = fp8 ? Cfg<true>::kSmem : Cfg<false>::kSmem;
+    const int grid = std::max(1, std::min(prm.n_items, g_num_sms));
+    if (fp8) {
+        static bool attr = false;
+        if (!attr) {
+            MB_CUDA(cudaFuncSetAttribute(tc_fused_teacher<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr = true;
+        }
+        tc_fused_teacher<true><<<grid, kThreads, smem, st>>>(prm);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            MB_CUDA(cudaFuncSetAttribute(tc_fused_teacher<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr = true;
+        }
+        tc_fused_teacher<false><<<grid, kThreads, smem, st>>>(prm);
+    }
+    count_launch();
+    MB_CUDA(cudaGetLastError());
+    return MB_OK;
+}
+
+// Fill the block table for up to kMaxBlocks blocks starting at `first`; returns blocks used.
+static int fill_blocks(mb_net* net, TcParams& prm, const mb_block* blocks, int n_blocks, int first,
+                       const int64_t* y0, const int64_t* x0, const int64_t* rows, const int64_t* cols,
+                       mb_out_type ot) {
+    int nb = 0, items = 0;
+    const int R = std::max(8, net->rows_per_item);
+    for (int i = first; i < n_blocks && nb < kMaxBlocks; ++i) {
+        const mb_block& b = blocks[i];
+        if (b.z == 0 || rows[i] == 0 || cols[i] == 0) continue;
+        TcBlockDesc& d = prm.blk[nb];
+        d.in = b.in;
+        d.out = b.out;
+        d.in_pitch = b.in_pitch;
+        d.in_slice = b.in_slice_pitch;
+        d.out_pitch = b.out_pitch;
+        d.out_slice = b.out_slice_pitch;
+        d.h = (int)b.h;
+        d.w = (int)b.w;
+        d.ry0 = (int)y0[i];
+        d.rx0 = (int)x0[i];
+        d.rh = (int)rows[i];
+        d.rw = (int)cols[i];
+        d.z = (int)b.z;
+        d.n_strips = (d.rw + kStrip - 1) / kStrip;
+        d.n_chunks = (d.rh + R - 1) / R;
+        d.item_start = items;
+        items += d.z * d.n_strips * d.n_chunks;
+        ++nb;
+    }
+    prm.n_blocks = nb;
+    prm.n_items = items;
+    prm.rows_per_item = R;
+    prm.lag = std::max(1, std::min(net->stages, kRing - 1));
+    prm.out_u8 = ot == MB_OUT_U8;
+    int used = first;
+    int counted = 0;
+    while (used < n_blocks && counted < kMaxBlocks) {
+        const mb_block& b = blocks[used];
+        if (!(b.z == 0 || rows[used] == 0 || cols[used] == 0)) ++counted;
+        ++used;
+    }
+    return used;
+}
+
+// A timed-out device wait is reported by the next call that looks (the word lives in mapped host
+// memory, so no synchronisation is needed to read it).
+static mb_status check_err(mb_net* net) {
+    TcState* S = state_of(net);
+    if (S && S->h_err && *(volatile int*)S->h_err) {
+        *(volatile int*)S->h_err = 0;
+        set_error("a tensor-core launch on this net gave up waiting (device-side wait limit)");
+        return MB_ERR_TIMEOUT;
+    }
+    return MB_OK;
+}
+
+mb_status tc_poll_error(mb_net* net) { return check_err(net); }
+
+mb_status tc_infer_blocks(mb_net* net, const mb_block* blocks, int n_blocks, const int64_t* y0, const int64_t* x0,
+                          const int64_t* rows, const int64_t* cols, mb_out_type ot, cudaStream_t st,
+                          bool use_graph) {
+    TcState* S = state_of(net);
+    if (!S || !S->d_wpack) {
+        set_error("tensor-core weights not prepared");
+        return MB_ERR_NOT_READY;
+    }
+    MB_TRY(check_err(net));
+    for (int i = 0; i < n_blocks; ++i)
+        if (blocks[i].h > (1 << 30) / 2 || blocks[i].w > (1 << 30) / 2) {
+            set_error("block %d too large", i);
+            return MB_ERR_SHAPE;
+        }
+    if (use_graph) {
+        for (GraphCacheEntry* g : net->graphs) {
+            if (g->ot != ot || (int)g->blocks.size() != n_blocks) continue;
+            if (memcmp(g->blocks.data(), blocks, sizeof(mb_block) * n_blocks) != 0) continue;
+            MB_CUDA(cudaGraphLaunch(g->exec, st));
+            count_launch((int)((n_blocks + kMaxBlocks - 1) / kMaxBlocks));
+            return check_err(net);
+        }
+        if (net->graphs.size() >= 8) drop_graphs(net);
+        GraphCacheEntry* g = new (std::nothrow) GraphCacheEntry();
+        if (!g) {
+            set_error("host allocation failed");
+            return MB_ERR_OOM;
+        }
+        g->blocks.assign(blocks, blocks + n_blocks);
+        g->ot = ot;
+        cudaStream_t cs = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete g;
+            return cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__);
+        }
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        mb_status s = e == cudaSuccess ? MB_OK : cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+        int first = 0;
+        const int64_t before = mb_launch_count();
+        while (s == MB_OK && first < n_blocks) {
+            TcParams prm = S->base;
+            int next = fill_blocks(net, prm, blocks, n_blocks, first, y0, x0, rows, cols, ot);
+            if (prm.n_items > 0) s = launch_tc(net, prm, cs);
+            first = next;
+        }
+        const int64_t launched = mb_launch_count() - before;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (s == MB_OK && e != cudaSuccess) s = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        if (s == MB_OK) {
+            e = cudaGraphInstantiate(&g->exec, graph, 0);
+            if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        }
+        cudaStreamDestroy(cs);
+        g->graph = graph;
+        if (s != MB_OK) {
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            if (g->graph) cudaGraphDestroy(g->graph);
+            delete g;
+            return s;
+        }
+        net->graphs.push_back(g);
+        (void)launched;
+        MB_CUDA(cudaGraphLaunch(g->exec, st));
+        return check_err(net);
+    }
+    int first = 0;
+    while (first < n_blocks) {
+        TcParams prm = S->base;
+        int next = fill_blocks(net, prm, blocks, n_blocks, first, y0, x0, rows, cols, ot);
+        if (prm.n_items > 0) MB_TRY(launch_tc(net, prm, st));
+        first = next;
+    }
+    return check_err(net);
+}
+
 }  // namespace mb
 
 extern "C" mb_status mb_autotune(mb_net*, int64_t, int64_t, int64_t, const char*, int32_t*, void*) {
