@@ -45,9 +45,8 @@ constexpr int kStrip = 118;          // valid output columns per 128-pixel strip
 constexpr int kInCols = 132;         // input columns read per row
 constexpr int kInRing = 8;           // input row ring
 constexpr int kRing = 4;             // mf1 / mf2 ring slots
-constexpr int kAccRing = 8;          // TMEM row accumulators per layer
 constexpr int kMaxBlocks = 64;       // blocks per launch (kernel-parameter table)
-constexpr int kGroupBytes = 5120;    // one B group: 2 chunks x 160 rows x 16 B
+constexpr int kWpackConstOff = 2 * 10 * 5120;  // constants follow the largest packed B (BF16)
 constexpr uint64_t kWaitNs = 4000000000ull;
 
 struct TcBlockDesc {
@@ -59,15 +58,14 @@ struct TcBlockDesc {
     int z, n_strips, n_chunks, item_start;
 };
 
+// Per-channel constants, staged into shared memory at kernel start (floats):
+//   w1[25 taps][32 ch] | b1 | ep2 scale | ep2 bias | ep3 scale | ep3 bias | q1 | q2 | head w
+constexpr int kCW1 = 0, kCB1 = 800, kCE2S = 832, kCE2B = 864, kCE3S = 896, kCE3B = 928, kCQ1 = 960,
+              kCQ2 = 992, kCHW = 1024, kConsts = 1056;
+
 struct TcParams {
-    float w1[32][25];
-    float b1[32];
-    float ep2_scale[32], ep2_bias[32];
-    float ep3_scale[32], ep3_bias[32];
-    float q1[32], q2[32];   // activation quantisation multipliers (FP8), 1 for BF16
-    float hw[32];
     float hb;
-    const uint8_t* wpack;   // packed B operands (global), layer 2 then layer 3
+    const uint8_t* wpack;   // global: packed B operands of layers 2 and 3, then the constants
     int* err;               // error word (MB_ERR_TIMEOUT on a timed-out wait)
     int n_blocks, n_items, rows_per_item, lag, out_u8;
     TcBlockDesc blk[kMaxBlocks];
@@ -78,7 +76,15 @@ struct Cfg {
     static constexpr int kChunks = FP8 ? 2 : 4;                 // 16-byte channel chunks per pixel
     static constexpr int kSlotBytes = kChunks * kPitch * 16;
     static constexpr int kGroups = FP8 ? 5 : 10;                // MMAs per (layer, input row, run)
-    static constexpr int kLayerB = kGroups * kGroupBytes;
+    // TMEM row accumulators per layer. BF16: a ring of 8 (windows of 5 rows that wrap are split
+    // into two MMAs). FP8: a ring of exactly 5 with the B blocks stored twice in order
+    // [0 1 2 3 4 0 1 2 3], so every full window is one N=160 MMA into slots 0..4 whose B rows
+    // start at the block that lands in slot 0.
+    static constexpr int kAcc = FP8 ? 5 : 8;
+    static constexpr int kBBlocks = FP8 ? 9 : 5;                 // 32-row blocks stored per group
+    static constexpr int kLboB = kBBlocks * 32 * 16;             // B chunk stride (bytes)
+    static constexpr int kGroupB = 2 * kLboB;                    // bytes per B group
+    static constexpr int kLayerB = kGroups * kGroupB;
     // shared memory map
     static constexpr int oB = 0;
     static constexpr int oR1 = oB + 2 * kLayerB;
@@ -86,8 +92,9 @@ struct Cfg {
     static constexpr int oIn = oR2 + kRing * kSlotBytes;
     static constexpr int oSt1 = oIn + kInRing * kPitch * 4;
     static constexpr int oSt2 = oSt1 + 2 * 4 * 32 * 4;
-    static constexpr int oBar = oSt2 + 2 * 4 * 32 * 4;
-    static constexpr int kBars = 2 * kInRing + 4 * kRing + 4 * kAccRing + 1;
+    static constexpr int oConst = oSt2 + 2 * 4 * 32 * 4;
+    static constexpr int oBar = oConst + kConsts * 4;
+    static constexpr int kBars = 2 * kInRing + 4 * kRing + 4 * 8 + 1;
     static constexpr int oMisc = oBar + kBars * 8;
     static constexpr int kSmem = oMisc + 16;
 };
@@ -196,37 +203,58 @@ __device__ __forceinline__ void store_pixel(uint8_t* slot, int c, const float (&
     }
 }
 
-// Issue the MMAs of one input row for one layer: output rows j = r-4+i of the layer for the
-// valid blocks i (0 <= j < n_out), split into runs of contiguous TMEM ring slots. Block 4 (row
-// j = r) is overwritten by the first group and accumulated by the others.
+// Issue the MMAs of one input row r for one layer: output rows j = r-4+i of the layer for the
+// valid blocks i (0 <= j < n_out). Every MMA accumulates; the epilogue zeroes an accumulator after
+// draining it, so a row's first contribution adds to zero. Blocks go to ring slots
+// (base + r - 4 + i) mod kAcc; runs of contiguous slots are one MMA each.
 template <bool FP8>
-__device__ __forceinline__ void issue_row(uint32_t tcol0, uint32_t acc_base_seq, int r, int n_out,
-                                          uint32_t a_slot_addr, uint32_t b_layer_addr) {
-    constexpr int G = Cfg<FP8>::kGroups;
+__device__ __forceinline__ void issue_row(uint32_t tcol0, uint32_t acc_base_seq, int r, int n_out, uint64_t adesc0,
+                                          uint64_t bdesc0) {
+    using C = Cfg<FP8>;
+    constexpr int G = C::kGroups;
+    constexpr int K = C::kAcc;
+    constexpr uint32_t fmt = FP8 ? ptx::kFmtE4M3 : ptx::kFmtBF16;
     const int ilo = max(0, 4 - r);
-    const int ihi = min(4, n_out - 1 - r + 4);
+    const int ihi = min(4, n_out + 3 - r);
     if (ilo > ihi) return;
-#pragma unroll 1
+    const int s_lo = (int)((acc_base_seq + (uint32_t)(r - 4 + ilo)) % K);
+    uint32_t d[2], boff[2], idesc[2];
+    int nrun;
+    if (K == 5 && ilo == 0 && ihi == 4) {
+        // full window: slots 0..4, B rows rotated so slot 0 receives block (5 - s_lo) mod 5
+        const int i0 = (5 - s_lo) % 5;
+        d[0] = tcol0;
+        boff[0] = (uint32_t)(i0 * 32 * 16) >> 4;
+        idesc[0] = ptx::idesc_f32acc(fmt, 128, 160);
+        nrun = 1;
+    } else {
+        const int iw = ilo + (K - s_lo);  // first block whose slot wrapped to 0
+        const int hi0 = iw <= ihi ? iw - 1 : ihi;
+        d[0] = tcol0 + 32u * (uint32_t)s_lo;
+        boff[0] = (uint32_t)(ilo * 32 * 16) >> 4;
+        idesc[0] = ptx::idesc_f32acc(fmt, 128, (uint32_t)(32 * (hi0 - ilo + 1)));
+        nrun = 1;
+        if (iw <= ihi) {
+            d[1] = tcol0;
+            boff[1] = (uint32_t)(iw * 32 * 16) >> 4;
+            idesc[1] = ptx::idesc_f32acc(fmt, 128, (uint32_t)(32 * (ihi - iw + 1)));
+            nrun = 2;
+        }
+    }
+#pragma unroll
     for (int g = 0; g < G; ++g) {
         const int dx = FP8 ? g : (g >> 1);
         const int hk = FP8 ? 0 : (g & 1);
-        const uint32_t a_addr = a_slot_addr + (uint32_t)(hk * 2 * kPitch * 16 + dx * 16);
-        const uint64_t adesc = ptx::smem_desc(a_addr, kPitch * 16, 128);
-        int i = ilo;
-        while (i <= ihi) {
-            const uint32_t slot0 = (acc_base_seq + (uint32_t)(r - 4 + i)) % kAccRing;
-            int i1 = i;
-            // extend the run while slots stay contiguous; block 4 of group 0 stands alone
-            while (i1 + 1 <= ihi && (slot0 + (uint32_t)(i1 + 1 - i)) < kAccRing && !(g == 0 && i1 + 1 == 4)) ++i1;
-            const int nb = i1 - i + 1;
-            const uint32_t d = tcol0 + 32u * slot0;
-            const uint64_t bdesc = ptx::smem_desc(b_layer_addr + (uint32_t)(g * kGroupBytes + i * 512), 160 * 16, 128);
-            const uint32_t acc = (g == 0 && i == 4) ? 0u : 1u;
-            if (FP8)
-                ptx::mma_e4m3(d, adesc, bdesc, ptx::idesc_f32acc(ptx::kFmtE4M3, 128, 32 * nb), acc);
-            else
-                ptx::mma_bf16(d, adesc, bdesc, ptx::idesc_f32acc(ptx::kFmtBF16, 128, 32 * nb), acc);
-            i = i1 + 1;
+        const uint64_t ad = adesc0 + (uint64_t)((hk * 2 * kPitch * 16 + dx * 16) >> 4);
+        const uint64_t bg = bdesc0 + (uint64_t)((g * C::kGroupB) >> 4);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k < nrun) {
+                if (FP8)
+                    ptx::mma_e4m3(d[k], ad, bg + boff[k], idesc[k], 1u);
+                else
+                    ptx::mma_bf16(d[k], ad, bg + boff[k], idesc[k], 1u);
+            }
         }
     }
 }
@@ -244,13 +272,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     B.m2_full = B.m1_empty + kRing;
     B.m2_empty = B.m2_full + kRing;
     B.a2_full = B.m2_empty + kRing;
-    B.a2_free = B.a2_full + kAccRing;
-    B.a3_full = B.a2_free + kAccRing;
-    B.a3_free = B.a3_full + kAccRing;
-    B.fin = B.a3_free + kAccRing;
+    B.a2_free = B.a2_full + 8;
+    B.a3_full = B.a2_free + 8;
+    B.a3_free = B.a3_full + 8;
+    B.fin = B.a3_free + 8;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::oMisc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::oMisc + 4);
     float* in_ring = reinterpret_cast<float*>(smem + C::oIn);
+    const float* cst = reinterpret_cast<const float*>(smem + C::oConst);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -267,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             ptx::mbar_init(&B.m2_full[i], 128);
             ptx::mbar_init(&B.m2_empty[i], 1);
         }
-        for (int i = 0; i < kAccRing; ++i) {
+        for (int i = 0; i < C::kAcc; ++i) {
             ptx::mbar_init(&B.a2_full[i], 1);
             ptx::mbar_init(&B.a2_free[i], 128);
             ptx::mbar_init(&B.a3_full[i], 1);
@@ -281,6 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         const uint4* src = reinterpret_cast<const uint4*>(p.wpack);
         uint4* dst = reinterpret_cast<uint4*>(smem + C::oB);
         for (int i = tid; i < 2 * C::kLayerB / 16; i += kThreads) dst[i] = __ldg(src + i);
+        const uint4* csrc = reinterpret_cast<const uint4*>(p.wpack + kWpackConstOff);
+        uint4* cdst = reinterpret_cast<uint4*>(smem + C::oConst);
+        for (int i = tid; i < kConsts / 4; i += kThreads) cdst[i] = __ldg(csrc + i);
         // zero the whole A rings once (the dx overrun pixels 128..135 are read but never written)
         uint4* r = reinterpret_cast<uint4*>(smem + C::oR1);
         for (int i = tid; i < 2 * kRing * C::kSlotBytes / 16; i += kThreads) r[i] = make_uint4(0, 0, 0, 0);
@@ -295,12 +327,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     ptx::tc_fence_after();
     const uint32_t tbase = *tmem_slot;
     const uint32_t smem_base = ptx::smem_u32(smem);
+    if (warp >= 4 && warp < 12) {
+        // every accumulator starts at zero (the MMAs only accumulate)
+        const uint32_t col0 = warp < 8 ? 0u : 256u;
+        const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+        for (int sl = 0; sl < C::kAcc; ++sl) ptx::tmem_st32_zero(tbase + lanes + col0 + 32u * sl);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
 
     if (warp == 0) {
         // ================= MMA issuer ========================================================
         if (lane == 0) {
             uint32_t m1_seq = 0, m2_seq = 0, a2_seq = 0, a3_seq = 0;
             bool ok = true;
+            // ring slot i of a layer's A operand: base descriptor + i slots (start-address field)
+            const uint64_t ad1 = ptx::smem_desc(smem_base + C::oR1, kPitch * 16, 128);
+            const uint64_t ad2 = ptx::smem_desc(smem_base + C::oR2, kPitch * 16, 128);
+            const uint64_t bd2 = ptx::smem_desc(smem_base + C::oB, C::kLboB, 128);
+            const uint64_t bd3 = ptx::smem_desc(smem_base + C::oB + C::kLayerB, C::kLboB, 128);
             for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
                 const ItemInfo it = decode_item(p, k);
                 const int NR = it.rows;
@@ -311,15 +357,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                         ok = ok && wait_phase(&B.m1_full[s], (q / kRing) & 1, abort_flag, p.err);
                         if (r < N2) {
                             const uint32_t qa = a2_seq + r;
-                            ok = ok && wait_phase(&B.a2_free[qa % kAccRing], ((qa / kAccRing) & 1) ^ 1, abort_flag,
+                            ok = ok && wait_phase(&B.a2_free[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag,
                                                   p.err);
                         }
                         ptx::tc_fence_after();
-                        if (ok)
-                            issue_row<FP8>(tbase, a2_seq, r, N2, smem_base + C::oR1 + s * C::kSlotBytes,
-                                           smem_base + C::oB);
+                        if (ok) issue_row<FP8>(tbase, a2_seq, r, N2, ad1 + (uint64_t)(s * (C::kSlotBytes >> 4)), bd2);
                         ptx::mma_commit(&B.m1_empty[s]);
-                        if (r >= 4 && r - 4 < N2) ptx::mma_commit(&B.a2_full[(a2_seq + r - 4) % kAccRing]);
+                        if (r >= 4 && r - 4 < N2) ptx::mma_commit(&B.a2_full[(a2_seq + r - 4) % C::kAcc]);
                     }
                     const int sr = r - 5 - p.lag;
                     if (sr >= 0 && sr < M2) {
@@ -327,15 +371,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                         ok = ok && wait_phase(&B.m2_full[s], (q / kRing) & 1, abort_flag, p.err);
                         if (sr < NR) {
                             const uint32_t qa = a3_seq + sr;
-                            ok = ok && wait_phase(&B.a3_free[qa % kAccRing], ((qa / kAccRing) & 1) ^ 1, abort_flag,
+                            ok = ok && wait_phase(&B.a3_free[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag,
                                                   p.err);
                         }
                         ptx::tc_fence_after();
-                        if (ok)
-                            issue_row<FP8>(tbase + 256, a3_seq, sr, NR, smem_base + C::oR2 + s * C::kSlotBytes,
-                                           smem_base + C::oB + C::kLayerB);
+                        if (ok) issue_row<FP8>(tbase + 256, a3_seq, sr, NR, ad2 + (uint64_t)(s * (C::kSlotBytes >> 4)), bd3);
                         ptx::mma_commit(&B.m2_empty[s]);
-                        if (sr >= 4 && sr - 4 < NR) ptx::mma_commit(&B.a3_full[(a3_seq + sr - 4) % kAccRing]);
+                        if (sr >= 4 && sr - 4 < NR) ptx::mma_commit(&B.a3_full[(a3_seq + sr - 4) % C::kAcc]);
                     }
                 }
                 m1_seq += M1;
@@ -386,54 +428,70 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const ItemInfo it = decode_item(p, k);
             const int NR = it.rows;
-            auto layer1 = [&](int row, float (&o)[32]) {
+            const int M1 = NR + 9;
+            for (int t = -1; t < M1; ++t) {
+                if (t < 0) {
+                    for (int u = 0; u < 5; ++u) {
+                        const uint32_t q = in_seq + u;
+                        wait_phase(&B.in_full[q % kInRing], (q / kInRing) & 1, abort_flag, p.err);
+                    }
+                } else {
+                    const uint32_t qi = in_seq + t + 5;
+                    wait_phase(&B.in_full[qi % kInRing], (qi / kInRing) & 1, abort_flag, p.err);
+                }
+                // layer 1 at input-frame row t+1, column c: FP32 (packed two-channel FMAs), weights
+                // broadcast from shared memory
+                float2 a2[16];
 #pragma unroll
-                for (int ch = 0; ch < 32; ++ch) o[ch] = p.b1[ch];
+                for (int j = 0; j < 8; ++j) {
+                    const float4 b = *reinterpret_cast<const float4*>(cst + kCB1 + 4 * j);
+                    a2[2 * j] = make_float2(b.x, b.y);
+                    a2[2 * j + 1] = make_float2(b.z, b.w);
+                }
 #pragma unroll
                 for (int ky = 0; ky < 5; ++ky) {
-                    const float* ir = in_ring + ((in_seq + row + ky) % kInRing) * kPitch + c;
+                    const float* ir = in_ring + ((in_seq + t + 1 + ky) % kInRing) * kPitch + c;
 #pragma unroll
                     for (int kx = 0; kx < 5; ++kx) {
                         const float x = ir[kx];
+                        const float2 xx = make_float2(x, x);
+                        const float4* wt = reinterpret_cast<const float4*>(cst + kCW1 + (ky * 5 + kx) * 32);
 #pragma unroll
-                        for (int ch = 0; ch < 32; ++ch) o[ch] = fmaf(p.w1[ch][ky * 5 + kx], x, o[ch]);
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 w = wt[j];
+                            a2[2 * j] = __ffma2_rn(make_float2(w.x, w.y), xx, a2[2 * j]);
+                            a2[2 * j + 1] = __ffma2_rn(make_float2(w.z, w.w), xx, a2[2 * j + 1]);
+                        }
                     }
                 }
 #pragma unroll
-                for (int ch = 0; ch < 32; ++ch) o[ch] = fmaxf(o[ch], 0.f);
-            };
-            for (int u = 0; u < 5; ++u) {
-                const uint32_t q = in_seq + u;
-                wait_phase(&B.in_full[q % kInRing], (q / kInRing) & 1, abort_flag, p.err);
-            }
-            layer1(0, prev);
-            ptx::mbar_arrive(&B.in_empty[in_seq % kInRing]);
-            const int M1 = NR + 9;
-            for (int t = 0; t < M1; ++t) {
-                const uint32_t qi = in_seq + t + 5;
-                wait_phase(&B.in_full[qi % kInRing], (qi / kInRing) & 1, abort_flag, p.err);
-                layer1(t + 1, cur);
-                ptx::mbar_arrive(&B.in_empty[(in_seq + t + 1) % kInRing]);
-                float m[32];
-#pragma unroll
-                for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], cur[ch]);
-                // horizontal neighbour c+1: shuffle inside the warp, staging across warps
-                float* st = stage + (t & 1) * 128;
-                if (lane == 0)
-#pragma unroll
-                    for (int ch = 0; ch < 32; ++ch) st[pw * 32 + ch] = m[ch];
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll
-                for (int ch = 0; ch < 32; ++ch) {
-                    float nb = __shfl_down_sync(0xffffffffu, m[ch], 1);
-                    if (lane == 31) nb = pw < 3 ? st[(pw + 1) * 32 + ch] : m[ch];
-                    m[ch] = fmaxf(m[ch], nb);
+                for (int j = 0; j < 16; ++j) {
+                    cur[2 * j] = fmaxf(a2[j].x, 0.f);
+                    cur[2 * j + 1] = fmaxf(a2[j].y, 0.f);
                 }
-                const uint32_t q = m1_seq + t, s = q % kRing;
-                wait_phase(&B.m1_empty[s], ((q / kRing) & 1) ^ 1, abort_flag, p.err);
-                store_pixel<FP8>(smem + C::oR1 + s * C::kSlotBytes, c, m, p.q1);
-                ptx::fence_proxy_async_smem();
-                ptx::mbar_arrive(&B.m1_full[s]);
+                ptx::mbar_arrive(&B.in_empty[(in_seq + t + 1) % kInRing]);
+                if (t >= 0) {
+                    float (&m)[32] = prev;  // vertical max in place; prev is reloaded from cur below
+#pragma unroll
+                    for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], cur[ch]);
+                    // horizontal neighbour c+1: shuffle inside the warp, staging across warps
+                    float* st = stage + (t & 1) * 128;
+                    if (lane == 0)
+#pragma unroll
+                        for (int ch = 0; ch < 32; ++ch) st[pw * 32 + ch] = m[ch];
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+                    for (int ch = 0; ch < 32; ++ch) {
+                        float nb = __shfl_down_sync(0xffffffffu, m[ch], 1);
+                        if (lane == 31) nb = pw < 3 ? st[(pw + 1) * 32 + ch] : m[ch];
+                        m[ch] = fmaxf(m[ch], nb);
+                    }
+                    const uint32_t q = m1_seq + t, s = q % kRing;
+                    wait_phase(&B.m1_empty[s], ((q / kRing) & 1) ^ 1, abort_flag, p.err);
+                    store_pixel<FP8>(smem + C::oR1 + s * C::kSlotBytes, c, m, cst + kCQ1);
+                    ptx::fence_proxy_async_smem();
+                    ptx::mbar_arrive(&B.m1_full[s]);
+                }
 #pragma unroll
                 for (int ch = 0; ch < 32; ++ch) prev[ch] = cur[ch];
             }
@@ -452,17 +510,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             const ItemInfo it = decode_item(p, k);
             const int N2 = it.rows + 5;
             for (int j = 0; j < N2; ++j) {
-                const uint32_t q = a2_seq + j, s = q % kAccRing;
-                wait_phase(&B.a2_full[s], (q / kAccRing) & 1, abort_flag, p.err);
+                const uint32_t q = a2_seq + j, s = q % C::kAcc;
+                wait_phase(&B.a2_full[s], (q / C::kAcc) & 1, abort_flag, p.err);
                 ptx::tc_fence_after();
                 float v[32];
-                ptx::tmem_ld32(tbase + ((uint32_t)(32 * pw) << 16) + 32u * s, v);
+                const uint32_t ta = tbase + ((uint32_t)(32 * pw) << 16) + 32u * s;
+                ptx::tmem_ld32(ta, v);
+                ptx::tmem_st32_zero(ta);
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(&B.a2_free[s]);
 #pragma unroll
-                for (int ch = 0; ch < 32; ++ch) v[ch] = fmaxf(fmaf(v[ch], p.ep2_scale[ch], p.ep2_bias[ch]), 0.f);
+                for (int ch = 0; ch < 32; ++ch) v[ch] = fmaxf(fmaf(v[ch], cst[kCE2S + ch], cst[kCE2B + ch]), 0.f);
                 if (j > 0) {
-                    float m[32];
+                    float (&m)[32] = prev;  // vertical max in place; prev is reloaded from v below
 #pragma unroll
                     for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], v[ch]);
                     float* st = stage + (j & 1) * 128;
@@ -478,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                     }
                     const uint32_t q2 = m2_seq + j - 1, s2 = q2 % kRing;
                     wait_phase(&B.m2_empty[s2], ((q2 / kRing) & 1) ^ 1, abort_flag, p.err);
-                    store_pixel<FP8>(smem + C::oR2 + s2 * C::kSlotBytes, c, m, p.q2);
+                    store_pixel<FP8>(smem + C::oR2 + s2 * C::kSlotBytes, c, m, cst + kCQ2);
                     ptx::fence_proxy_async_smem();
                     ptx::mbar_arrive(&B.m2_full[s2]);
                 }
@@ -499,17 +559,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             const int NR = it.rows;
             const bool col_ok = c < kStrip && it.x0 + c < d.rw;
             for (int y = 0; y < NR; ++y) {
-                const uint32_t q = a3_seq + y, s = q % kAccRing;
-                wait_phase(&B.a3_full[s], (q / kAccRing) & 1, abort_flag, p.err);
+                const uint32_t q = a3_seq + y, s = q % C::kAcc;
+                wait_phase(&B.a3_full[s], (q / C::kAcc) & 1, abort_flag, p.err);
                 ptx::tc_fence_after();
                 float v[32];
-                ptx::tmem_ld32(tbase + 256u + ((uint32_t)(32 * pw) << 16) + 32u * s, v);
+                const uint32_t ta = tbase + 256u + ((uint32_t)(32 * pw) << 16) + 32u * s;
+                ptx::tmem_ld32(ta, v);
+                ptx::tmem_st32_zero(ta);
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(&B.a3_free[s]);
                 float z = p.hb;
 #pragma unroll
                 for (int ch = 0; ch < 32; ++ch)
-                    z = fmaf(p.hw[ch], fmaxf(fmaf(v[ch], p.ep3_scale[ch], p.ep3_bias[ch]), 0.f), z);
+                    z = fmaf(cst[kCHW + ch], fmaxf(fmaf(v[ch], cst[kCE3S + ch], cst[kCE3B + ch]), 0.f), z);
                 const float prob = 1.0f / (1.0f + expf(-z));
                 if (col_ok && !*abort_flag) {
                     const int64_t idx = (int64_t)it.zi * d.out_slice + (int64_t)(it.y0 + y) * d.out_pitch + it.x0 + c;
@@ -541,23 +603,27 @@ static uint16_t bf16_bits(float f) {
     return (uint16_t)(u >> 16);
 }
 
-// Pack one 5x5 32->32 layer's weights W[co][ci][dy][dx] (already scaled) as the B operand groups.
-static void pack_layer(const float* W, bool fp8, const float* wscale_inv, uint8_t* out) {
+// Pack one 5x5 32->32 layer's weights W[co][ci][dy][dx] (already scaled) as the B operand groups:
+// group g = (dx, K-half) for BF16 or dx for FP8; in a group, row n = 32 b + co of stored block b
+// holds row tap dy = 4 - (b mod 5); K-major [chunk][n][16 B].
+template <bool FP8>
+static void pack_layer(const float* W, const float* wscale_inv, uint8_t* out) {
+    using C = Cfg<FP8>;
     for (int dx = 0; dx < 5; ++dx)
-        for (int i = 0; i < 5; ++i) {
-            const int dy = 4 - i;
+        for (int b = 0; b < C::kBBlocks; ++b) {
+            const int dy = 4 - (b % 5);
             for (int co = 0; co < 32; ++co) {
-                const int n = i * 32 + co;
+                const int n = b * 32 + co;
                 for (int ci = 0; ci < 32; ++ci) {
                     const float w = W[((co * 32 + ci) * 5 + dy) * 5 + dx];
-                    if (!fp8) {
+                    if (!FP8) {
                         const int g = dx * 2 + ci / 16, kc = (ci % 16) / 8;
-                        uint16_t b = bf16_bits(w);
-                        memcpy(out + g * kGroupBytes + kc * 2560 + n * 16 + (ci % 8) * 2, &b, 2);
+                        uint16_t v = bf16_bits(w);
+                        memcpy(out + g * C::kGroupB + kc * C::kLboB + n * 16 + (ci % 8) * 2, &v, 2);
                     } else {
                         const int g = dx, kc = ci / 16;
                         __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(w * wscale_inv[co], __NV_SATFINITE, __NV_E4M3);
-                        out[g * kGroupBytes + kc * 2560 + n * 16 + (ci % 16)] = q;
+                        out[g * C::kGroupB + kc * C::kLboB + n * 16 + (ci % 16)] = q;
                     }
                 }
             }
@@ -604,25 +670,26 @@ mb_status tc_prepare(mb_net* net) {
     const float* B3 = W3 + 25600;
     const float* HW = B3 + 32;
     TcParams& q = S->base;
+    std::vector<float> cs(kConsts, 0.f);
     for (int co = 0; co < 32; ++co) {
-        for (int k = 0; k < 25; ++k) q.w1[co][k] = W1[co * 25 + k];
-        q.b1[co] = B1[co];
-        q.hw[co] = HW[co];
+        for (int k = 0; k < 25; ++k) cs[kCW1 + k * 32 + co] = W1[co * 25 + k];
+        cs[kCB1 + co] = B1[co];
+        cs[kCHW + co] = HW[co];
     }
     q.hb = HW[32];
-    const size_t layer_bytes = (size_t)(fp8 ? 5 : 10) * kGroupBytes;
+    const size_t layer_bytes = (size_t)(fp8 ? Cfg<true>::kLayerB : Cfg<false>::kLayerB);
     std::vector<uint8_t> pack(2 * layer_bytes, 0);
     if (!fp8) {
         for (int c = 0; c < 32; ++c) {
-            q.ep2_scale[c] = 1.f;
-            q.ep2_bias[c] = B2[c];
-            q.ep3_scale[c] = 1.f;
-            q.ep3_bias[c] = B3[c];
-            q.q1[c] = 1.f;
-            q.q2[c] = 1.f;
+            cs[kCE2S + c] = 1.f;
+            cs[kCE2B + c] = B2[c];
+            cs[kCE3S + c] = 1.f;
+            cs[kCE3B + c] = B3[c];
+            cs[kCQ1 + c] = 1.f;
+            cs[kCQ2 + c] = 1.f;
         }
-        pack_layer(W2, false, nullptr, pack.data());
-        pack_layer(W3, false, nullptr, pack.data() + layer_bytes);
+        pack_layer<false>(W2, nullptr, pack.data());
+        pack_layer<false>(W3, nullptr, pack.data() + layer_bytes);
     } else {
         // activation scale s_a = amax / 448 per input channel, folded into the next layer's
         // weights; then a per-output-channel weight scale s_w = amax|W'| / 448.
@@ -633,7 +700,7 @@ mb_status tc_prepare(mb_net* net) {
             for (int ci = 0; ci < 32; ++ci) {
                 const float a = net->fp8_amax[l][ci];
                 sa[ci] = a > 0.f ? a / 448.f : 1.f;
-                (l == 0 ? q.q1 : q.q2)[ci] = 1.f / sa[ci];
+                cs[(l == 0 ? kCQ1 : kCQ2) + ci] = 1.f / sa[ci];
             }
             std::vector<float> Wp(25600);
             float inv[32];
@@ -647,13 +714,13 @@ mb_status tc_prepare(mb_net* net) {
                     }
                 const float sw = amax > 0.f ? amax / 448.f : 1.f;
                 inv[co] = 1.f / sw;
-                (l == 0 ? q.ep2_scale : q.ep3_scale)[co] = sw;
-                (l == 0 ? q.ep2_bias : q.ep3_bias)[co] = Bs[l][co];
+                cs[(l == 0 ? kCE2S : kCE3S) + co] = sw;
+                cs[(l == 0 ? kCE2B : kCE3B) + co] = Bs[l][co];
             }
-            pack_layer(Wp.data(), true, inv, pack.data() + l * layer_bytes);
+            pack_layer<true>(Wp.data(), inv, pack.data() + l * layer_bytes);
         }
     }
-    if (!S->d_wpack) MB_TRY(dev_alloc((void**)&S->d_wpack, 2 * 10 * kGroupBytes));
+    if (!S->d_wpack) MB_TRY(dev_alloc((void**)&S->d_wpack, kWpackConstOff + kConsts * 4));
     if (!S->h_err) {
         if (fault_oom()) {
             set_error("pinned allocation failed (MB_FAULT_OOM injected)");
@@ -664,6 +731,7 @@ mb_status tc_prepare(mb_net* net) {
         MB_CUDA(cudaHostGetDevicePointer((void**)&S->d_err, S->h_err, 0));
     }
     MB_CUDA(cudaMemcpy(S->d_wpack, pack.data(), pack.size(), cudaMemcpyHostToDevice));
+    MB_CUDA(cudaMemcpy(S->d_wpack + kWpackConstOff, cs.data(), kConsts * 4, cudaMemcpyHostToDevice));
     q.wpack = S->d_wpack;
     q.err = S->d_err;
     return MB_OK;
