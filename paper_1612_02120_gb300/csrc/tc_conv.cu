@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                     a2[2 * j] = make_float2(b.x, b.y);
                     a2[2 * j + 1] = make_float2(b.z, b.w);
                 }
-#pragma unroll
+#pragma unroll 1
                 for (int ky = 0; ky < 5; ++ky) {
                     const float* ir = in_ring + ((in_seq + t + 1 + ky) % kInRing) * kPitch + c;
 #pragma unroll
