@@ -16,187 +16,9 @@
 #include <vector>
 
 #include "internal.h"
+#include "simt_conv.cuh"
 
 namespace mb {
-
-enum { IN_U8 = 0, IN_F32 = 1, IN_F32_MAXF = 2 };
-enum { OUT_ACT = 0, OUT_HEAD_F32 = 1, OUT_HEAD_U8 = 2 };
-
-struct ConvArgs {
-    const void* in;
-    int64_t in_slice;  // u8: bytes per slice; f32: floats per slice
-    int64_t in_pitch;  // u8: bytes per row; f32: pixels per row
-    int in_rows, in_cols;  // extent of the (virtual) input domain this layer reads
-    int src_h, src_w;      // u8: slice size (reflect-101 range)
-    int off_y, off_x;      // u8: input (r, c) reads slice (refl(r + off_y), refl(c + off_x))
-    int out_h, out_w;
-    void* out;
-    int64_t out_slice, out_pitch;  // elements
-    const float* wt;      // [CIN][K][K][COUT]
-    const float* bias;    // [COUT]
-    const float* head_w;  // [COUT] followed by the head bias
-};
-
-__device__ __forceinline__ int refl101(int t, int n) {
-    t = t < 0 ? -t : t;
-    return t >= n ? 2 * (n - 1) - t : t;
-}
-
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ float4 max4(float4 a, float4 b) {
-    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
-}
-
-// One CTA of 256 threads computes a TH x 32 output tile with all COUT channels; each thread holds
-// 4 consecutive pixels x 8 channels in registers. Input channels are staged CC at a time.
-template <int K, int CIN, int COUT, int CC, int IN, int OUT>
-__global__ void __launch_bounds__(256) conv_simt(const ConvArgs a) {
-    constexpr int NCG = COUT / 8;
-    constexpr int TW = 32;
-    constexpr int TH = 256 / (8 * NCG);
-    constexpr int IH = TH + K - 1;
-    constexpr int IW = TW + K - 1;
-    constexpr int IWP = 36;  // reads reach 4*7 + 7 = 35
-    static_assert(IW <= IWP, "tile too wide");
-    static_assert(CIN % CC == 0, "channel chunking");
-    __shared__ __align__(16) float s_in[CC * IH * IWP];
-    __shared__ __align__(16) float s_w[CC * K * K * COUT];
-
-    const int t = threadIdx.x;
-    const int tx = t & 7, cg = (t >> 3) % NCG, ty = (t >> 3) / NCG;
-    const int ox0 = blockIdx.x * TW, oy0 = blockIdx.y * TH;
-    const int zi = blockIdx.z;
-
-    float acc[4][8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        float b = a.bias[cg * 8 + c];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j][c] = b;
-    }
-
-    for (int c0 = 0; c0 < CIN; c0 += CC) {
-        __syncthreads();
-        for (int e = t; e < IH * IWP; e += 256) {
-            const int r = e / IWP, c = e - (e / IWP) * IWP;
-            const int gy = oy0 + r, gx = ox0 + c;
-            const bool ok = c < IW && gy < a.in_rows && gx < a.in_cols;
-            if (IN == IN_U8) {
-                float v = 0.f;
-                if (ok) {
-                    const uint8_t* src = static_cast<const uint8_t*>(a.in) + (int64_t)zi * a.in_slice;
-                    int sy = refl101(gy + a.off_y, a.src_h), sx = refl101(gx + a.off_x, a.src_w);
-                    v = (float)src[(int64_t)sy * a.in_pitch + sx] / 255.0f;
-                }
-                s_in[r * IWP + c] = v;
-            } else {
-                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-                if (ok) {
-                    const float* p = static_cast<const float*>(a.in) + (int64_t)zi * a.in_slice +
-                                     ((int64_t)gy * a.in_pitch + gx) * CIN + c0;
-                    v0 = ldg4(p);
-                    v1 = ldg4(p + 4);
-                    if (IN == IN_F32_MAXF) {
-                        const float* q = p + CIN;
-                        const float* s = p + a.in_pitch * CIN;
-                        const float* u = s + CIN;
-                        v0 = max4(max4(v0, ldg4(q)), max4(ldg4(s), ldg4(u)));
-                        v1 = max4(max4(v1, ldg4(q + 4)), max4(ldg4(s + 4), ldg4(u + 4)));
-                    }
-                }
-                float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-                for (int cc = 0; cc < CC; ++cc) s_in[(cc * IH + r) * IWP + c] = vv[cc];
-            }
-        }
-        {
-            const float4* src = reinterpret_cast<const float4*>(a.wt + (int64_t)c0 * K * K * COUT);
-            float4* dst = reinterpret_cast<float4*>(s_w);
-            for (int e = t; e < CC * K * K * COUT / 4; e += 256) dst[e] = __ldg(src + e);
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int cc = 0; cc < CC; ++cc) {
-#pragma unroll
-            for (int ky = 0; ky < K; ++ky) {
-                const float* row = s_in + (cc * IH + ty + ky) * IWP + 4 * tx;
-                float4 p0 = *reinterpret_cast<const float4*>(row);
-                float4 p1 = *reinterpret_cast<const float4*>(row + 4);
-                float v[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-                const float* wr = s_w + ((cc * K + ky) * K) * COUT + 8 * cg;
-#pragma unroll
-                for (int kx = 0; kx < K; ++kx) {
-                    float4 w0 = *reinterpret_cast<const float4*>(wr + kx * COUT);
-                    float4 w1 = *reinterpret_cast<const float4*>(wr + kx * COUT + 4);
-                    float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) acc[j][c] = fmaf(v[j + kx], wv[c], acc[j][c]);
-                }
-            }
-        }
-    }
-
-    const int oy = oy0 + ty;
-    if (OUT == OUT_ACT) {
-        if (oy < a.out_h) {
-            float* o = static_cast<float*>(a.out) + (int64_t)zi * a.out_slice;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int ox = ox0 + 4 * tx + j;
-                if (ox < a.out_w) {
-                    float* d = o + ((int64_t)oy * a.out_pitch + ox) * COUT + 8 * cg;
-                    *reinterpret_cast<float4*>(d) = make_float4(fmaxf(acc[j][0], 0.f), fmaxf(acc[j][1], 0.f),
-                                                                fmaxf(acc[j][2], 0.f), fmaxf(acc[j][3], 0.f));
-                    *reinterpret_cast<float4*>(d + 4) = make_float4(fmaxf(acc[j][4], 0.f), fmaxf(acc[j][5], 0.f),
-                                                                    fmaxf(acc[j][6], 0.f), fmaxf(acc[j][7], 0.f));
-                }
-            }
-        }
-    } else {
-        float hw[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) hw[c] = a.head_w[cg * 8 + c];
-        const float hb = a.head_w[COUT];
-        float s[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float v = 0.f;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) v = fmaf(fmaxf(acc[j][c], 0.f), hw[c], v);
-#pragma unroll
-            for (int m = 8; m < 8 * NCG; m <<= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-            s[j] = v;
-        }
-        if (cg == 0 && oy < a.out_h) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int ox = ox0 + 4 * tx + j;
-                if (ox < a.out_w) {
-                    float p = 1.0f / (1.0f + expf(-(s[j] + hb)));
-                    int64_t idx = (int64_t)zi * a.out_slice + (int64_t)oy * a.out_pitch + ox;
-                    if (OUT == OUT_HEAD_F32) {
-                        static_cast<float*>(a.out)[idx] = p;
-                    } else {
-                        float q = floorf(255.0f * p + 0.5f);
-                        static_cast<uint8_t*>(a.out)[idx] = (uint8_t)fminf(q, 255.0f);
-                    }
-                }
-            }
-        }
-    }
-}
-
-template <int K, int CIN, int COUT, int CC, int IN, int OUT>
-static mb_status launch_conv(const ConvArgs& a, int nz, cudaStream_t st) {
-    constexpr int TH = 256 / COUT;
-    dim3 grid((a.out_w + 31) / 32, (a.out_h + TH - 1) / TH, nz);
-    conv_simt<K, CIN, COUT, CC, IN, OUT><<<grid, 256, 0, st>>>(a);
-    count_launch();
-    MB_CUDA(cudaGetLastError());
-    return MB_OK;
-}
 
 // Per-channel max of a 2x2 max-filtered activation map (all values >= 0 after ReLU, so the
 // float bit patterns order like unsigned integers and atomicMax is exact and deterministic).

@@ -925,7 +925,181 @@ mb_status tc_infer_blocks(mb_net* net, const mb_block* blocks, int n_blocks, con
 
 }  // namespace mb
 
-extern "C" mb_status mb_autotune(mb_net*, int64_t, int64_t, int64_t, const char*, int32_t*, void*) {
-    mb::set_error("autotuner not built yet");
-    return MB_ERR_UNSUPPORTED;
+namespace mb {
+
+__global__ void fill_bytes(uint8_t* p, int64_t n, uint32_t seed) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)i * 2654435761u ^ seed;
+        x ^= x >> 15;
+        x *= 2246822519u;
+        x ^= x >> 13;
+        p[i] = (uint8_t)(x >> 24);
+    }
+}
+
+static std::string tune_key(int dev, mb_precision prec, int64_t z, int64_t h, int64_t w) {
+    cudaDeviceProp pr;
+    char buf[512];
+    const char* name = cudaGetDeviceProperties(&pr, dev) == cudaSuccess ? pr.name : "unknown";
+    snprintf(buf, sizeof(buf), "%s|%s|%lldx%lldx%lld", name, prec == MB_PREC_FP8 ? "fp8" : "bf16", (long long)z,
+             (long long)h, (long long)w);
+    for (char* c = buf; *c; ++c)
+        if (*c == '"' || *c == '\\') *c = '_';
+    return buf;
+}
+
+// Cache file: one JSON object per line, {"key": "...", "rows_per_item": R, "stages": S, "ms": T}.
+static bool cache_lookup(const char* path, const std::string& key, int* rows, int* stages) {
+    FILE* f = path ? fopen(path, "r") : nullptr;
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string pat = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof(line), f)) {
+        if (!strstr(line, pat.c_str())) continue;
+        const char* r = strstr(line, "\"rows_per_item\": ");
+        const char* s = strstr(line, "\"stages\": ");
+        if (r && s) {
+            *rows = atoi(r + 17);
+            *stages = atoi(s + 10);
+            found = *rows > 0 && *stages > 0;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void cache_store(const char* path, const std::string& key, int rows, int stages, float ms) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"rows_per_item\": %d, \"stages\": %d, \"ms\": %.4f}\n", key.c_str(), rows, stages,
+            ms);
+    fclose(f);
+}
+
+mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path, int32_t* choice,
+                      cudaStream_t st) {
+    int dev = 0;
+    MB_CUDA(cudaGetDevice(&dev));
+    const std::string key = tune_key(dev, net->prec, z, h, w);
+    int rows = 0, stages = 0;
+    if (cache_lookup(cache_path, key, &rows, &stages)) {
+        net->rows_per_item = rows;
+        net->stages = stages;
+        net->tuned = true;
+        if (choice) {
+            choice[0] = rows;
+            choice[1] = stages;
+            choice[2] = 1;
+        }
+        return MB_OK;
+    }
+    uint8_t* in = nullptr;
+    float* out = nullptr;
+    MB_TRY(dev_alloc((void**)&in, (size_t)(z * h * w)));
+    mb_status rc = dev_alloc((void**)&out, (size_t)(z * h * w) * 4);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == MB_OK) {
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__);
+    }
+    const int saved_rows = net->rows_per_item, saved_stages = net->stages;
+    int best_r = saved_rows, best_s = saved_stages;
+    float best = 1e30f;
+    if (rc == MB_OK) {
+        fill_bytes<<<1024, 256, 0, st>>>(in, z * h * w, 12345u);
+        count_launch();
+        const int cand_rows[] = {32, 64, 128, 256, 1024};
+        const int cand_stages[] = {1, 2, 3};
+        mb_block b;
+        b.in = in;
+        b.z = z;
+        b.h = h;
+        b.w = w;
+        b.in_pitch = w;
+        b.in_slice_pitch = h * w;
+        b.out = out;
+        b.out_pitch = w;
+        b.out_slice_pitch = h * w;
+        const int64_t y0 = 0, x0 = 0;
+        for (int R : cand_rows) {
+            if (R > 2 * h && R != cand_rows[0]) continue;
+            for (int S : cand_stages) {
+                net->rows_per_item = R;
+                net->stages = S;
+                float ms_sum = 0.f;
+                for (int rep = 0; rep < 3 && rc == MB_OK; ++rep) {
+                    cudaError_t e = cudaEventRecord(e0, st);
+                    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__); break; }
+                    rc = tc_infer_blocks(net, &b, 1, &y0, &x0, &h, &w, MB_OUT_F32, st, false);
+                    if (rc != MB_OK) break;
+                    e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing", __FILE__, __LINE__); break; }
+                    if (rep > 0) ms_sum += ms;  // first repetition warms up
+                }
+                if (rc != MB_OK) break;
+                if (ms_sum / 2 < best) {
+                    best = ms_sum / 2;
+                    best_r = R;
+                    best_s = S;
+                }
+            }
+            if (rc != MB_OK) break;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(in);
+    dev_free(out);
+    if (rc == MB_OK) rc = check_err(net);
+    if (rc != MB_OK) {
+        net->rows_per_item = saved_rows;
+        net->stages = saved_stages;
+        return rc;
+    }
+    net->rows_per_item = best_r;
+    net->stages = best_s;
+    net->tuned = true;
+    drop_graphs(net);
+    cache_store(cache_path, key, best_r, best_s, best);
+    if (choice) {
+        choice[0] = best_r;
+        choice[1] = best_s;
+        choice[2] = 0;
+    }
+    return MB_OK;
+}
+
+}  // namespace mb
+
+extern "C" mb_status mb_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path,
+                                 int32_t* choice_out, void* stream) {
+    mb::clear_error();
+    if (!net) {
+        mb::set_error("mb_autotune: net is NULL");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (!net->loaded || (net->prec == MB_PREC_FP8 && !net->calibrated)) {
+        mb::set_error("mb_autotune: net not ready (weights / FP8 calibration)");
+        return MB_ERR_NOT_READY;
+    }
+    if (net->family != mb::FAMILY_TEACHER || net->prec == MB_PREC_FP32) {
+        mb::set_error("mb_autotune: only the tensor-core teacher (BF16/FP8) has tunables");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (z <= 0 || h < 8 || w < 8 || z * h * w > ((int64_t)1 << 32)) {
+        mb::set_error("mb_autotune: workload %lldx%lldx%lld out of range", (long long)z, (long long)h, (long long)w);
+        return MB_ERR_SHAPE;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != net->device) cudaSetDevice(net->device);
+    mb_status s = mb::tc_autotune(net, z, h, w, cache_path, choice_out, (cudaStream_t)stream);
+    if (prev != net->device) cudaSetDevice(prev);
+    return s;
 }
