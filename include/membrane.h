@@ -199,6 +199,24 @@ mb_status mb_infer_cascade(mb_net* student, mb_net* teacher, const uint8_t* in, 
                            int64_t w, float* out, int32_t tile, float lo, float hi, float max_frac,
                            double* fallback_rate, uint8_t* tile_flags, void* stream);
 
+/*
+ * mb_infer_volume without any device allocation (the paper has no counterpart: it is a service
+ * for callers of this library). For callers that must not allocate device memory once running:
+ * a service whose memory budget is fixed at start-up, or a pipeline that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause while other streams are busy.
+ * FP32 teacher nets only; device pointers in[z][h][w] -> out[z][h][w] (float32 or uint8 as in
+ * mb_infer_volume); asynchronous on `stream`.
+ * Scratch: a fixed 64 MiB array in the library's device memory, held by every GPU that loads the
+ * library until exit. Slices are processed in row bands that fit it; a width needing more than
+ * 64 MiB for a single-row band (w > 30,832) returns MB_ERR_SHAPE. The first call on each
+ * device looks up the array's device address; make that first call before any stream capture.
+ * All calls on a device share the array: calls that overlap on the GPU (other streams or host
+ * threads) race and must be serialised by the caller. Nothing in the array needs clearing.
+ * This call makes no cudaMalloc/cudaFree and calls no allocating library routine.
+ */
+mb_status mb_infer_volume_noalloc(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,
+                                  mb_out_type out_type, void* stream);
+
 /* Static string for a status code. */
 const char* mb_status_string(mb_status s);
 
