@@ -1,12 +1,21 @@
 """Throughput of dense membrane-probability inference (Sec. 2.1-2.2) on one GB300.
 
-One step = one pass of the inference path over the 1024x1024x32 uint8 synthetic EM volume
-(32 independent slices, the generator's 120 cells per 256^2): every pixel's probability map.
-`value` is output megavoxels per second with the volume resident in HBM; `e2e` is the same
-metric through the C ABI with pinned HOST buffers (host<->device copies inside the timed region).
-L2 is flushed (a 256 MB write) between timed steps. The reference arm is the FP64 CPU oracle.
+Headline step: one pass of the BF16 tensor-core path over the 1024x1024x32 uint8 synthetic EM
+volume (32 independent slices; 120 Voronoi cells per 256^2, membranes 2-3 px, blur sigma 1), every
+pixel's probability map. `value` = output megavoxels/s with the volume resident in HBM; `e2e` =
+the same through the C ABI with pinned HOST buffers (copies inside the timed region). L2 is flushed
+(256 MB write) between timed steps. The same run measures, under "paths":
+  cfg1  FP32 / BF16 / FP8 on the same volume, each with max-abs, mean-abs, agreement at 0.5 and
+        near-threshold mass against the FP64 oracle on 2 seeded slices;
+  cfg2  64 uneven blocks (sides U[256,1536], depth U[1,16]) BF16: one persistent launch under a
+        captured CUDA graph (autotuned) vs one launch per block;
+  cfg3  4096x4096x64 FP8 (calibrated on 4 slices) and BF16, resident and streamed from pinned host
+        memory; errors on 3 seeded 512x512 crops (true context);
+  cfg4  student training (200 x 512^2, batch 32, lr 1e-3, 2000 steps) on FP32-teacher maps, then
+        student-only and cascade (teacher fallback on 256^2 tiles) on the cfg3 volume.
+The reference arm (--impl reference) is the FP64 CPU oracle on bounded samples.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32|fp8] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--configs 1,2,3,4]
 """
 from __future__ import annotations
 
@@ -17,7 +26,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -25,33 +33,35 @@ sys.path.insert(0, ROOT)
 
 METRIC = "membrane-prob megavoxels/s on 1 GB300: FP32 vs BF16/FP8 vs student, at stated error"
 Z, H, W = 32, 1024, 1024
-WORKLOAD = "1024x1024x32 uint8 synthetic EM volume (32 independent slices), stand-in teacher CNN"
+WORKLOAD = "1024x1024x32 uint8 synthetic EM volume (32 independent slices), stand-in teacher CNN, BF16"
 FLOP_PER_PX = 2 * (25 * 32 + 2 * 25 * 32 * 32 + 32)        # 104,064
 TENSOR_FLOP_PER_PX = 2 * 2 * 25 * 32 * 32                   # 102,400 (layers 2 and 3)
-BYTES_PER_PX = {0: 5, 1: 2}                                 # 1 B in + 4 B (float) or 1 B (u8) out
+STUDENT_FLOP_PER_PX = 2 * (9 * 16 + 9 * 16 * 16 + 16)       # 4,928
+# DRAM bytes per output voxel of tc_fused_teacher (BF16), from the ncu capture summarised in
+# profiles/tc_fused_teacher_bf16_1024x1024x4.md; None when the kernel changed since.
+TC_TRAFFIC_PER_VOX = None
+TOL = {"fp32": {"max_abs": 1e-5}, "bf16": {"max_abs": 3e-2, "mean_abs": 2e-3},
+       "fp8": {"max_abs": 1e-1, "mean_abs": 1e-2}, "student": {"mean_abs": 3e-2}}
 
 
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            p = json.load(f)
-        return p, "measured"
+            return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples every 200 ms during a timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.path = None
+        self.gpu, self.proc, self.path = gpu_index, None, None
 
     def __enter__(self):
         try:
@@ -77,48 +87,52 @@ class ClockSampler:
     def summary(self):
         if not self.proc or not self.path:
             return None
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = [[p.strip() for p in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(params, vol, budget_s=20.0):
-    """The FP64 oracle as it stands, on a bounded sample: 256x256 crops (true context) of
-    successive slices until about budget_s of CPU time."""
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(params, vol, budget_s=15.0):
+    """The FP64 oracle as it stands on a bounded sample: 256x256 crops (true context) of successive
+    slices until about budget_s."""
     import oracle
     import synth
     t0 = time.perf_counter()
     n = 0
     while True:
-        zi = n % vol.shape[0]
-        oracle.forward_region(synth.TEACHER, params, vol[zi], 384, 384, 256, 256)
+        oracle.forward_region(synth.TEACHER, params, vol[n % vol.shape[0]], 384, 384, 256, 256)
         n += 1
         if time.perf_counter() - t0 > budget_s or n >= 64:
             break
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": n * 256 * 256 / dt / 1e6, "unit": "Mvox/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} crops of 256x256 (7-px true context) from slices of the 1024x1024x32 volume, "
-                      f"FP64 direct loops, {dt:.1f} s"}
+    return {"value": n * 256 * 256 / dt / 1e6, "unit": "Mvox/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{n} crops of 256x256 (7-px true context) of the 1024x1024x32 volume's slices, FP64 "
+                      f"direct loops, {dt:.1f} s"}
 
 
 def run_reference(args):
-    import numpy as np  # noqa: F401
+    import oracle
     import synth
     params = synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED)
     vol = synth.em_volume(synth.BASE_SEED + 1, 4, H, W)
-    import oracle
     crop = 256
 
     def step(i):
@@ -131,15 +145,42 @@ def run_reference(args):
         step(i)
     dt = time.perf_counter() - t0
     value = args.steps * crop * crop / dt / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mvox/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64-oracle"},
-            "cpu_baseline": {"value": value, "unit": "Mvox/s", "cores": cores, "kind": "oracle",
-                             "sample": f"one 256x256 crop (true context) per step, FP64 direct loops"},
-            "e2e": {"value": value, "unit": "Mvox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mvox/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64-oracle"},
+        "cpu_baseline": {"value": value, "unit": "Mvox/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "one 256x256 crop (true context) of a 1024x1024 slice per step, FP64"},
+        "e2e": {"value": value, "unit": "Mvox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def time_device(fn, steps, warmup, stream, flush):
+    """Per-step CUDA-event times (ms) of fn() on `stream`, L2 flushed between steps."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def err_metrics(maps, refs, tol):
+    import numpy as np
+    import oracle
+    a = np.concatenate([np.asarray(m, dtype=np.float64).ravel() for m in maps])
+    r = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in refs])
+    met = oracle.metrics(a, r)
+    met["within_tolerance"] = all((met[k] <= v) for k, v in tol.items()) and met["agreement"] >= 0.995
+    return met
 
 
 def main():
@@ -148,16 +189,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--configs", default="1,2,3,4", help="extra configurations measured after the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extra", action="store_true", help="also time the other precision paths")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
@@ -166,55 +204,43 @@ def main():
     import numpy as np
     import torch
 
+    import oracle
     import synth
     from paper_1612_02120_gb300 import build as pbuild
     from paper_1612_02120_gb300 import membrane as m
 
-    if rank == 0:
-        pbuild.build()
+    pbuild.build()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        if rank != 0:
-            pbuild.build()
-
-    prec = {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16, "fp8": m.MB_PREC_FP8}[args.prec]
-    params = synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED)
-    vol = synth.em_volume(synth.BASE_SEED + 1, Z, H, W)
-    x = torch.from_numpy(vol).cuda()
-    out = torch.empty((Z, H, W), dtype=torch.float32, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.Stream()
-
-    net = m.Net(synth.TEACHER, prec, local, params)
-    if prec == m.MB_PREC_FP8:
-        m.mb_calibrate_fp8(net.handle, x[:4], 4, H, W, stream=stream)
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
+    params = synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED)
+    vol = synth.em_volume(synth.BASE_SEED + 1, Z, H, W)
+    x = torch.from_numpy(vol).cuda()
+    out = torch.empty((Z, H, W), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    vox = Z * H * W
+
+    # ---- headline: BF16 fused tensor-core kernel on cfg1 ------------------------------------------
+    net = m.Net(synth.TEACHER, m.MB_PREC_BF16, local, params)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        def step():
             m.mb_infer_volume(net.handle, x, Z, H, W, out, m.MB_OUT_F32, stream)
+        for _ in range(args.warmup):
+            step()
         barrier()
         launches0 = m.launch_count()
-        times = []
         with ClockSampler(local) as clk:
-            for _ in range(args.steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                m.mb_infer_volume(net.handle, x, Z, H, W, out, m.MB_OUT_F32, stream)
-                e1.record(stream)
-                times.append((e0, e1))
-            torch.cuda.synchronize()
+            step_ms = time_device(step, args.steps, 0, stream, flush)
         launches = m.launch_count() - launches0
-        step_ms = [a.elapsed_time(b) for a, b in times]
     total_ms = sum(step_ms)
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda")
@@ -222,12 +248,12 @@ def main():
         total_ms = float(t.item())
         barrier()
     ms_per_step = total_ms / args.steps
-    vox = Z * H * W
     value = world * vox / (ms_per_step / 1e3) / 1e6
+    bf16_map = out.cpu().numpy()
 
     # end to end through the C ABI with pinned host buffers
     pin_in = torch.from_numpy(vol).pin_memory()
-    pin_out = torch.empty((Z, H, W), dtype=torch.float32).pin_memory()
+    pin_out = torch.empty((Z, H, W), dtype=torch.float32, pin_memory=True)
     m.mb_infer_volume(net.handle, pin_in, Z, H, W, pin_out)
     barrier()
     t0 = time.perf_counter()
@@ -238,31 +264,183 @@ def main():
 
     pk, pk_kind = peaks()
     kernel_ms = statistics.mean(step_ms)
-    if prec == m.MB_PREC_FP32:
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        achieved = FLOP_PER_PX * vox / (kernel_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "conv_simt (3 launches per step, all layers)",
-                "peak_kind": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
-    else:
-        peak = pk["bf16_tflops_sustained"] if prec == m.MB_PREC_BF16 else 2 * pk["bf16_tflops_sustained"]
-        achieved = TENSOR_FLOP_PER_PX * vox / (kernel_ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tc_fused_teacher (1 launch per step)",
-                "peak_kind": f"{pk_kind} bf16 sustained" + (" x 2 (nominal fp8/bf16 ratio)" if prec == m.MB_PREC_FP8 else "")}
+    achieved = TENSOR_FLOP_PER_PX * vox / (kernel_ms / 1e3) / 1e12
+    peak = pk["bf16_tflops_sustained"]
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": (TC_TRAFFIC_PER_VOX * vox if TC_TRAFFIC_PER_VOX else None),
+            "kernel": "tc_fused_teacher<bf16> (1 launch per step)",
+            "algorithmic": f"{TENSOR_FLOP_PER_PX} tensor FLOP/px x {vox} px per launch; "
+                           f"{FLOP_PER_PX} FLOP/px in all; 5 B/px of DRAM",
+            "peak_kind": f"{pk_kind} bf16 dense, sustained",
+            "hbm_frac": 5 * vox / (kernel_ms / 1e3) / 1e9 / pk["hbm_gbs"]}
 
     line = {"metric": METRIC, "value": value, "unit": "Mvox/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[args.prec],
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.prec, "out": "float32",
-                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas{world}"},
-            "gb_per_hour": value * 1e6 * 3600 / 1e9,
-            "roofline": roof,
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "bf16 (layers 2-3), fp32 (layer 1, head)",
+                       "out": "float32", "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas{world}"},
+            "gb_per_hour": value * 1e6 * 3600 / 1e9, "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "Mvox/s", "h2d_bytes_per_step": vox, "d2h_bytes_per_step": 4 * vox},
-            "gpu_launches": launches,
-            "clocks": clk.summary()}
+            "gpu_launches": launches, "clocks": clk.summary()}
+    configs = {c.strip() for c in args.configs.split(",") if c.strip()} if world == 1 else set()
+    paths = {}
+
+    # ---- cfg1: FP32 / BF16 / FP8 on the same volume + errors on 2 seeded slices --------------------
+    if "1" in configs:
+        zs = [int(z) for z in np.random.default_rng(synth.BASE_SEED + 1).choice(Z, 2, replace=False)]
+        refs = [oracle.forward_region(synth.TEACHER, params, vol[z]) for z in zs]
+        p = {"bf16": {"mvox_s": value, "ms": ms_per_step,
+                      "error": err_metrics([bf16_map[z] for z in zs], refs, TOL["bf16"])}}
+        fp32 = m.Net(synth.TEACHER, m.MB_PREC_FP32, local, params)
+        with torch.cuda.stream(stream):
+            ms = time_device(lambda: m.mb_infer_volume(fp32.handle, x, Z, H, W, out, m.MB_OUT_F32, stream),
+                             3, 1, stream, flush)
+        p["fp32"] = {"mvox_s": vox / (statistics.mean(ms) / 1e3) / 1e6, "ms": statistics.mean(ms),
+                     "error": err_metrics([out[z].cpu().numpy() for z in zs], refs, TOL["fp32"])}
+        fp32.close()
+        fp8 = m.Net(synth.TEACHER, m.MB_PREC_FP8, local, params)
+        m.mb_calibrate_fp8(fp8.handle, x[:4], 4, H, W, stream=stream)
+        with torch.cuda.stream(stream):
+            ms = time_device(lambda: m.mb_infer_volume(fp8.handle, x, Z, H, W, out, m.MB_OUT_F32, stream),
+                             args.steps, 3, stream, flush)
+        p["fp8"] = {"mvox_s": vox / (statistics.mean(ms) / 1e3) / 1e6, "ms": statistics.mean(ms),
+                    "error": err_metrics([out[z].cpu().numpy() for z in zs], refs, TOL["fp8"])}
+        fp8.close()
+        for k in ("bf16", "fp8"):
+            p[k]["speedup_vs_fp32"] = p[k]["mvox_s"] / p["fp32"]["mvox_s"]
+        p["sampled_slices"] = zs
+        paths["cfg1_1024x1024x32"] = p
+
+    # ---- cfg2: 64 uneven blocks, persistent launch + graph vs per-block launches --------------------
+    if "2" in configs:
+        shapes = synth.block_shapes(synth.BASE_SEED + 2, 64)
+        ins, outs, blocks = [], [], []
+        for i, (d, h, w) in enumerate(shapes):
+            v = torch.from_numpy(synth.em_volume(synth.BASE_SEED + 2, d, h, w, block=i)).cuda()
+            o = torch.empty((d, h, w), dtype=torch.float32, device="cuda")
+            ins.append(v)
+            outs.append(o)
+            blocks.append((v, d, h, w, w, h * w, o, w, h * w))
+        bvox = sum(d * h * w for d, h, w in shapes)
+        tune = m.mb_autotune(net.handle, 4, 896, 896, os.path.join(tempfile.gettempdir(), "membrane_tune.json"),
+                             stream)
+        with torch.cuda.stream(stream):
+            ms_b = time_device(lambda: m.mb_infer_batch(net.handle, blocks, m.MB_OUT_F32, stream), args.steps, 3,
+                               stream, flush)
+            l0 = m.launch_count()
+            m.mb_infer_batch(net.handle, blocks, m.MB_OUT_F32, stream)
+            lb = m.launch_count() - l0
+            ms_p = time_device(lambda: m.mb_infer_batch_per_block(net.handle, blocks, m.MB_OUT_F32, stream),
+                               args.steps, 3, stream, flush)
+        paths["cfg2_64_uneven_blocks"] = {
+            "voxels": bvox, "persistent_graph_mvox_s": bvox / (statistics.mean(ms_b) / 1e3) / 1e6,
+            "per_block_mvox_s": bvox / (statistics.mean(ms_p) / 1e3) / 1e6,
+            "speedup": statistics.mean(ms_p) / statistics.mean(ms_b), "launches_per_batch": lb,
+            "autotune": tune}
+
+    # ---- cfg3: 4096x4096x64, FP8 and BF16, resident and streamed --------------------------------
+    big = None
+    if "3" in configs or "4" in configs:
+        Z3, H3, W3 = 64, 4096, 4096
+        big = torch.empty((Z3, H3, W3), dtype=torch.uint8, pin_memory=True)
+        synth.em_volume(synth.BASE_SEED + 3, Z3, H3, W3, out=big.numpy())
+        xb = big.cuda()
+        ob = torch.empty((Z3, H3, W3), dtype=torch.float32, device="cuda")
+        v3 = Z3 * H3 * W3
+        rng = np.random.default_rng(synth.BASE_SEED + 3)
+        crops = [(int(rng.integers(Z3)), int(rng.integers(H3 - 512)), int(rng.integers(W3 - 512))) for _ in range(3)]
+        crop_refs = [oracle.forward_region(synth.TEACHER, params, big[z].numpy(), y, x0, 512, 512)
+                     for z, y, x0 in crops]
+    if "3" in configs:
+        p = {}
+        for name, prec in (("fp8", m.MB_PREC_FP8), ("bf16", m.MB_PREC_BF16)):
+            n3 = m.Net(synth.TEACHER, prec, local, params)
+            if prec == m.MB_PREC_FP8:
+                m.mb_calibrate_fp8(n3.handle, xb[:4], 4, H3, W3, stream=stream)
+            with torch.cuda.stream(stream):
+                ms = time_device(lambda: m.mb_infer_volume(n3.handle, xb, Z3, H3, W3, ob, m.MB_OUT_F32, stream),
+                                 3, 1, stream, flush)
+            err = err_metrics([ob[z, y:y + 512, x0:x0 + 512].cpu().numpy() for z, y, x0 in crops], crop_refs,
+                              TOL[name])
+            entry = {"mvox_s": v3 / (statistics.mean(ms) / 1e3) / 1e6, "ms": statistics.mean(ms), "error": err}
+            if prec == m.MB_PREC_FP8:
+                pin_o = torch.empty((Z3, H3, W3), dtype=torch.float32, pin_memory=True)
+                t0 = time.perf_counter()
+                m.mb_infer_volume(n3.handle, big, Z3, H3, W3, pin_o)
+                entry["streamed_mvox_s"] = v3 / (time.perf_counter() - t0) / 1e6
+                del pin_o
+            p[name] = entry
+            n3.close()
+        p["fp8"]["speedup_vs_bf16"] = p["fp8"]["mvox_s"] / p["bf16"]["mvox_s"]
+        p["crops"] = crops
+        paths["cfg3_4096x4096x64"] = p
+
+    # ---- cfg4: student training, student-only and cascade inference ------------------------------
+    if "4" in configs:
+        n_tr, s_tr = 200, 512
+        tv = torch.from_numpy(synth.em_volume(synth.BASE_SEED + 4, n_tr, s_tr, s_tr)).cuda()
+        tgt = torch.empty((n_tr, s_tr, s_tr), dtype=torch.float32, device="cuda")
+        teacher32 = m.Net(synth.TEACHER, m.MB_PREC_FP32, local, params)
+        m.mb_infer_volume(teacher32.handle, tv, n_tr, s_tr, s_tr, tgt)
+        teacher32.close()
+        sp = synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0)
+        student = m.Net(synth.STUDENT, m.MB_PREC_BF16, local, sp)
+        untrained = m.Net(synth.STUDENT, m.MB_PREC_BF16, local, sp)
+        cfg = m.train_cfg(batch=32, steps=2000, lr=1e-3, seed=synth.BASE_SEED + 4)
+        curve = np.zeros(2000, dtype=np.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.mb_student_train(student.handle, tv, tgt, n_tr, s_tr, s_tr, cfg, None, curve)
+        train_s = time.perf_counter() - t0
+        del tv, tgt
+        Z3, H3, W3 = 64, 4096, 4096
+        v3 = Z3 * H3 * W3
+        with torch.cuda.stream(stream):
+            ms_s = time_device(lambda: m.mb_infer_volume(student.handle, xb, Z3, H3, W3, ob, m.MB_OUT_F32, stream),
+                               3, 1, stream, flush)
+        s_map = [ob[z, y:y + 512, x0:x0 + 512].cpu().numpy() for z, y, x0 in crops]
+        m.mb_infer_volume(untrained.handle, xb, Z3, H3, W3, ob, m.MB_OUT_F32, stream)
+        torch.cuda.synchronize()
+        u_map = [ob[z, y:y + 512, x0:x0 + 512].cpu().numpy() for z, y, x0 in crops]
+        teacher = m.Net(synth.TEACHER, m.MB_PREC_BF16, local, params)
+        m.mb_infer_volume(teacher.handle, xb, Z3, H3, W3, ob, m.MB_OUT_F32, stream)
+        torch.cuda.synchronize()
+        t_map = [ob[z, y:y + 512, x0:x0 + 512].cpu().numpy() for z, y, x0 in crops]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rate = m.mb_infer_cascade(student.handle, teacher.handle, xb, Z3, H3, W3, ob, 256, 0.3, 0.7, 0.05,
+                                  stream=stream)
+        casc_s = time.perf_counter() - t0
+        c_map = [ob[z, y:y + 512, x0:x0 + 512].cpu().numpy() for z, y, x0 in crops]
+        # a second reading of "ambiguous": a band around the 0.5 decision threshold
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rate_d = m.mb_infer_cascade(student.handle, teacher.handle, xb, Z3, H3, W3, ob, 256, 0.48, 0.52, 0.05,
+                                    stream=stream)
+        casc_d_s = time.perf_counter() - t0
+        d_map = [ob[z, y:y + 512, x0:x0 + 512].cpu().numpy() for z, y, x0 in crops]
+        paths["cfg4_student"] = {
+            "train": {"steps": 2000, "batch": 32, "slices": n_tr, "seconds": train_s, "steps_per_s": 2000 / train_s,
+                      "loss_first10": float(curve[:10].mean()), "loss_last10": float(curve[-10:].mean())},
+            "student_only_mvox_s": v3 / (statistics.mean(ms_s) / 1e3) / 1e6,
+            "student_tflops": STUDENT_FLOP_PER_PX * v3 / (statistics.mean(ms_s) / 1e3) / 1e12,
+            "student_vs_teacher": err_metrics(s_map, t_map, TOL["student"]),
+            "student_vs_oracle": err_metrics(s_map, crop_refs, TOL["student"]),
+            "untrained_vs_teacher": err_metrics(u_map, t_map, TOL["student"]),
+            "cascade": {"band": [0.3, 0.7], "tile": 256, "max_frac": 0.05, "fallback_rate": rate,
+                        "mvox_s": v3 / casc_s / 1e6,
+                        "vs_teacher": err_metrics(c_map, t_map, TOL["student"]),
+                        "vs_oracle": err_metrics(c_map, crop_refs, TOL["student"])},
+            "cascade_decision_band": {"band": [0.48, 0.52], "tile": 256, "max_frac": 0.05, "fallback_rate": rate_d,
+                                      "mvox_s": v3 / casc_d_s / 1e6,
+                                      "vs_teacher": err_metrics(d_map, t_map, TOL["student"]),
+                                      "vs_oracle": err_metrics(d_map, crop_refs, TOL["student"])}}
+        student.close()
+        untrained.close()
+        teacher.close()
+    if paths:
+        line["paths"] = paths
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(params, vol)
     net.close()
