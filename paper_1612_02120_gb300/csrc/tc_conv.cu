@@ -68,6 +68,8 @@ struct TcParams {
     const uint8_t* wpack;   // global: packed B operands of layers 2 and 3, then the constants
     int* err;               // error word (MB_ERR_TIMEOUT on a timed-out wait)
     int n_blocks, n_items, rows_per_item, lag, out_u8;
+    int fault_stall;        // test injection: the input loader withholds its arrivals
+    uint64_t wait_ns;       // limit of every device-side wait
     TcBlockDesc blk[kMaxBlocks];
 };
 
@@ -122,7 +124,7 @@ __device__ __forceinline__ uint64_t gtime() {
 // Bounded wait. Returns false (and raises the CTA-wide abort flag) when the phase did not
 // complete within kWaitNs, or immediately once the CTA is aborting.
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                           int* err) {
+                                           int* err, uint64_t limit_ns = kWaitNs) {
     if (*abort_flag) return false;
     if (ptx::mbar_test(bar, parity)) return true;
     const uint64_t t0 = gtime();
@@ -130,7 +132,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
     while (!ptx::mbar_test(bar, parity)) {
         if ((++n & 255u) == 0) {
             if (*abort_flag) return false;
-            if (gtime() - t0 > kWaitNs) {
+            if (gtime() - t0 > limit_ns) {
                 *abort_flag = 1;
                 *(volatile int*)err = MB_ERR_TIMEOUT;
                 return false;
@@ -354,11 +356,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                 for (int r = 0; r < M1 + p.lag; ++r) {
                     if (r < M1) {
                         const uint32_t q = m1_seq + r, s = q % kRing;
-                        ok = ok && wait_phase(&B.m1_full[s], (q / kRing) & 1, abort_flag, p.err);
+                        ok = ok && wait_phase(&B.m1_full[s], (q / kRing) & 1, abort_flag, p.err, p.wait_ns);
                         if (r < N2) {
                             const uint32_t qa = a2_seq + r;
                             ok = ok && wait_phase(&B.a2_free[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag,
-                                                  p.err);
+                                                  p.err, p.wait_ns);
                         }
                         ptx::tc_fence_after();
                         if (ok) issue_row<FP8>(tbase, a2_seq, r, N2, ad1 + (uint64_t)(s * (C::kSlotBytes >> 4)), bd2);
@@ -368,11 +370,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                     const int sr = r - 5 - p.lag;
                     if (sr >= 0 && sr < M2) {
                         const uint32_t q = m2_seq + sr, s = q % kRing;
-                        ok = ok && wait_phase(&B.m2_full[s], (q / kRing) & 1, abort_flag, p.err);
+                        ok = ok && wait_phase(&B.m2_full[s], (q / kRing) & 1, abort_flag, p.err, p.wait_ns);
                         if (sr < NR) {
                             const uint32_t qa = a3_seq + sr;
                             ok = ok && wait_phase(&B.a3_free[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag,
-                                                  p.err);
+                                                  p.err, p.wait_ns);
                         }
                         ptx::tc_fence_after();
                         if (ok) issue_row<FP8>(tbase + 256, a3_seq, sr, NR, ad2 + (uint64_t)(s * (C::kSlotBytes >> 4)), bd3);
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             ptx::mma_commit(B.fin);
             uint64_t t0 = gtime();
             while (!ptx::mbar_test(B.fin, 0)) {
-                if (gtime() - t0 > kWaitNs) {
+                if (gtime() - t0 > p.wait_ns) {
                     *(volatile int*)p.err = MB_ERR_TIMEOUT;
                     break;
                 }
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             const int nrows = it.rows + 14;
             for (int u = 0; u < nrows; ++u) {
                 const uint32_t q = in_seq + u, s = q % kInRing;
-                wait_phase(&B.in_empty[s], ((q / kInRing) & 1) ^ 1, abort_flag, p.err);
+                wait_phase(&B.in_empty[s], ((q / kInRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
                 const int sy = refl_clamp(d.ry0 + it.y0 - 7 + u, d.h);
                 const uint8_t* row = src + (int64_t)sy * d.in_pitch;
                 float* dst = in_ring + s * kPitch;
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                     const int sx = refl_clamp(d.rx0 + it.x0 - 7 + c, d.w);
                     dst[c] = (float)__ldg(row + sx) / 255.0f;
                 }
-                ptx::mbar_arrive(&B.in_full[s]);
+                if (!p.fault_stall) ptx::mbar_arrive(&B.in_full[s]);
             }
             in_seq += nrows;
         }
@@ -433,11 +435,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                 if (t < 0) {
                     for (int u = 0; u < 5; ++u) {
                         const uint32_t q = in_seq + u;
-                        wait_phase(&B.in_full[q % kInRing], (q / kInRing) & 1, abort_flag, p.err);
+                        wait_phase(&B.in_full[q % kInRing], (q / kInRing) & 1, abort_flag, p.err, p.wait_ns);
                     }
                 } else {
                     const uint32_t qi = in_seq + t + 5;
-                    wait_phase(&B.in_full[qi % kInRing], (qi / kInRing) & 1, abort_flag, p.err);
+                    wait_phase(&B.in_full[qi % kInRing], (qi / kInRing) & 1, abort_flag, p.err, p.wait_ns);
                 }
                 // layer 1 at input-frame row t+1, column c: FP32 (packed two-channel FMAs), weights
                 // broadcast from shared memory
@@ -487,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                         m[ch] = fmaxf(m[ch], nb);
                     }
                     const uint32_t q = m1_seq + t, s = q % kRing;
-                    wait_phase(&B.m1_empty[s], ((q / kRing) & 1) ^ 1, abort_flag, p.err);
+                    wait_phase(&B.m1_empty[s], ((q / kRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
                     store_pixel<FP8>(smem + C::oR1 + s * C::kSlotBytes, c, m, cst + kCQ1);
                     ptx::fence_proxy_async_smem();
                     ptx::mbar_arrive(&B.m1_full[s]);
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             const int N2 = it.rows + 5;
             for (int j = 0; j < N2; ++j) {
                 const uint32_t q = a2_seq + j, s = q % C::kAcc;
-                wait_phase(&B.a2_full[s], (q / C::kAcc) & 1, abort_flag, p.err);
+                wait_phase(&B.a2_full[s], (q / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
                 ptx::tc_fence_after();
                 float v[32];
                 const uint32_t ta = tbase + ((uint32_t)(32 * pw) << 16) + 32u * s;
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                         m[ch] = fmaxf(m[ch], nb);
                     }
                     const uint32_t q2 = m2_seq + j - 1, s2 = q2 % kRing;
-                    wait_phase(&B.m2_empty[s2], ((q2 / kRing) & 1) ^ 1, abort_flag, p.err);
+                    wait_phase(&B.m2_empty[s2], ((q2 / kRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
                     store_pixel<FP8>(smem + C::oR2 + s2 * C::kSlotBytes, c, m, cst + kCQ2);
                     ptx::fence_proxy_async_smem();
                     ptx::mbar_arrive(&B.m2_full[s2]);
@@ -560,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             const bool col_ok = c < kStrip && it.x0 + c < d.rw;
             for (int y = 0; y < NR; ++y) {
                 const uint32_t q = a3_seq + y, s = q % C::kAcc;
-                wait_phase(&B.a3_full[s], (q / C::kAcc) & 1, abort_flag, p.err);
+                wait_phase(&B.a3_full[s], (q / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
                 ptx::tc_fence_after();
                 float v[32];
                 const uint32_t ta = tbase + 256u + ((uint32_t)(32 * pw) << 16) + 32u * s;
@@ -822,6 +824,11 @@ static int fill_blocks(mb_net* net, TcParams& prm, const mb_block* blocks, int n
     prm.rows_per_item = R;
     prm.lag = std::max(1, std::min(net->stages, kRing - 1));
     prm.out_u8 = ot == MB_OUT_U8;
+    // host-side fault injection for tests: MB_FAULT_STALL=1 makes every launch's first wait run
+    // out (the loader never signals its rows) after a short limit
+    const char* stall = getenv("MB_FAULT_STALL");
+    prm.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
+    prm.wait_ns = prm.fault_stall ? 200000000ull : kWaitNs;
     int used = first;
     int counted = 0;
     while (used < n_blocks && counted < kMaxBlocks) {

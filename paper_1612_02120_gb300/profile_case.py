@@ -1,0 +1,46 @@
+"""Small, fixed inference case for profilers: `reps` launches of one path on a z x h x w synthetic
+volume (the generator of `synth`), so a capture of one kernel stays a few hundred MB on the device.
+
+    python -m paper_1612_02120_gb300.profile_case --prec bf16 --z 4 --h 1024 --w 1024 --reps 3
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp8", "student"])
+    ap.add_argument("--z", type=int, default=4)
+    ap.add_argument("--h", type=int, default=1024)
+    ap.add_argument("--w", type=int, default=1024)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    import torch
+
+    import synth
+    from paper_1612_02120_gb300 import build, membrane as m
+    build.build()
+    v = synth.em_volume(synth.BASE_SEED + 1, a.z, a.h, a.w)
+    x = torch.from_numpy(v).cuda()
+    out = torch.empty((a.z, a.h, a.w), dtype=torch.float32, device="cuda")
+    if a.prec == "student":
+        net = m.Net(synth.STUDENT, m.MB_PREC_BF16, 0, synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED))
+    else:
+        prec = {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16, "fp8": m.MB_PREC_FP8}[a.prec]
+        net = m.Net(synth.TEACHER, prec, 0, synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED))
+        if prec == m.MB_PREC_FP8:
+            m.mb_calibrate_fp8(net.handle, x[: min(4, a.z)], min(4, a.z), a.h, a.w)
+    for _ in range(a.reps):
+        m.mb_infer_volume(net.handle, x, a.z, a.h, a.w, out)
+    torch.cuda.synchronize()
+    print(f"ok {a.prec} {a.z}x{a.h}x{a.w} mean p {float(out.mean()):.6f}")
+    net.close()
+
+
+if __name__ == "__main__":
+    main()
