@@ -17,9 +17,10 @@
 // of 8 row accumulators per layer); the column tap dx is a 16-byte shift of the A descriptor's
 // start address in the no-swizzle K-major layout [channel chunk][pixel][16 B].
 //
-// Warp roles (512 threads): warp 0 issues MMAs (one thread) and owns TMEM; warp 1 loads uint8
-// input rows (reflect-101 mirror padding, /255); warps 4-7 drain layer-2 accumulators; warps
-// 8-11 drain layer-3 accumulators; warps 12-15 compute layer 1. Hand-offs are mbarriers; every
+// Warp roles (512 threads): warp 0 owns TMEM and one thread of it issues layer-2 MMAs; one
+// thread of warp 2 issues layer-3 MMAs; warp 1 loads uint8 input rows (reflect-101 mirror
+// padding, /255); warps 4-7 drain layer-2 accumulators; warps 8-11 drain layer-3 accumulators;
+// warps 12-15 compute layer 1. Hand-offs are mbarriers; every
 // wait is bounded by a 4 s global-timer limit after which the CTA records MB_ERR_TIMEOUT, stops
 // issuing work and leaves cleanly (TMEM is always freed).
 #include <cuda_bf16.h>
@@ -96,7 +97,7 @@ struct Cfg {
     static constexpr int oSt2 = oSt1 + 2 * 4 * 32 * 4;
     static constexpr int oConst = oSt2 + 2 * 4 * 32 * 4;
     static constexpr int oBar = oConst + kConsts * 4;
-    static constexpr int kBars = 2 * kInRing + 4 * kRing + 4 * 8 + 1;
+    static constexpr int kBars = 2 * kInRing + 4 * kRing + 4 * 8 + 2;
     static constexpr int oMisc = oBar + kBars * 8;
     static constexpr int kSmem = oMisc + 16;
 };
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             ptx::mbar_init(&B.a3_free[i], 128);
         }
         ptx::mbar_init(B.fin, 1);
+        ptx::mbar_init(B.fin + 1, 1);
         *abort_flag = 0;
         ptx::mbar_fence_init();
     }
@@ -339,58 +341,47 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     __syncthreads();
     ptx::tc_fence_after();
 
-    if (warp == 0) {
-        // ================= MMA issuer ========================================================
+    if (warp == 0 || warp == 2) {
+        // ================= MMA issuers: warp 0 lane 0 for layer 2, warp 2 lane 0 for layer 3 ======
+        // Each issuer commits (and finally drains) only its own MMAs.
         if (lane == 0) {
-            uint32_t m1_seq = 0, m2_seq = 0, a2_seq = 0, a3_seq = 0;
+            const bool l2 = warp == 0;
+            uint32_t in_seq = 0, acc_seq = 0;  // A-ring rows consumed, accumulator rows completed
             bool ok = true;
-            // ring slot i of a layer's A operand: base descriptor + i slots (start-address field)
-            const uint64_t ad1 = ptx::smem_desc(smem_base + C::oR1, kPitch * 16, 128);
-            const uint64_t ad2 = ptx::smem_desc(smem_base + C::oR2, kPitch * 16, 128);
-            const uint64_t bd2 = ptx::smem_desc(smem_base + C::oB, C::kLboB, 128);
-            const uint64_t bd3 = ptx::smem_desc(smem_base + C::oB + C::kLayerB, C::kLboB, 128);
+            // ring slot i of the layer's A operand: base descriptor + i slots (start-address field)
+            const uint64_t ad = ptx::smem_desc(smem_base + (l2 ? C::oR1 : C::oR2), kPitch * 16, 128);
+            const uint64_t bd = ptx::smem_desc(smem_base + C::oB + (l2 ? 0 : C::kLayerB), C::kLboB, 128);
+            const uint32_t tcol = tbase + (l2 ? 0u : 256u);
+            uint64_t* full = l2 ? B.m1_full : B.m2_full;
+            uint64_t* empty = l2 ? B.m1_empty : B.m2_empty;
+            uint64_t* afree = l2 ? B.a2_free : B.a3_free;
+            uint64_t* afull = l2 ? B.a2_full : B.a3_full;
             for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
                 const ItemInfo it = decode_item(p, k);
                 const int NR = it.rows;
-                const int M1 = NR + 9, N2 = NR + 5, M2 = NR + 4;
-                for (int r = 0; r < M1 + p.lag; ++r) {
-                    if (r < M1) {
-                        const uint32_t q = m1_seq + r, s = q % kRing;
-                        ok = ok && wait_phase(&B.m1_full[s], (q / kRing) & 1, abort_flag, p.err, p.wait_ns);
-                        if (r < N2) {
-                            const uint32_t qa = a2_seq + r;
-                            ok = ok && wait_phase(&B.a2_free[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag,
-                                                  p.err, p.wait_ns);
-                        }
-                        ptx::tc_fence_after();
-                        if (ok) issue_row<FP8>(tbase, a2_seq, r, N2, ad1 + (uint64_t)(s * (C::kSlotBytes >> 4)), bd2);
-                        ptx::mma_commit(&B.m1_empty[s]);
-                        if (r >= 4 && r - 4 < N2) ptx::mma_commit(&B.a2_full[(a2_seq + r - 4) % C::kAcc]);
+                const int n_in = l2 ? NR + 9 : NR + 4;   // input rows of this layer
+                const int n_out = l2 ? NR + 5 : NR;      // output rows of this layer
+                for (int r = 0; r < n_in; ++r) {
+                    const uint32_t q = in_seq + r, s = q % kRing;
+                    ok = ok && wait_phase(&full[s], (q / kRing) & 1, abort_flag, p.err, p.wait_ns);
+                    if (r < n_out) {
+                        const uint32_t qa = acc_seq + r;
+                        ok = ok && wait_phase(&afree[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag, p.err,
+                                              p.wait_ns);
                     }
-                    const int sr = r - 5 - p.lag;
-                    if (sr >= 0 && sr < M2) {
-                        const uint32_t q = m2_seq + sr, s = q % kRing;
-                        ok = ok && wait_phase(&B.m2_full[s], (q / kRing) & 1, abort_flag, p.err, p.wait_ns);
-                        if (sr < NR) {
-                            const uint32_t qa = a3_seq + sr;
-                            ok = ok && wait_phase(&B.a3_free[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag,
-                                                  p.err, p.wait_ns);
-                        }
-                        ptx::tc_fence_after();
-                        if (ok) issue_row<FP8>(tbase + 256, a3_seq, sr, NR, ad2 + (uint64_t)(s * (C::kSlotBytes >> 4)), bd3);
-                        ptx::mma_commit(&B.m2_empty[s]);
-                        if (sr >= 4 && sr - 4 < NR) ptx::mma_commit(&B.a3_full[(a3_seq + sr - 4) % C::kAcc]);
-                    }
+                    ptx::tc_fence_after();
+                    if (ok) issue_row<FP8>(tcol, acc_seq, r, n_out, ad + (uint64_t)(s * (C::kSlotBytes >> 4)), bd);
+                    ptx::mma_commit(&empty[s]);
+                    if (r >= 4 && r - 4 < n_out) ptx::mma_commit(&afull[(acc_seq + r - 4) % C::kAcc]);
                 }
-                m1_seq += M1;
-                m2_seq += M2;
-                a2_seq += N2;
-                a3_seq += NR;
+                in_seq += n_in;
+                acc_seq += n_out;
             }
-            // drain: all MMAs complete before TMEM is released
-            ptx::mma_commit(B.fin);
-            uint64_t t0 = gtime();
-            while (!ptx::mbar_test(B.fin, 0)) {
+            // drain: all of this issuer's MMAs complete before TMEM is released
+            uint64_t* fin = B.fin + (l2 ? 0 : 1);
+            ptx::mma_commit(fin);
+            const uint64_t t0 = gtime();
+            while (!ptx::mbar_test(fin, 0)) {
                 if (gtime() - t0 > p.wait_ns) {
                     *(volatile int*)p.err = MB_ERR_TIMEOUT;
                     break;
@@ -586,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             a3_seq += NR;
         }
     }
-    // warps 2 and 3 have no role
+    // warp 3 has no role
 
     ptx::tc_fence_before();
     __syncthreads();
