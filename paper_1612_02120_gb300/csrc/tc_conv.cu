@@ -206,6 +206,38 @@ __device__ __forceinline__ void store_pixel(uint8_t* slot, int c, const float (&
     }
 }
 
+// Store 16 channels (one half h of the 32) of one pixel: BF16 chunks 2h and 2h+1, or E4M3 chunk h.
+template <bool FP8>
+__device__ __forceinline__ void store_half(uint8_t* slot, int c, int h, const float (&m)[16], const float* q) {
+    if (!FP8) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            uint4 u;
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(m[8 * k + 0], m[8 * k + 1]);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(m[8 * k + 2], m[8 * k + 3]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(m[8 * k + 4], m[8 * k + 5]);
+            __nv_bfloat162 h3 = __floats2bfloat162_rn(m[8 * k + 6], m[8 * k + 7]);
+            u.x = *reinterpret_cast<uint32_t*>(&h0);
+            u.y = *reinterpret_cast<uint32_t*>(&h1);
+            u.z = *reinterpret_cast<uint32_t*>(&h2);
+            u.w = *reinterpret_cast<uint32_t*>(&h3);
+            *reinterpret_cast<uint4*>(slot + ((2 * h + k) * kPitch + c) * 16) = u;
+        }
+    } else {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int ch = 4 * j;
+            __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(m[ch] * q[ch], m[ch + 1] * q[ch + 1]),
+                                                               __NV_SATFINITE, __NV_E4M3);
+            __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(m[ch + 2] * q[ch + 2], m[ch + 3] * q[ch + 3]), __NV_SATFINITE, __NV_E4M3);
+            w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        *reinterpret_cast<uint4*>(slot + (h * kPitch + c) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 // Issue the MMAs of one input row r for one layer: output rows j = r-4+i of the layer for the
 // valid blocks i (0 <= j < n_out). Every MMA accumulates; the epilogue zeroes an accumulator after
 // draining it, so a row's first contribution adds to zero. Blocks go to ring slots
@@ -413,11 +445,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         }
     } else if (warp >= 12) {
         // ================= layer 1 + max-filter producer ======================================
-        const int c = tid - 384;  // pixel column 0..127
+        // Thread = (channel half h, column pair cp): columns c0 = 2 cp and c0 + 1, channels
+        // 16h .. 16h+15. Warps 12,13 hold half 0 (columns 0-63, 64-127), warps 14,15 half 1, so
+        // every weight load is a warp-wide broadcast feeding two columns.
         const int pw = warp - 12;
+        const int h = pw >> 1;
+        const int c0 = 2 * ((pw & 1) * 32 + lane);
         float* stage = reinterpret_cast<float*>(smem + C::oSt1);
         uint32_t in_seq = 0, m1_seq = 0;
-        float prev[32], cur[32];
+        float prev[2][16], cur[2][16];
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const ItemInfo it = decode_item(p, k);
             const int NR = it.rows;
@@ -432,61 +468,82 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                     const uint32_t qi = in_seq + t + 5;
                     wait_phase(&B.in_full[qi % kInRing], (qi / kInRing) & 1, abort_flag, p.err, p.wait_ns);
                 }
-                // layer 1 at input-frame row t+1, column c: FP32 (packed two-channel FMAs), weights
-                // broadcast from shared memory
-                float2 a2[16];
+                // layer 1 at input-frame row t+1: FP32 packed two-channel FMAs, weights broadcast
+                float2 a0[8], a1[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float4 b = *reinterpret_cast<const float4*>(cst + kCB1 + 4 * j);
-                    a2[2 * j] = make_float2(b.x, b.y);
-                    a2[2 * j + 1] = make_float2(b.z, b.w);
+                for (int j = 0; j < 4; ++j) {
+                    const float4 b = *reinterpret_cast<const float4*>(cst + kCB1 + 16 * h + 4 * j);
+                    a0[2 * j] = make_float2(b.x, b.y);
+                    a0[2 * j + 1] = make_float2(b.z, b.w);
+                    a1[2 * j] = a0[2 * j];
+                    a1[2 * j + 1] = a0[2 * j + 1];
                 }
 #pragma unroll 1
                 for (int ky = 0; ky < 5; ++ky) {
-                    const float* ir = in_ring + ((in_seq + t + 1 + ky) % kInRing) * kPitch + c;
+                    const float* ir = in_ring + ((in_seq + t + 1 + ky) % kInRing) * kPitch + c0;
+                    const float2 x01 = *reinterpret_cast<const float2*>(ir);
+                    const float2 x23 = *reinterpret_cast<const float2*>(ir + 2);
+                    const float2 x45 = *reinterpret_cast<const float2*>(ir + 4);
+                    const float x[6] = {x01.x, x01.y, x23.x, x23.y, x45.x, x45.y};
 #pragma unroll
                     for (int kx = 0; kx < 5; ++kx) {
-                        const float x = ir[kx];
-                        const float2 xx = make_float2(x, x);
-                        const float4* wt = reinterpret_cast<const float4*>(cst + kCW1 + (ky * 5 + kx) * 32);
+                        const float2 xa = make_float2(x[kx], x[kx]);
+                        const float2 xb = make_float2(x[kx + 1], x[kx + 1]);
+                        const float4* wt = reinterpret_cast<const float4*>(cst + kCW1 + (ky * 5 + kx) * 32 + 16 * h);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < 4; ++j) {
                             const float4 w = wt[j];
-                            a2[2 * j] = __ffma2_rn(make_float2(w.x, w.y), xx, a2[2 * j]);
-                            a2[2 * j + 1] = __ffma2_rn(make_float2(w.z, w.w), xx, a2[2 * j + 1]);
+                            const float2 wl = make_float2(w.x, w.y), wh = make_float2(w.z, w.w);
+                            a0[2 * j] = __ffma2_rn(wl, xa, a0[2 * j]);
+                            a0[2 * j + 1] = __ffma2_rn(wh, xa, a0[2 * j + 1]);
+                            a1[2 * j] = __ffma2_rn(wl, xb, a1[2 * j]);
+                            a1[2 * j + 1] = __ffma2_rn(wh, xb, a1[2 * j + 1]);
                         }
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    cur[2 * j] = fmaxf(a2[j].x, 0.f);
-                    cur[2 * j + 1] = fmaxf(a2[j].y, 0.f);
+                for (int j = 0; j < 8; ++j) {
+                    cur[0][2 * j] = fmaxf(a0[j].x, 0.f);
+                    cur[0][2 * j + 1] = fmaxf(a0[j].y, 0.f);
+                    cur[1][2 * j] = fmaxf(a1[j].x, 0.f);
+                    cur[1][2 * j + 1] = fmaxf(a1[j].y, 0.f);
                 }
                 ptx::mbar_arrive(&B.in_empty[(in_seq + t + 1) % kInRing]);
                 if (t >= 0) {
-                    float (&m)[32] = prev;  // vertical max in place; prev is reloaded from cur below
+                    // vertical max in place (prev is reloaded from cur below)
 #pragma unroll
-                    for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], cur[ch]);
-                    // horizontal neighbour c+1: shuffle inside the warp, staging across warps
-                    float* st = stage + (t & 1) * 128;
-                    if (lane == 0)
+                    for (int ch = 0; ch < 16; ++ch) {
+                        prev[0][ch] = fmaxf(prev[0][ch], cur[0][ch]);
+                        prev[1][ch] = fmaxf(prev[1][ch], cur[1][ch]);
+                    }
+                    // horizontal: column c0 pairs with c0+1 (same thread); column c0+1 with c0+2 =
+                    // the next lane's first column, or for lane 31 the next warp's lane 0
+                    float* st = stage + (t & 1) * 64;
+                    if ((pw & 1) == 1 && lane == 0)
 #pragma unroll
-                        for (int ch = 0; ch < 32; ++ch) st[pw * 32 + ch] = m[ch];
+                        for (int ch = 0; ch < 16; ++ch) st[h * 16 + ch] = prev[0][ch];
                     asm volatile("bar.sync 1, 128;" ::: "memory");
+                    float o0[16], o1[16];
 #pragma unroll
-                    for (int ch = 0; ch < 32; ++ch) {
-                        float nb = __shfl_down_sync(0xffffffffu, m[ch], 1);
-                        if (lane == 31) nb = pw < 3 ? st[(pw + 1) * 32 + ch] : m[ch];
-                        m[ch] = fmaxf(m[ch], nb);
+                    for (int ch = 0; ch < 16; ++ch) {
+                        float nb = __shfl_down_sync(0xffffffffu, prev[0][ch], 1);
+                        if (lane == 31) nb = (pw & 1) == 0 ? st[h * 16 + ch] : prev[1][ch];
+                        o0[ch] = fmaxf(prev[0][ch], prev[1][ch]);
+                        o1[ch] = fmaxf(prev[1][ch], nb);
                     }
                     const uint32_t q = m1_seq + t, s = q % kRing;
                     wait_phase(&B.m1_empty[s], ((q / kRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                    store_pixel<FP8>(smem + C::oR1 + s * C::kSlotBytes, c, m, cst + kCQ1);
+                    uint8_t* slot = smem + C::oR1 + s * C::kSlotBytes;
+                    store_half<FP8>(slot, c0, h, o0, cst + kCQ1 + 16 * h);
+                    store_half<FP8>(slot, c0 + 1, h, o1, cst + kCQ1 + 16 * h);
                     ptx::fence_proxy_async_smem();
                     ptx::mbar_arrive(&B.m1_full[s]);
                 }
 #pragma unroll
-                for (int ch = 0; ch < 32; ++ch) prev[ch] = cur[ch];
+                for (int ch = 0; ch < 16; ++ch) {
+                    prev[0][ch] = cur[0][ch];
+                    prev[1][ch] = cur[1][ch];
+                }
             }
             for (int u = M1 + 1; u < NR + 14; ++u) ptx::mbar_arrive(&B.in_empty[(in_seq + u) % kInRing]);
             in_seq += NR + 14;
