@@ -363,6 +363,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     ptx::tc_fence_after();
     const uint32_t tbase = *tmem_slot;
     const uint32_t smem_base = ptx::smem_u32(smem);
+    // Register budget per warpgroup (launched with 128 per thread = the whole register file):
+    // MMA issuers + loader 56, layer-2 epilogue 112, layer-3 epilogue 80, layer-1 producers 232.
+    // Sum 480 <= 512 per thread-slot, so the producers' increase is always satisfiable.
+    static_assert(56 + 112 + 80 + 232 <= 4 * 128, "register budget exceeds the launch allocation");
     if (warp >= 4 && warp < 12) {
         // every accumulator starts at zero (the MMAs only accumulate)
         const uint32_t col0 = warp < 8 ? 0u : 256u;
@@ -373,7 +377,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     __syncthreads();
     ptx::tc_fence_after();
 
-    if (warp == 0 || warp == 2) {
+    if (warp < 4) {
+        ptx::setmaxnreg_dec<56>();
+        if (warp == 0 || warp == 2) {
         // ================= MMA issuers: warp 0 lane 0 for layer 2, warp 2 lane 0 for layer 3 ======
         // Each issuer commits (and finally drains) only its own MMAs.
         if (lane == 0) {
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             }
         }
         __syncwarp();
-    } else if (warp == 1) {
+        } else if (warp == 1) {
         // ================= input loader ======================================================
         uint32_t in_seq = 0;
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
@@ -443,7 +449,96 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             }
             in_seq += nrows;
         }
-    } else if (warp >= 12) {
+        }
+        // warp 3 has no role
+    } else if (warp < 8) {
+        ptx::setmaxnreg_dec<112>();
+        // ================= layer-2 epilogue: bias, ReLU, max-filter -> A ring of layer 3 =======
+        const int c = tid - 128;
+        const int pw = warp - 4;
+        float* stage = reinterpret_cast<float*>(smem + C::oSt2);
+        uint32_t a2_seq = 0, m2_seq = 0;
+        float prev[32];
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const ItemInfo it = decode_item(p, k);
+            const int N2 = it.rows + 5;
+            for (int j = 0; j < N2; ++j) {
+                const uint32_t q = a2_seq + j, s = q % C::kAcc;
+                wait_phase(&B.a2_full[s], (q / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
+                ptx::tc_fence_after();
+                float v[32];
+                const uint32_t ta = tbase + ((uint32_t)(32 * pw) << 16) + 32u * s;
+                ptx::tmem_ld32(ta, v);
+                ptx::tmem_st32_zero(ta);
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&B.a2_free[s]);
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) v[ch] = fmaxf(fmaf(v[ch], cst[kCE2S + ch], cst[kCE2B + ch]), 0.f);
+                if (j > 0) {
+                    float (&m)[32] = prev;  // vertical max in place; prev is reloaded from v below
+#pragma unroll
+                    for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], v[ch]);
+                    float* st = stage + (j & 1) * 128;
+                    if (lane == 0)
+#pragma unroll
+                        for (int ch = 0; ch < 32; ++ch) st[pw * 32 + ch] = m[ch];
+                    asm volatile("bar.sync 2, 128;" ::: "memory");
+#pragma unroll
+                    for (int ch = 0; ch < 32; ++ch) {
+                        float nb = __shfl_down_sync(0xffffffffu, m[ch], 1);
+                        if (lane == 31) nb = pw < 3 ? st[(pw + 1) * 32 + ch] : m[ch];
+                        m[ch] = fmaxf(m[ch], nb);
+                    }
+                    const uint32_t q2 = m2_seq + j - 1, s2 = q2 % kRing;
+                    wait_phase(&B.m2_empty[s2], ((q2 / kRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                    store_pixel<FP8>(smem + C::oR2 + s2 * C::kSlotBytes, c, m, cst + kCQ2);
+                    ptx::fence_proxy_async_smem();
+                    ptx::mbar_arrive(&B.m2_full[s2]);
+                }
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch) prev[ch] = v[ch];
+            }
+            a2_seq += N2;
+            m2_seq += N2 - 1;
+        }
+    } else if (warp < 12) {
+        ptx::setmaxnreg_dec<80>();
+        // ================= layer-3 epilogue: bias, ReLU, head, sigmoid, store ==================
+        const int c = tid - 256;
+        const int pw = warp - 8;
+        uint32_t a3_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const ItemInfo it = decode_item(p, k);
+            const TcBlockDesc& d = p.blk[it.b];
+            const int NR = it.rows;
+            const bool col_ok = c < kStrip && it.x0 + c < d.rw;
+            for (int y = 0; y < NR; ++y) {
+                const uint32_t q = a3_seq + y, s = q % C::kAcc;
+                wait_phase(&B.a3_full[s], (q / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
+                ptx::tc_fence_after();
+                float v[32];
+                const uint32_t ta = tbase + 256u + ((uint32_t)(32 * pw) << 16) + 32u * s;
+                ptx::tmem_ld32(ta, v);
+                ptx::tmem_st32_zero(ta);
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&B.a3_free[s]);
+                float z = p.hb;
+#pragma unroll
+                for (int ch = 0; ch < 32; ++ch)
+                    z = fmaf(cst[kCHW + ch], fmaxf(fmaf(v[ch], cst[kCE3S + ch], cst[kCE3B + ch]), 0.f), z);
+                const float prob = 1.0f / (1.0f + expf(-z));
+                if (col_ok && !*abort_flag) {
+                    const int64_t idx = (int64_t)it.zi * d.out_slice + (int64_t)(it.y0 + y) * d.out_pitch + it.x0 + c;
+                    if (p.out_u8)
+                        static_cast<uint8_t*>(d.out)[idx] = (uint8_t)fminf(floorf(255.0f * prob + 0.5f), 255.0f);
+                    else
+                        static_cast<float*>(d.out)[idx] = prob;
+                }
+            }
+            a3_seq += NR;
+        }
+    } else {
+        ptx::setmaxnreg_inc<232>();
         // ================= layer 1 + max-filter producer ======================================
         // Thread = (channel half h, column pair cp): columns c0 = 2 cp and c0 + 1, channels
         // 16h .. 16h+15. Warps 12,13 hold half 0 (columns 0-63, 64-127), warps 14,15 half 1, so
@@ -480,20 +575,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                 }
 #pragma unroll 1
                 for (int ky = 0; ky < 5; ++ky) {
+                    // all loads of this row tap first (20 broadcast weight vectors, 6 inputs), then
+                    // 80 packed FMAs
                     const float* ir = in_ring + ((in_seq + t + 1 + ky) % kInRing) * kPitch + c0;
                     const float2 x01 = *reinterpret_cast<const float2*>(ir);
                     const float2 x23 = *reinterpret_cast<const float2*>(ir + 2);
                     const float2 x45 = *reinterpret_cast<const float2*>(ir + 4);
                     const float x[6] = {x01.x, x01.y, x23.x, x23.y, x45.x, x45.y};
+                    const float4* wrow = reinterpret_cast<const float4*>(cst + kCW1 + ky * 5 * 32 + 16 * h);
+                    float4 w[5][4];
+#pragma unroll
+                    for (int kx = 0; kx < 5; ++kx)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) w[kx][j] = wrow[kx * 8 + j];
 #pragma unroll
                     for (int kx = 0; kx < 5; ++kx) {
                         const float2 xa = make_float2(x[kx], x[kx]);
                         const float2 xb = make_float2(x[kx + 1], x[kx + 1]);
-                        const float4* wt = reinterpret_cast<const float4*>(cst + kCW1 + (ky * 5 + kx) * 32 + 16 * h);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float4 w = wt[j];
-                            const float2 wl = make_float2(w.x, w.y), wh = make_float2(w.z, w.w);
+                            const float2 wl = make_float2(w[kx][j].x, w[kx][j].y), wh = make_float2(w[kx][j].z, w[kx][j].w);
                             a0[2 * j] = __ffma2_rn(wl, xa, a0[2 * j]);
                             a0[2 * j + 1] = __ffma2_rn(wh, xa, a0[2 * j + 1]);
                             a1[2 * j] = __ffma2_rn(wl, xb, a1[2 * j]);
@@ -549,92 +650,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             in_seq += NR + 14;
             m1_seq += M1;
         }
-    } else if (warp >= 4 && warp < 8) {
-        // ================= layer-2 epilogue: bias, ReLU, max-filter -> A ring of layer 3 =======
-        const int c = tid - 128;
-        const int pw = warp - 4;
-        float* stage = reinterpret_cast<float*>(smem + C::oSt2);
-        uint32_t a2_seq = 0, m2_seq = 0;
-        float prev[32];
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const ItemInfo it = decode_item(p, k);
-            const int N2 = it.rows + 5;
-            for (int j = 0; j < N2; ++j) {
-                const uint32_t q = a2_seq + j, s = q % C::kAcc;
-                wait_phase(&B.a2_full[s], (q / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
-                ptx::tc_fence_after();
-                float v[32];
-                const uint32_t ta = tbase + ((uint32_t)(32 * pw) << 16) + 32u * s;
-                ptx::tmem_ld32(ta, v);
-                ptx::tmem_st32_zero(ta);
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(&B.a2_free[s]);
-#pragma unroll
-                for (int ch = 0; ch < 32; ++ch) v[ch] = fmaxf(fmaf(v[ch], cst[kCE2S + ch], cst[kCE2B + ch]), 0.f);
-                if (j > 0) {
-                    float (&m)[32] = prev;  // vertical max in place; prev is reloaded from v below
-#pragma unroll
-                    for (int ch = 0; ch < 32; ++ch) m[ch] = fmaxf(prev[ch], v[ch]);
-                    float* st = stage + (j & 1) * 128;
-                    if (lane == 0)
-#pragma unroll
-                        for (int ch = 0; ch < 32; ++ch) st[pw * 32 + ch] = m[ch];
-                    asm volatile("bar.sync 2, 128;" ::: "memory");
-#pragma unroll
-                    for (int ch = 0; ch < 32; ++ch) {
-                        float nb = __shfl_down_sync(0xffffffffu, m[ch], 1);
-                        if (lane == 31) nb = pw < 3 ? st[(pw + 1) * 32 + ch] : m[ch];
-                        m[ch] = fmaxf(m[ch], nb);
-                    }
-                    const uint32_t q2 = m2_seq + j - 1, s2 = q2 % kRing;
-                    wait_phase(&B.m2_empty[s2], ((q2 / kRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                    store_pixel<FP8>(smem + C::oR2 + s2 * C::kSlotBytes, c, m, cst + kCQ2);
-                    ptx::fence_proxy_async_smem();
-                    ptx::mbar_arrive(&B.m2_full[s2]);
-                }
-#pragma unroll
-                for (int ch = 0; ch < 32; ++ch) prev[ch] = v[ch];
-            }
-            a2_seq += N2;
-            m2_seq += N2 - 1;
-        }
-    } else if (warp >= 8 && warp < 12) {
-        // ================= layer-3 epilogue: bias, ReLU, head, sigmoid, store ==================
-        const int c = tid - 256;
-        const int pw = warp - 8;
-        uint32_t a3_seq = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const ItemInfo it = decode_item(p, k);
-            const TcBlockDesc& d = p.blk[it.b];
-            const int NR = it.rows;
-            const bool col_ok = c < kStrip && it.x0 + c < d.rw;
-            for (int y = 0; y < NR; ++y) {
-                const uint32_t q = a3_seq + y, s = q % C::kAcc;
-                wait_phase(&B.a3_full[s], (q / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
-                ptx::tc_fence_after();
-                float v[32];
-                const uint32_t ta = tbase + 256u + ((uint32_t)(32 * pw) << 16) + 32u * s;
-                ptx::tmem_ld32(ta, v);
-                ptx::tmem_st32_zero(ta);
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(&B.a3_free[s]);
-                float z = p.hb;
-#pragma unroll
-                for (int ch = 0; ch < 32; ++ch)
-                    z = fmaf(cst[kCHW + ch], fmaxf(fmaf(v[ch], cst[kCE3S + ch], cst[kCE3B + ch]), 0.f), z);
-                const float prob = 1.0f / (1.0f + expf(-z));
-                if (col_ok && !*abort_flag) {
-                    const int64_t idx = (int64_t)it.zi * d.out_slice + (int64_t)(it.y0 + y) * d.out_pitch + it.x0 + c;
-                    if (p.out_u8)
-                        static_cast<uint8_t*>(d.out)[idx] = (uint8_t)fminf(floorf(255.0f * prob + 0.5f), 255.0f);
-                    else
-                        static_cast<float*>(d.out)[idx] = prob;
-                }
-            }
-            a3_seq += NR;
-        }
     }
-    // warp 3 has no role
 
     ptx::tc_fence_before();
     __syncthreads();

@@ -129,6 +129,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// ---- per-warpgroup register budget (all four warps of a warpgroup execute the same one) -------
+template <uint32_t N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <uint32_t N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+
 // ---- registers -> TMEM: zero 32 lanes x 32 consecutive columns per warp, then wait ---------------
 __device__ __forceinline__ void tmem_st32_zero(uint32_t taddr) {
     const uint32_t z = 0u;
