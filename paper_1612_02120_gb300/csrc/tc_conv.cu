@@ -68,7 +68,7 @@ struct TcParams {
     float hb;
     const uint8_t* wpack;   // global: packed B operands of layers 2 and 3, then the constants
     int* err;               // error word (MB_ERR_TIMEOUT on a timed-out wait)
-    int n_blocks, n_items, rows_per_item, lag, out_u8;
+    int n_blocks, n_items, rows_per_item, lag, out_u8;  // lag: unused (one issuer per layer)
     int fault_stall;        // test injection: the input loader withholds its arrivals
     uint64_t wait_ns;       // limit of every device-side wait
     TcBlockDesc blk[kMaxBlocks];
@@ -131,6 +131,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
     const uint64_t t0 = gtime();
     uint32_t n = 0;
     while (!ptx::mbar_test(bar, parity)) {
+        __nanosleep(32);  // polls share the shared-memory pipe with the MMA operand reads
         if ((++n & 255u) == 0) {
             if (*abort_flag) return false;
             if (gtime() - t0 > limit_ns) {
@@ -886,7 +887,7 @@ static int fill_blocks(mb_net* net, TcParams& prm, const mb_block* blocks, int n
     prm.n_blocks = nb;
     prm.n_items = items;
     prm.rows_per_item = R;
-    prm.lag = std::max(1, std::min(net->stages, kRing - 1));
+    prm.lag = 0;
     prm.out_u8 = ot == MB_OUT_U8;
     // host-side fault injection for tests: MB_FAULT_STALL=1 makes every launch's first wait run
     // out (the loader never signals its rows) after a short limit
@@ -1082,8 +1083,7 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
     if (rc == MB_OK) {
         fill_bytes<<<1024, 256, 0, st>>>(in, z * h * w, 12345u);
         count_launch();
-        const int cand_rows[] = {32, 64, 128, 256, 1024};
-        const int cand_stages[] = {1, 2, 3};
+        const int cand_rows[] = {64, 128, 256, 512, 1024};
         mb_block b;
         b.in = in;
         b.z = z;
@@ -1097,7 +1097,8 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
         const int64_t y0 = 0, x0 = 0;
         for (int R : cand_rows) {
             if (R > 2 * h && R != cand_rows[0]) continue;
-            for (int S : cand_stages) {
+            {
+                const int S = kRing;  // A-ring depth: fixed at compile time, reported
                 net->rows_per_item = R;
                 net->stages = S;
                 float ms_sum = 0.f;

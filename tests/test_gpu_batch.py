@@ -81,7 +81,7 @@ def test_autotune_choice_and_cache(bf16, tmp_path):
     before = infer(bf16, v)
     cache = str(tmp_path / "tune.json")
     c1 = m.mb_autotune(bf16.handle, 2, 300, 260, cache)
-    assert not c1["from_cache"] and c1["rows_per_item"] > 0 and c1["stages"] in (1, 2, 3)
+    assert not c1["from_cache"] and c1["rows_per_item"] in (64, 128, 256, 512, 1024) and c1["stages"] >= 2
     c2 = m.mb_autotune(bf16.handle, 2, 300, 260, cache)
     assert c2["from_cache"] and c2["rows_per_item"] == c1["rows_per_item"] and c2["stages"] == c1["stages"]
     np.testing.assert_array_equal(infer(bf16, v), before)
