@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CONV, MAXF, HEAD = 0, 1, 2
+CONV, MAXF, HEAD, SOFTMAX = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -45,7 +45,10 @@ def _load():
             sig = {
                 "oracle_reflect101": ([i64, i64], i64),
                 "oracle_conv": ([p, i64, i64, i64, p, p, i64, i64, ci, p], ci),
+                "oracle_conv_dil": ([p, i64, i64, i64, p, p, i64, i64, i64, ci, p], ci),
                 "oracle_maxfilter2": ([p, i64, i64, i64, p], ci),
+                "oracle_maxfilter2_dil": ([p, i64, i64, i64, i64, p], ci),
+                "oracle_maxout": ([p, i64, i64, i64, p], ci),
                 "oracle_head_sigmoid": ([p, i64, i64, i64, p, d, p], ci),
                 "oracle_net_radius": ([p, ci], i64),
                 "oracle_param_count": ([p, ci], i64),
@@ -71,7 +74,13 @@ def _chk(rc, what):
 
 
 def _desc(layers) -> np.ndarray:
-    return np.ascontiguousarray(np.array(layers, dtype=np.int32).reshape(-1, 5))
+    """Layer tuples (kind, k, cin, cout, relu[, dilation[, maxout groups]]) as n x 7 int32."""
+    rows = []
+    for t in layers:
+        t = tuple(int(v) for v in t)
+        assert 5 <= len(t) <= 7, t
+        rows.append(t + (1, 1)[len(t) - 5:])
+    return np.ascontiguousarray(np.array(rows, dtype=np.int32).reshape(-1, 7))
 
 
 def _f64(a) -> np.ndarray:
@@ -95,6 +104,37 @@ def conv(x, W, b, relu: bool) -> np.ndarray:
     y = np.empty((cout, h - k + 1, w - k + 1), dtype=np.float64)
     _chk(_load().oracle_conv(x.ctypes.data, cin, h, w, W.ctypes.data, b.ctypes.data, cout, k, int(relu),
                              y.ctypes.data), "conv")
+    return y
+
+
+def conv_dil(x, W, b, dilation: int, relu: bool) -> np.ndarray:
+    """Dilated valid cross-correlation: y[i][j] = b + sum W[ky][kx] x[i + d ky][j + d kx]."""
+    x, W, b = _f64(x), _f64(W), _f64(b)
+    cin, h, w = x.shape
+    cout, cin2, k, k2 = W.shape
+    assert cin2 == cin and k == k2 and b.shape == (cout,)
+    s = (k - 1) * dilation
+    y = np.empty((cout, h - s, w - s), dtype=np.float64)
+    _chk(_load().oracle_conv_dil(x.ctypes.data, cin, h, w, W.ctypes.data, b.ctypes.data, cout, k, dilation,
+                                 int(relu), y.ctypes.data), "conv_dil")
+    return y
+
+
+def maxfilter2_dil(x, dilation: int) -> np.ndarray:
+    x = _f64(x)
+    c, h, w = x.shape
+    y = np.empty((c, h - dilation, w - dilation), dtype=np.float64)
+    _chk(_load().oracle_maxfilter2_dil(x.ctypes.data, c, h, w, dilation, y.ctypes.data), "maxfilter2_dil")
+    return y
+
+
+def maxout(x, groups: int) -> np.ndarray:
+    """Max-out over consecutive channel groups: y[c] = max_g x[c*G + g]."""
+    x = _f64(x)
+    cg, h, w = x.shape
+    assert cg % groups == 0
+    y = np.empty((cg // groups, h, w), dtype=np.float64)
+    _chk(_load().oracle_maxout(x.ctypes.data, cg // groups, groups, h * w, y.ctypes.data), "maxout")
     return y
 
 
@@ -135,9 +175,7 @@ def pad_region(slice_u8, y0, x0, h, w, R) -> np.ndarray:
 
 def run_layers(layers, params, xp) -> np.ndarray:
     d, prm, xp = _desc(layers), _f64(params), _f64(xp)
-    s = 0
-    for kind, k, *_ in d:
-        s += int(k) - 1
+    s = sum((int(row[1]) - 1) * int(row[5]) for row in d)
     ph, pw = xp.shape
     p = np.empty((ph - s, pw - s), dtype=np.float64)
     _chk(_load().oracle_run_layers(d.ctypes.data, len(d), prm.ctypes.data, xp.ctypes.data, ph, pw,

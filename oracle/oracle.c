@@ -19,8 +19,16 @@
  *    forward, mean-squared-error loss against teacher maps, and the analytic weight gradient.
  *  - Adam (Kingma and Ba, 2014) with bias correction.
  *
+ * FastMemb (Sec. 2.2, "A lightweight network architecture"; "Accelerating dense computation"):
+ *    its dense form is the stride-1 network in which every stride-2 max-pool becomes a 2x2
+ *    max-filter and every later layer is dilated by the accumulated stride (dilated cross-
+ *    correlation y[i][j] = b + sum W[ky][kx] x[i + d ky][j + d kx]); max-out keeps the maximum
+ *    over groups of feature maps (output channel c = max_g of conv channel c*G + g); the 2-class
+ *    softmax head outputs p = exp(z1) / (exp(z0) + exp(z1)).
+ *
  * Conventions: activations are [c][y][x] row-major; parameters per parameterised layer are
- * W[cout][cin][k][k] followed by b[cout]; the input pixel value is u / 255.
+ * W[cout*G][cin][k][k] followed by b[cout*G] (G = max-out groups, 1 without max-out); the input
+ * pixel value is u / 255. A layer description is 7 ints {kind, k, cin, cout, relu, dilation, G}.
  * Compile with -ffp-contract=off.
  */
 #include <math.h>
@@ -32,10 +40,12 @@
 #define OR_ERR_ARG 1
 #define OR_ERR_OOM 2
 
-/* layer kinds of a layer description: {kind, k, cin, cout, relu} per layer */
+/* layer kinds of a layer description: {kind, k, cin, cout, relu, dilation, maxout} per layer */
 #define OR_CONV 0
 #define OR_MAXF 1
 #define OR_HEAD 2
+#define OR_SOFTMAX 3
+#define OR_DW 7
 
 /* reflect-101 index map for n >= 2 (one reflection suffices when |overhang| < n) */
 int64_t oracle_reflect101(int64_t t, int64_t n) {
@@ -45,14 +55,17 @@ int64_t oracle_reflect101(int64_t t, int64_t n) {
 }
 
 /*
- * Valid cross-correlation: y[co][i][j] = b[co] + sum_ci sum_ky sum_kx W[co][ci][ky][kx] *
- * x[ci][i+ky][j+kx], then max(0, .) when relu. x is cin x h x w, y is cout x (h-k+1) x (w-k+1).
- * Each output element accumulates its terms in the order (ci, ky, kx), starting from the bias.
+ * Valid cross-correlation with dilation d: y[co][i][j] = b[co] + sum_ci sum_ky sum_kx
+ * W[co][ci][ky][kx] * x[ci][i + d ky][j + d kx], then max(0, .) when relu. x is cin x h x w, y is
+ * cout x (h - (k-1)d) x (w - (k-1)d). Each output element accumulates its terms in the order
+ * (ci, ky, kx), starting from the bias.
  */
-int oracle_conv(const double* x, int64_t cin, int64_t h, int64_t w, const double* W, const double* b,
-                int64_t cout, int64_t k, int relu, double* y) {
-    if (!x || !W || !b || !y || cin < 1 || cout < 1 || k < 1 || h < k || w < k) return OR_ERR_ARG;
-    int64_t oh = h - k + 1, ow = w - k + 1;
+int oracle_conv_dil(const double* x, int64_t cin, int64_t h, int64_t w, const double* W, const double* b,
+                    int64_t cout, int64_t k, int64_t dil, int relu, double* y) {
+    if (!x || !W || !b || !y || cin < 1 || cout < 1 || k < 1 || dil < 1) return OR_ERR_ARG;
+    const int64_t span = (k - 1) * dil;
+    if (h <= span || w <= span) return OR_ERR_ARG;
+    int64_t oh = h - span, ow = w - span;
 #pragma omp parallel for schedule(static)
     for (int64_t co = 0; co < cout; ++co) {
         double* yc = y + co * oh * ow;
@@ -61,7 +74,7 @@ int oracle_conv(const double* x, int64_t cin, int64_t h, int64_t w, const double
             for (int64_t ky = 0; ky < k; ++ky)
                 for (int64_t kx = 0; kx < k; ++kx) {
                     double wt = W[((co * cin + ci) * k + ky) * k + kx];
-                    const double* xs = x + (ci * h + ky) * w + kx;
+                    const double* xs = x + (ci * h + ky * dil) * w + kx * dil;
                     for (int64_t i = 0; i < oh; ++i)
                         for (int64_t j = 0; j < ow; ++j) yc[i * ow + j] += wt * xs[i * w + j];
                 }
@@ -71,20 +84,44 @@ int oracle_conv(const double* x, int64_t cin, int64_t h, int64_t w, const double
     return OR_OK;
 }
 
-/* 2x2 stride-1 max-filter, valid: y[c][i][j] = max of x[c][i..i+1][j..j+1]; y is c x (h-1) x (w-1). */
-int oracle_maxfilter2(const double* x, int64_t c, int64_t h, int64_t w, double* y) {
-    if (!x || !y || c < 1 || h < 2 || w < 2) return OR_ERR_ARG;
-    int64_t oh = h - 1, ow = w - 1;
+/* Valid cross-correlation without dilation (see oracle_conv_dil). */
+int oracle_conv(const double* x, int64_t cin, int64_t h, int64_t w, const double* W, const double* b,
+                int64_t cout, int64_t k, int relu, double* y) {
+    return oracle_conv_dil(x, cin, h, w, W, b, cout, k, 1, relu, y);
+}
+
+/* 2x2 stride-1 max-filter with dilation d, valid: y[c][i][j] = max of x[c][i + {0,d}][j + {0,d}];
+ * y is c x (h-d) x (w-d). */
+int oracle_maxfilter2_dil(const double* x, int64_t c, int64_t h, int64_t w, int64_t d, double* y) {
+    if (!x || !y || c < 1 || d < 1 || h <= d || w <= d) return OR_ERR_ARG;
+    int64_t oh = h - d, ow = w - d;
     for (int64_t ch = 0; ch < c; ++ch)
         for (int64_t i = 0; i < oh; ++i)
             for (int64_t j = 0; j < ow; ++j) {
                 const double* p = x + (ch * h + i) * w + j;
                 double m = p[0];
-                if (p[1] > m) m = p[1];
-                if (p[w] > m) m = p[w];
-                if (p[w + 1] > m) m = p[w + 1];
+                if (p[d] > m) m = p[d];
+                if (p[d * w] > m) m = p[d * w];
+                if (p[d * w + d] > m) m = p[d * w + d];
                 y[(ch * oh + i) * ow + j] = m;
             }
+    return OR_OK;
+}
+
+int oracle_maxfilter2(const double* x, int64_t c, int64_t h, int64_t w, double* y) {
+    return oracle_maxfilter2_dil(x, c, h, w, 1, y);
+}
+
+/* Max-out: y[c] = max over g < G of x[c*G + g]; x has c_out*G channels, y has c_out. */
+int oracle_maxout(const double* x, int64_t c_out, int64_t G, int64_t hw, double* y) {
+    if (!x || !y || c_out < 1 || G < 1 || hw < 1) return OR_ERR_ARG;
+    for (int64_t c = 0; c < c_out; ++c)
+        for (int64_t i = 0; i < hw; ++i) {
+            double m = x[(c * G) * hw + i];
+            for (int64_t g = 1; g < G; ++g)
+                if (x[(c * G + g) * hw + i] > m) m = x[(c * G + g) * hw + i];
+            y[c * hw + i] = m;
+        }
     return OR_OK;
 }
 
@@ -100,10 +137,13 @@ int oracle_head_sigmoid(const double* x, int64_t c, int64_t h, int64_t w, const 
     return OR_OK;
 }
 
-/* Sum over layers of the size each one removes: (k - 1) for convs and max-filters. */
+static int64_t dil_of(const int32_t* d) { return d[5] > 0 ? d[5] : 1; }
+static int64_t groups_of(const int32_t* d) { return d[6] > 0 ? d[6] : 1; }
+
+/* Sum over layers of the size each one removes: (k - 1) d for convs and max-filters. */
 static int64_t net_shrink(const int32_t* desc, int n_layers) {
     int64_t s = 0;
-    for (int l = 0; l < n_layers; ++l) s += desc[5 * l + 1] - 1;
+    for (int l = 0; l < n_layers; ++l) s += (int64_t)(desc[OR_DW * l + 1] - 1) * dil_of(desc + OR_DW * l);
     return s;
 }
 
@@ -115,8 +155,9 @@ int64_t oracle_net_radius(const int32_t* desc, int n_layers) {
 int64_t oracle_param_count(const int32_t* desc, int n_layers) {
     int64_t n = 0;
     for (int l = 0; l < n_layers; ++l) {
-        const int32_t* d = desc + 5 * l;
-        if (d[0] == OR_CONV || d[0] == OR_HEAD) n += (int64_t)d[3] * d[2] * d[1] * d[1] + d[3];
+        const int32_t* d = desc + OR_DW * l;
+        const int64_t co = (int64_t)d[3] * groups_of(d);
+        if (d[0] == OR_CONV || d[0] == OR_HEAD || d[0] == OR_SOFTMAX) n += co * d[2] * d[1] * d[1] + co;
     }
     return n;
 }
@@ -151,31 +192,52 @@ int oracle_run_layers(const int32_t* desc, int n_layers, const double* params, c
     const double* prm = params;
     int rc = OR_OK;
     for (int l = 0; l < n_layers && rc == OR_OK; ++l) {
-        const int32_t* d = desc + 5 * l;
-        int64_t k = d[1], cin = d[2], cout = d[3];
-        if (d[0] == OR_CONV) {
-            if (cin != c || h < k || w < k) { rc = OR_ERR_ARG; break; }
-            int64_t oh = h - k + 1, ow = w - k + 1;
-            double* nxt = (double*)malloc(sizeof(double) * (size_t)(cout * oh * ow));
-            if (!nxt) { rc = OR_ERR_OOM; break; }
-            rc = oracle_conv(cur, cin, h, w, prm, prm + cout * cin * k * k, cout, k, d[4], nxt);
-            prm += cout * cin * k * k + cout;
-            free(cur); cur = nxt; c = cout; h = oh; w = ow;
+        const int32_t* d = desc + OR_DW * l;
+        const int64_t k = d[1], cin = d[2], cout = d[3], dl = dil_of(d), G = groups_of(d);
+        const int last = l == n_layers - 1;
+        if (d[0] == OR_CONV || d[0] == OR_SOFTMAX) {
+            const int64_t span = (k - 1) * dl, cg = cout * G;
+            if (cin != c || h <= span || w <= span) { rc = OR_ERR_ARG; break; }
+            if (d[0] == OR_SOFTMAX && (cout != 2 || G != 1 || !last)) { rc = OR_ERR_ARG; break; }
+            int64_t oh = h - span, ow = w - span;
+            double* full = (double*)malloc(sizeof(double) * (size_t)(cg * oh * ow));
+            if (!full) { rc = OR_ERR_OOM; break; }
+            rc = oracle_conv_dil(cur, cin, h, w, prm, prm + cg * cin * k * k, cg, k, dl, d[4], full);
+            prm += cg * cin * k * k + cg;
+            free(cur);
+            if (rc == OR_OK && d[0] == OR_SOFTMAX) {
+                for (int64_t i = 0; i < oh * ow; ++i) p[i] = 1.0 / (1.0 + exp(full[i] - full[oh * ow + i]));
+                free(full);
+                cur = NULL;
+                c = 1; h = oh; w = ow;
+                continue;
+            }
+            if (rc == OR_OK && G > 1) {
+                double* mo = (double*)malloc(sizeof(double) * (size_t)(cout * oh * ow));
+                if (!mo) { free(full); rc = OR_ERR_OOM; cur = NULL; break; }
+                rc = oracle_maxout(full, cout, G, oh * ow, mo);
+                free(full);
+                full = mo;
+            }
+            cur = full; c = cout; h = oh; w = ow;
         } else if (d[0] == OR_MAXF) {
-            if (k != 2 || h < 2 || w < 2) { rc = OR_ERR_ARG; break; }
-            double* nxt = (double*)malloc(sizeof(double) * (size_t)(c * (h - 1) * (w - 1)));
+            if (k != 2 || h <= dl || w <= dl) { rc = OR_ERR_ARG; break; }
+            double* nxt = (double*)malloc(sizeof(double) * (size_t)(c * (h - dl) * (w - dl)));
             if (!nxt) { rc = OR_ERR_OOM; break; }
-            rc = oracle_maxfilter2(cur, c, h, w, nxt);
-            free(cur); cur = nxt; h -= 1; w -= 1;
+            rc = oracle_maxfilter2_dil(cur, c, h, w, dl, nxt);
+            free(cur); cur = nxt; h -= dl; w -= dl;
         } else if (d[0] == OR_HEAD) {
-            if (cin != c || cout != 1 || k != 1 || l != n_layers - 1) { rc = OR_ERR_ARG; break; }
+            if (cin != c || cout != 1 || k != 1 || !last) { rc = OR_ERR_ARG; break; }
             rc = oracle_head_sigmoid(cur, c, h, w, prm, prm[c], p);
             prm += c + 1;
         } else {
             rc = OR_ERR_ARG;
         }
     }
-    if (rc == OR_OK && desc[5 * (n_layers - 1)] != OR_HEAD) rc = OR_ERR_ARG;
+    {
+        const int kind = desc[OR_DW * (n_layers - 1)];
+        if (rc == OR_OK && kind != OR_HEAD && kind != OR_SOFTMAX) rc = OR_ERR_ARG;
+    }
     free(cur);
     return rc;
 }
@@ -236,8 +298,9 @@ int oracle_maxfilter_amax(const int32_t* desc, int n_layers, const double* param
     int64_t c = 1, hh = ph, ww = pw, m = 0;
     const double* prm = params;
     for (int l = 0; l < n_layers && rc == OR_OK; ++l) {
-        const int32_t* d = desc + 5 * l;
+        const int32_t* d = desc + OR_DW * l;
         int64_t k = d[1], cin = d[2], cout = d[3];
+        if (dil_of(d) != 1 || groups_of(d) != 1) { rc = OR_ERR_ARG; break; }
         if (d[0] == OR_CONV) {
             int64_t oh = hh - k + 1, ow = ww - k + 1;
             double* nxt = (double*)malloc(sizeof(double) * (size_t)(cout * oh * ow));
@@ -287,11 +350,11 @@ int oracle_student_loss_grad(const int32_t* desc, int n_layers, const double* pa
     int64_t R = oracle_net_radius(desc, n_layers);
     if (R < 0) return OR_ERR_ARG;
     for (int l = 0; l < n_layers; ++l) {
-        int kind = desc[5 * l];
-        if (kind == OR_MAXF) return OR_ERR_ARG;
+        int kind = desc[OR_DW * l];
+        if (kind == OR_MAXF || dil_of(desc + OR_DW * l) != 1 || groups_of(desc + OR_DW * l) != 1) return OR_ERR_ARG;
         if (kind == OR_HEAD && l != n_layers - 1) return OR_ERR_ARG;
     }
-    if (desc[5 * (n_layers - 1)] != OR_HEAD) return OR_ERR_ARG;
+    if (desc[OR_DW * (n_layers - 1)] != OR_HEAD) return OR_ERR_ARG;
     int64_t np = oracle_param_count(desc, n_layers);
     memset(grad, 0, sizeof(double) * (size_t)np);
     double N = (double)(n * H * W);
@@ -304,7 +367,7 @@ int oracle_student_loss_grad(const int32_t* desc, int n_layers, const double* pa
         int64_t o = 0;
         for (int l = 0; l < n_layers; ++l) {
             off[l] = o;
-            const int32_t* d = desc + 5 * l;
+            const int32_t* d = desc + OR_DW * l;
             o += (int64_t)d[3] * d[2] * d[1] * d[1] + d[3];
         }
     }
@@ -321,7 +384,7 @@ int oracle_student_loss_grad(const int32_t* desc, int n_layers, const double* pa
         if (!acts[0]) { rc = OR_ERR_OOM; break; }
         oracle_pad_region(in + s * spitch, H, W, pitch, 0, 0, H, W, R, acts[0]);
         for (int l = 0; l < n_layers - 1 && rc == OR_OK; ++l) {
-            const int32_t* d = desc + 5 * l;
+            const int32_t* d = desc + OR_DW * l;
             int64_t k = d[1], cin = d[2], cout = d[3];
             int64_t oh = ah[l] - k + 1, ow = aw[l] - k + 1;
             pre[l] = (double*)malloc(sizeof(double) * (size_t)(cout * oh * ow));
@@ -334,7 +397,7 @@ int oracle_student_loss_grad(const int32_t* desc, int n_layers, const double* pa
             ac[l + 1] = cout; ah[l + 1] = oh; aw[l + 1] = ow;
         }
         int L = n_layers - 1; /* head index */
-        if (rc == OR_OK && (ah[L] != H || aw[L] != W || ac[L] != desc[5 * L + 2])) rc = OR_ERR_ARG;
+        if (rc == OR_OK && (ah[L] != H || aw[L] != W || ac[L] != desc[OR_DW * L + 2])) rc = OR_ERR_ARG;
         double* dcur = NULL;
         if (rc == OR_OK) {
             int64_t C = ac[L];
@@ -357,7 +420,7 @@ int oracle_student_loss_grad(const int32_t* desc, int n_layers, const double* pa
             }
         }
         for (int l = L - 1; l >= 0 && rc == OR_OK; --l) {
-            const int32_t* d = desc + 5 * l;
+            const int32_t* d = desc + OR_DW * l;
             int64_t k = d[1], cin = d[2], cout = d[3];
             int64_t ih = ah[l], iw = aw[l], oh = ah[l + 1], ow = aw[l + 1];
             const double* Wl = params + off[l];

@@ -21,9 +21,9 @@ _lock = threading.Lock()
 _lib = None
 
 # Layer kinds of the workload descriptions (same numbering as the library's mb_layer_kind).
-CONV, MAXFILTER, HEAD_SIGMOID = 0, 1, 2
+CONV, MAXFILTER, HEAD_SIGMOID, HEAD_SOFTMAX2 = 0, 1, 2, 3
 
-# (kind, ksize, cin, cout, relu)
+# (kind, ksize, cin, cout, relu[, dilation[, maxout groups]]); dilation and groups default to 1.
 # The measured stand-in network: conv5x5 1->32 ReLU, 2x2 stride-1 max-filter, conv5x5 32->32
 # ReLU, max-filter, conv5x5 32->32 ReLU, conv1x1 32->1 sigmoid (receptive field 15x15).
 TEACHER = (
@@ -41,8 +41,22 @@ STUDENT = (
     (HEAD_SIGMOID, 1, 16, 1, 0),
 )
 
+# FastMemb (Sec. 2.2) in dense form: three [conv4x4 -> max-out over 2 -> 2x2 max-filter] stages
+# whose stride-2 pooling has become dilation 1, 2, 4, then conv4x4 with dilation 8 to 2 classes
+# and a softmax; no ReLU. Field of view 53x53, 67,778 parameters.
+FASTMEMB = (
+    (CONV, 4, 1, 32, 0, 1, 2),
+    (MAXFILTER, 2, 32, 32, 0, 1, 1),
+    (CONV, 4, 32, 32, 0, 2, 2),
+    (MAXFILTER, 2, 32, 32, 0, 2, 1),
+    (CONV, 4, 32, 32, 0, 4, 2),
+    (MAXFILTER, 2, 32, 32, 0, 4, 1),
+    (HEAD_SOFTMAX2, 4, 32, 2, 0, 8, 1),
+)
+
 TEACHER_WEIGHT_SEED = 20161206
 STUDENT_WEIGHT_SEED = 20161207
+FASTMEMB_WEIGHT_SEED = 20161208
 BASE_SEED = 1612021200  # + workload index
 
 
@@ -130,22 +144,31 @@ def uniform_floats(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
     return out
 
 
+def _groups(layer) -> int:
+    return int(layer[6]) if len(layer) > 6 else 1
+
+
 def param_count(layers) -> int:
     n = 0
-    for kind, k, cin, cout, _ in layers:
-        if kind in (CONV, HEAD_SIGMOID):
-            n += cout * cin * k * k + cout
+    for layer in layers:
+        kind, k, cin, cout = layer[:4]
+        if kind in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2):
+            co = cout * _groups(layer)
+            n += co * cin * k * k + co
     return n
 
 
 def init_params(layers, seed: int, bias_std: float = 0.01) -> np.ndarray:
-    """He-normal FP32 parameters for `layers`, packed per parameterised layer as W[cout][cin][k][k]
-    then b[cout]; parameterised layer number l draws from seed + l. bias_std 0 gives zero biases."""
+    """He-normal FP32 parameters for `layers`, packed per parameterised layer as
+    W[cout*G][cin][k][k] then b[cout*G] (G max-out groups); parameterised layer number l draws
+    from seed + l. bias_std 0 gives zero biases."""
     parts = []
     l = 0
-    for kind, k, cin, cout, _ in layers:
-        if kind in (CONV, HEAD_SIGMOID):
-            w, b = he_normal(seed + l, cin * k * k, cout * cin * k * k, cout, bias_std)
+    for layer in layers:
+        kind, k, cin, cout = layer[:4]
+        if kind in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2):
+            co = cout * _groups(layer)
+            w, b = he_normal(seed + l, cin * k * k, co * cin * k * k, co, bias_std)
             parts += [w, b]
             l += 1
     return np.concatenate(parts).astype(np.float32)

@@ -19,8 +19,10 @@ def teacher_params(seed=synth.TEACHER_WEIGHT_SEED):
 def split_params(layers, params):
     """Unpack a flat parameter vector into [(W, b)] per parameterised layer."""
     out, o = [], 0
-    for kind, k, cin, cout, _ in layers:
-        if kind in (synth.CONV, synth.HEAD_SIGMOID):
+    for layer in layers:
+        kind, k, cin, cout = layer[:4]
+        if kind in (synth.CONV, synth.HEAD_SIGMOID, synth.HEAD_SOFTMAX2):
+            cout *= layer[6] if len(layer) > 6 else 1
             n = cout * cin * k * k
             out.append((params[o:o + n].reshape(cout, cin, k, k), params[o + n:o + n + cout]))
             o += n + cout
