@@ -21,7 +21,8 @@
  *    asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream). Calls given
  *    host pointers are synchronous on return.
  *  - Sizes are element counts; pitches are in elements of the buffer's type.
- *  - Slices need h >= 8 and w >= 8 so reflect-101 padding by 7 is defined; else MB_ERR_SHAPE.
+ *  - Slices need h and w above the net's radius so reflect-101 padding is defined (>= 8 for the
+ *    teacher and student, >= 27 for FastMemb); else MB_ERR_SHAPE.
  *  - A net/precision combination without a kernel returns MB_ERR_UNSUPPORTED.
  *  - Host-side fault injection for tests: environment MB_FAULT_OOM=1 makes every library
  *    allocation fail with MB_ERR_OOM.
@@ -51,18 +52,27 @@ typedef enum {
 
 typedef enum { MB_PREC_FP32 = 0, MB_PREC_BF16 = 1, MB_PREC_FP8 = 2 } mb_precision;
 typedef enum { MB_OUT_F32 = 0, MB_OUT_U8 = 1 } mb_out_type;
-typedef enum { MB_CONV = 0, MB_MAXFILTER = 1, MB_HEAD_SIGMOID = 2 } mb_layer_kind;
+typedef enum { MB_CONV = 0, MB_MAXFILTER = 1, MB_HEAD_SIGMOID = 2, MB_HEAD_SOFTMAX2 = 3 } mb_layer_kind;
 
 /*
- * One layer of a network description (Sec. 2.2 describes the network in prose as alternating
- * convolution / max-filter layers).
- *   MB_CONV:         ksize x ksize valid cross-correlation cin -> cout, + bias, ReLU if relu.
- *   MB_MAXFILTER:    ksize x ksize stride-1 max over each channel (cin == cout).
- *   MB_HEAD_SIGMOID: 1x1 cin -> 1, + bias, sigmoid; must be the last layer.
- * dilation must be 1 and maxout_groups 1 (0 is read as 1) in this version.
+ * One layer of a network description (Sec. 2.2 describes the networks in prose as alternating
+ * convolution / max-pooling layers, which dense computation turns into max-filters).
+ *   MB_CONV:          ksize x ksize valid cross-correlation cin -> cout*G with dilation d
+ *                     (y[i][j] = b + sum W[ky][kx] x[i + d ky][j + d kx]), + bias, ReLU if relu,
+ *                     then max-out over G = maxout_groups adjacent channels (channel c of the
+ *                     output is the max of conv channels c*G .. c*G + G-1). Parameters
+ *                     W[cout*G][cin][k][k] then b[cout*G].
+ *   MB_MAXFILTER:     2x2 stride-1 max over each channel at offsets {0, d} x {0, d} (cin == cout).
+ *   MB_HEAD_SIGMOID:  1x1 cin -> 1, + bias, sigmoid; must be the last layer.
+ *   MB_HEAD_SOFTMAX2: ksize x ksize cross-correlation with dilation d, cin -> 2, + bias, then the
+ *                     2-class softmax's class-1 probability 1 / (1 + exp(z0 - z1)); last layer.
+ * dilation and maxout_groups 0 are read as 1.
  * Supported networks: the teacher (conv5x5 1->32 ReLU, maxfilter 2, conv5x5 32->32 ReLU,
- * maxfilter 2, conv5x5 32->32 ReLU, head 32->1) in FP32, BF16 and FP8, and the student
- * (conv3x3 1->16 ReLU, conv3x3 16->16 ReLU, head 16->1) in FP32 and BF16.
+ * maxfilter 2, conv5x5 32->32 ReLU, head 32->1) in FP32, BF16 and FP8; the student (conv3x3
+ * 1->16 ReLU, conv3x3 16->16 ReLU, head 16->1) in FP32 and BF16; and FastMemb in dense form
+ * (Sec. 2.2: conv4x4 1->32 G=2 d=1, maxfilter d=1, conv4x4 32->32 G=2 d=2, maxfilter d=2,
+ * conv4x4 32->32 G=2 d=4, maxfilter d=4, softmax head conv4x4 32->2 d=8; no ReLU; radius 26,
+ * so its slices need h, w >= 27) in FP32.
  */
 typedef struct {
     int32_t kind, ksize, dilation, cin, cout, relu, maxout_groups;

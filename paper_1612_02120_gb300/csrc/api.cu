@@ -108,7 +108,19 @@ static bool same_layer(const mb_layer_desc& a, int kind, int k, int cin, int cou
            dil == 1 && mo == 1;
 }
 
+static bool same_layer_dm(const mb_layer_desc& a, int kind, int k, int cin, int cout, int dil, int groups) {
+    const int d = a.dilation == 0 ? 1 : a.dilation;
+    const int mo = a.maxout_groups == 0 ? 1 : a.maxout_groups;
+    return a.kind == kind && a.ksize == k && a.cin == cin && a.cout == cout && a.relu == 0 && d == dil &&
+           mo == groups;
+}
+
 static int detect_family(const mb_layer_desc* L, int n) {
+    if (n == 7 && same_layer_dm(L[0], MB_CONV, 4, 1, 32, 1, 2) && same_layer_dm(L[1], MB_MAXFILTER, 2, 32, 32, 1, 1) &&
+        same_layer_dm(L[2], MB_CONV, 4, 32, 32, 2, 2) && same_layer_dm(L[3], MB_MAXFILTER, 2, 32, 32, 2, 1) &&
+        same_layer_dm(L[4], MB_CONV, 4, 32, 32, 4, 2) && same_layer_dm(L[5], MB_MAXFILTER, 2, 32, 32, 4, 1) &&
+        same_layer_dm(L[6], MB_HEAD_SOFTMAX2, 4, 32, 2, 8, 1))
+        return FAMILY_FASTMEMB;
     if (n == 6 && same_layer(L[0], MB_CONV, 5, 1, 32, 1) && same_layer(L[1], MB_MAXFILTER, 2, 32, 32, 0) &&
         same_layer(L[2], MB_CONV, 5, 32, 32, 1) && same_layer(L[3], MB_MAXFILTER, 2, 32, 32, 0) &&
         same_layer(L[4], MB_CONV, 5, 32, 32, 1) && same_layer(L[5], MB_HEAD_SIGMOID, 1, 32, 1, 0))
@@ -140,6 +152,26 @@ static mb_status check_ready(const mb_net* net) {
     if (net->prec == MB_PREC_FP8 && !net->calibrated) {
         set_error("FP8 net not calibrated (call mb_calibrate_fp8 first)");
         return MB_ERR_NOT_READY;
+    }
+    return MB_OK;
+}
+
+static int net_radius(const mb_net* net) {
+    if (!net) return kTeacherRadius;
+    switch (net->family) {
+        case FAMILY_STUDENT: return kStudentRadius;
+        case FAMILY_FASTMEMB: return kFastMembRadius;
+        default: return kTeacherRadius;
+    }
+}
+
+// A slice must be larger than the net's radius for reflect-101 padding.
+static mb_status check_net_slice(const mb_net* net, int64_t h, int64_t w) {
+    const int R = net_radius(net);
+    if (h <= R || w <= R) {
+        set_error("slice %lldx%lld: this net's radius is %d, so h and w must be >= %d", (long long)h, (long long)w,
+                  R, R + 1);
+        return MB_ERR_SHAPE;
     }
     return MB_OK;
 }
@@ -183,6 +215,8 @@ mb_status teacher_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, i
 
 static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,
                             int64_t x0, int64_t rows, int64_t cols, void* out, mb_out_type ot, cudaStream_t st) {
+    if (net->family == FAMILY_FASTMEMB)
+        return simt_fastmemb_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
     if (net->family == FAMILY_TEACHER)
         return teacher_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
     if (z == 0) return MB_OK;
@@ -318,7 +352,7 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
     }
     for (int i = 0; i < n_layers; ++i) {
         const mb_layer_desc& L = layers[i];
-        if (L.kind < MB_CONV || L.kind > MB_HEAD_SIGMOID || L.ksize <= 0 || L.cin <= 0 || L.cout <= 0 ||
+        if (L.kind < MB_CONV || L.kind > MB_HEAD_SOFTMAX2 || L.ksize <= 0 || L.cin <= 0 || L.cout <= 0 ||
             L.dilation < 0 || L.maxout_groups < 0) {
             set_error("mb_net_create: layer %d is malformed", i);
             return MB_ERR_INVALID_ARG;
@@ -326,11 +360,15 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
     }
     const int fam = detect_family(layers, n_layers);
     if (!fam) {
-        set_error("mb_net_create: no kernel for this layer stack (teacher 5x5/32 or student 3x3/16 only)");
+        set_error("mb_net_create: no kernel for this layer stack (teacher 5x5/32, student 3x3/16 or FastMemb only)");
         return MB_ERR_UNSUPPORTED;
     }
     if (fam == FAMILY_STUDENT && prec == MB_PREC_FP8) {
         set_error("mb_net_create: the student runs in FP32 or BF16");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (fam == FAMILY_FASTMEMB && prec != MB_PREC_FP32) {
+        set_error("mb_net_create: FastMemb runs in FP32");
         return MB_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -350,7 +388,10 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
     net->layers.assign(layers, layers + n_layers);
     int64_t np = 0;
     for (const auto& L : net->layers)
-        if (L.kind != MB_MAXFILTER) np += (int64_t)L.cout * L.cin * L.ksize * L.ksize + L.cout;
+        if (L.kind != MB_MAXFILTER) {
+            const int64_t co = (int64_t)L.cout * (L.maxout_groups > 1 ? L.maxout_groups : 1);
+            np += co * L.cin * L.ksize * L.ksize + co;
+        }
     net->n_params = np;
     {
         DeviceGuard g(device);
@@ -505,6 +546,7 @@ mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
         return MB_ERR_INVALID_ARG;
     }
     MB_TRY(check_slice(z, h, w));
+    MB_TRY(check_net_slice(net, h, w));
     if (z == 0) return MB_OK;
     API_GUARD(net)
     const bool din = is_device_ptr(in), dout = is_device_ptr(out);
@@ -529,6 +571,7 @@ mb_status mb_infer_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
         return MB_ERR_INVALID_ARG;
     }
     MB_TRY(check_slice(z, h, w));
+    MB_TRY(check_net_slice(net, h, w));
     if (y0 < 0 || x0 < 0 || rows < 0 || cols < 0 || y0 + rows > h || x0 + cols > w) {
         set_error("mb_infer_region: region [%lld,+%lld) x [%lld,+%lld) outside the %lldx%lld slice",
                   (long long)y0, (long long)rows, (long long)x0, (long long)cols, (long long)h, (long long)w);
@@ -559,6 +602,7 @@ static mb_status check_blocks(const mb_net* net, const mb_block* blocks, int32_t
     for (int i = 0; i < n; ++i) {
         const mb_block& b = blocks[i];
         mb_status s = check_slice(b.z, b.h, b.w);
+        if (s == MB_OK) s = check_net_slice(net, b.h, b.w);
         if (s != MB_OK) {
             set_error("block %d: %s", i, mb_last_error());
             return s;
@@ -573,7 +617,6 @@ static mb_status check_blocks(const mb_net* net, const mb_block* blocks, int32_t
             return MB_ERR_INVALID_ARG;
         }
     }
-    (void)net;
     return MB_OK;
 }
 
@@ -589,6 +632,9 @@ mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t 
         if (net->family == FAMILY_TEACHER) {
             MB_TRY(teacher_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w, b.out,
                                   b.out_pitch, b.out_slice_pitch, out_type, st));
+        } else if (net->family == FAMILY_FASTMEMB) {
+            MB_TRY(simt_fastmemb_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w,
+                                        b.out, b.out_pitch, b.out_slice_pitch, out_type, st));
         } else if (b.z > 0) {
             MB_TRY(simt_student_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w,
                                        b.out, b.out_pitch, b.out_slice_pitch, out_type, st));

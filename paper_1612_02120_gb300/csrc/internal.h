@@ -12,7 +12,7 @@
 
 namespace mb {
 
-enum Family { FAMILY_TEACHER = 1, FAMILY_STUDENT = 2 };
+enum Family { FAMILY_TEACHER = 1, FAMILY_STUDENT = 2, FAMILY_FASTMEMB = 3 };
 
 // Teacher geometry: conv5x5 x3 with two 2x2 max-filters -> receptive radius 7.
 constexpr int kTeacherRadius = 7;
@@ -20,6 +20,9 @@ constexpr int kTeacherC = 32;
 // Student geometry: conv3x3 x2 -> radius 2.
 constexpr int kStudentRadius = 2;
 constexpr int kStudentC = 16;
+// FastMemb dense form: conv4x4 (dilation 1, 2, 4) with max-out 2, max-filters (1, 2, 4), conv4x4
+// dilation 8 -> radius 26 (53x53 field of view).
+constexpr int kFastMembRadius = 26;
 
 void set_error(const char* fmt, ...);
 void clear_error();
@@ -90,6 +93,10 @@ mb_status simt_student_region(mb_net* net, const uint8_t* in, int64_t z, int64_t
                               int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
                               int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
                               mb_out_type ot, cudaStream_t st);
+mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
+                               int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
+                               int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
+                               mb_out_type ot, cudaStream_t st);
 // FP32 teacher activations after the two max-filters: per-channel amax over n slices (device out[64]).
 mb_status simt_teacher_amax(mb_net* net, const uint8_t* in, int64_t n, int64_t h, int64_t w, float* d_amax,
                             cudaStream_t st);

@@ -46,8 +46,8 @@ void simt_pack(const mb_net* net, const float* params, std::vector<float>& out) 
     out.clear();
     const float* p = params;
     for (const mb_layer_desc& L : net->layers) {
-        if (L.kind == MB_CONV) {
-            const int k = L.ksize, ci = L.cin, co = L.cout;
+        if (L.kind == MB_CONV || L.kind == MB_HEAD_SOFTMAX2) {
+            const int k = L.ksize, ci = L.cin, co = L.cout * (L.maxout_groups > 1 ? L.maxout_groups : 1);
             size_t base = out.size();
             out.resize(base + (size_t)ci * k * k * co + co);
             for (int o = 0; o < co; ++o)

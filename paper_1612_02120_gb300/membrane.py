@@ -16,7 +16,7 @@ MB_OK, MB_ERR_INVALID_ARG, MB_ERR_SHAPE, MB_ERR_OOM, MB_ERR_CUDA, MB_ERR_TIMEOUT
     MB_ERR_UNSUPPORTED = range(8)
 MB_PREC_FP32, MB_PREC_BF16, MB_PREC_FP8 = 0, 1, 2
 MB_OUT_F32, MB_OUT_U8 = 0, 1
-MB_CONV, MB_MAXFILTER, MB_HEAD_SIGMOID = 0, 1, 2
+MB_CONV, MB_MAXFILTER, MB_HEAD_SIGMOID, MB_HEAD_SOFTMAX2 = 0, 1, 2, 3
 
 EXPORTED = (
     "mb_net_create", "mb_net_destroy", "mb_net_param_count", "mb_load_weights", "mb_get_weights",
@@ -127,10 +127,13 @@ def stream_handle(stream) -> int | None:
 
 
 def layer_array(layers):
-    """layers: iterable of (kind, ksize, cin, cout, relu) tuples."""
+    """layers: iterable of (kind, ksize, cin, cout, relu[, dilation[, maxout groups]]) tuples."""
     arr = (mb_layer_desc * len(layers))()
-    for i, (kind, k, cin, cout, relu) in enumerate(layers):
-        arr[i] = mb_layer_desc(kind, k, 1, cin, cout, relu, 1)
+    for i, layer in enumerate(layers):
+        kind, k, cin, cout, relu = layer[:5]
+        dil = layer[5] if len(layer) > 5 else 1
+        groups = layer[6] if len(layer) > 6 else 1
+        arr[i] = mb_layer_desc(kind, k, dil, cin, cout, relu, groups)
     return arr
 
 
