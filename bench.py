@@ -12,7 +12,9 @@ the same through the C ABI with pinned HOST buffers (copies inside the timed reg
   cfg3  4096x4096x64 FP8 (calibrated on 4 slices) and BF16, resident and streamed from pinned host
         memory; errors on 3 seeded 512x512 crops (true context);
   cfg4  student training (200 x 512^2, batch 32, lr 1e-3, 2000 steps) on FP32-teacher maps, then
-        student-only and cascade (teacher fallback on 256^2 tiles) on the cfg3 volume.
+        student-only and cascade (teacher fallback on 256^2 tiles) on the cfg3 volume;
+  cfg5  FastMemb in dense form (Sec. 2.2) on the cfg1 volume, with errors against the oracle on 3
+        seeded 384x384 crops (true context).
 The reference arm (--impl reference) is the FP64 CPU oracle on bounded samples.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--configs 1,2,3,4]
@@ -37,6 +39,7 @@ WORKLOAD = "1024x1024x32 uint8 synthetic EM volume (32 independent slices), stan
 FLOP_PER_PX = 2 * (25 * 32 + 2 * 25 * 32 * 32 + 32)        # 104,064
 TENSOR_FLOP_PER_PX = 2 * 2 * 25 * 32 * 32                   # 102,400 (layers 2 and 3)
 STUDENT_FLOP_PER_PX = 2 * (9 * 16 + 9 * 16 * 16 + 16)       # 4,928
+FASTMEMB_FLOP_PER_PX = 2 * (16 * 64 + 2 * 16 * 32 * 64 + 16 * 32 * 2)  # 135,168
 # DRAM bytes per output voxel of tc_fused_teacher (BF16), from the ncu capture summarised in
 # profiles/tc_fused_teacher_bf16_1024x1024x4.md; None when the kernel changed since.
 TC_TRAFFIC_PER_VOX = None
@@ -189,7 +192,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--configs", default="1,2,3,4", help="extra configurations measured after the headline")
+    ap.add_argument("--configs", default="1,2,3,4,5", help="extra configurations measured after the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -443,6 +446,27 @@ def main():
         student.close()
         untrained.close()
         teacher.close()
+    # ---- cfg5: FastMemb dense form on the cfg1 volume ------------------------------------------------
+    if "5" in configs:
+        fm_params = synth.init_params(synth.FASTMEMB, synth.FASTMEMB_WEIGHT_SEED)
+        rng = np.random.default_rng(synth.BASE_SEED + 5)
+        crops = [(int(rng.integers(0, Z)), int(rng.integers(0, H - 384)), int(rng.integers(0, W - 384)))
+                 for _ in range(3)]
+        refs = [oracle.forward_region(synth.FASTMEMB, fm_params, vol[z], y, x0, 384, 384) for z, y, x0 in crops]
+        p = {"crops_384": crops}
+        for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16)):
+            fm = m.Net(synth.FASTMEMB, prec, local, fm_params)
+            with torch.cuda.stream(stream):
+                ms = time_device(lambda: m.mb_infer_volume(fm.handle, x, Z, H, W, out, m.MB_OUT_F32, stream),
+                                 3 if name == "fp32" else args.steps, 1 if name == "fp32" else 3, stream, flush)
+            got = [out[z, y:y + 384, x0:x0 + 384].cpu().numpy() for z, y, x0 in crops]
+            mv = vox / (statistics.mean(ms) / 1e3) / 1e6
+            p[name] = {"mvox_s": mv, "ms": statistics.mean(ms),
+                       "tflops": FASTMEMB_FLOP_PER_PX * mv * 1e6 / 1e12,
+                       "error": err_metrics(got, refs, TOL[name])}
+            fm.close()
+        p["bf16"]["speedup_vs_fp32"] = p["bf16"]["mvox_s"] / p["fp32"]["mvox_s"]
+        paths["cfg5_fastmemb_1024x1024x32"] = p
     if paths:
         line["paths"] = paths
     if rank == 0 and not args.no_cpu_baseline:

@@ -213,10 +213,20 @@ mb_status teacher_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, i
     return tc_infer_blocks(net, &b, 1, &y0, &x0, &rows, &cols, ot, st, false);
 }
 
+static mb_status fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+                                 int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
+                                 int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st) {
+    if (net->prec == MB_PREC_BF16)
+        return bf16_fastmemb_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch,
+                                    out_slice, ot, st);
+    return simt_fastmemb_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch, out_slice,
+                                ot, st);
+}
+
 static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,
                             int64_t x0, int64_t rows, int64_t cols, void* out, mb_out_type ot, cudaStream_t st) {
     if (net->family == FAMILY_FASTMEMB)
-        return simt_fastmemb_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
+        return fastmemb_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
     if (net->family == FAMILY_TEACHER)
         return teacher_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
     if (z == 0) return MB_OK;
@@ -367,8 +377,8 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
         set_error("mb_net_create: the student runs in FP32 or BF16");
         return MB_ERR_UNSUPPORTED;
     }
-    if (fam == FAMILY_FASTMEMB && prec != MB_PREC_FP32) {
-        set_error("mb_net_create: FastMemb runs in FP32");
+    if (fam == FAMILY_FASTMEMB && prec == MB_PREC_FP8) {
+        set_error("mb_net_create: FastMemb runs in FP32 or BF16");
         return MB_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -418,6 +428,7 @@ mb_status mb_net_destroy(mb_net* net) {
         DeviceGuard g(net->device);
         cudaDeviceSynchronize();
         tc_release(net);
+        fm_tc_release(net);
         dev_free(net->d_params);
         dev_free(net->d_simt);
         dev_free(net->d_queue);
@@ -469,6 +480,7 @@ mb_status mb_load_weights(mb_net* net, const float* params, int64_t n_params) {
     net->calibrated = false;
     net->loaded = true;
     if (net->family == FAMILY_TEACHER && net->prec == MB_PREC_BF16) MB_TRY(tc_prepare(net));
+    if (net->family == FAMILY_FASTMEMB && net->prec == MB_PREC_BF16) MB_TRY(fm_tc_prepare(net));
     return MB_OK;
 }
 
@@ -633,8 +645,8 @@ mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t 
             MB_TRY(teacher_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w, b.out,
                                   b.out_pitch, b.out_slice_pitch, out_type, st));
         } else if (net->family == FAMILY_FASTMEMB) {
-            MB_TRY(simt_fastmemb_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w,
-                                        b.out, b.out_pitch, b.out_slice_pitch, out_type, st));
+            MB_TRY(fastmemb_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w, b.out,
+                                   b.out_pitch, b.out_slice_pitch, out_type, st));
         } else if (b.z > 0) {
             MB_TRY(simt_student_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w,
                                        b.out, b.out_pitch, b.out_slice_pitch, out_type, st));

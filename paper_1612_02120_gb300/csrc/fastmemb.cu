@@ -21,6 +21,7 @@
 // Domains for an output region rows x cols (radius 26):
 //   conv1 out (rows+49)^2 .. conv2 out (rows+42) .. conv3 out (rows+28) .. head out rows
 //   (each conv removes 3d, each max-filter d).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,7 +34,7 @@ namespace mb {
 namespace {
 
 enum { FM_IN_U8 = 0, FM_IN_F32 = 1 };
-enum { FM_OUT_MAXOUT = 0, FM_OUT_SOFTMAX_F32 = 1, FM_OUT_SOFTMAX_U8 = 2 };
+enum { FM_OUT_MAXOUT = 0, FM_OUT_SOFTMAX_F32 = 1, FM_OUT_SOFTMAX_U8 = 2, FM_OUT_MAXOUT_BF16 = 3 };
 
 struct FmArgs {
     const void* in;
@@ -61,7 +62,6 @@ __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret
 __device__ __forceinline__ float4 max4(float4 a, float4 b) {
     return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
 }
-
 template <int CIN, int CC, int CO, int CPT, int IN, int OUT>
 __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
     constexpr int K = 4;
@@ -169,7 +169,21 @@ __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
 
     const int oy = ry + d * (fy0 + ty);
     if (oy >= a.out_h) return;
-    if constexpr (OUT == FM_OUT_MAXOUT) {
+    if constexpr (OUT == FM_OUT_MAXOUT_BF16) {
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + (int64_t)zi * a.out_slice;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int ox = rx + d * (fx0 + 4 * tx + j);
+            if (ox < a.out_w) {
+                __nv_bfloat162 lo = __floats2bfloat162_rn(fmaxf(acc[j][0], acc[j][1]), fmaxf(acc[j][2], acc[j][3]));
+                __nv_bfloat162 hi = __floats2bfloat162_rn(fmaxf(acc[j][4], acc[j][5]), fmaxf(acc[j][6], acc[j][7]));
+                uint2 u;
+                u.x = *reinterpret_cast<uint32_t*>(&lo);
+                u.y = *reinterpret_cast<uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(o + ((int64_t)oy * a.out_pitch + ox) * (CO / 2) + 4 * cg) = u;
+            }
+        }
+    } else if constexpr (OUT == FM_OUT_MAXOUT) {
         static_assert(CPT == 8, "max-out epilogue writes 4 channels per thread");
         float* o = static_cast<float*>(a.out) + (int64_t)zi * a.out_slice;
 #pragma unroll
@@ -326,6 +340,59 @@ mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
         }
     }
     return MB_OK;
+}
+
+// BF16 path: layer 1 on CUDA cores (FP32 arithmetic, BF16 out); the two 32->64 dilated convs and
+// the head on the tensor cores (fastmemb_tc.cu); activations between layers are BF16 [slice][y][x][32].
+mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+                               int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
+                               int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st) {
+    if (z == 0 || rows == 0 || cols == 0) return MB_OK;
+    MB_TRY(fm_tc_poll_error(net));
+    const int64_t r1 = rows + 49, c1 = cols + 49, r2 = rows + 42, c2 = cols + 42, r3 = rows + 28, c3 = cols + 28;
+    auto up = [](int64_t n) { return (n + 127) & ~(int64_t)127; };  // 256-byte aligned sub-buffers
+    const int64_t n1 = up(r1 * c1 * 32), n2 = up(r2 * c2 * 32), n3 = up(r3 * c3 * 32);
+    const size_t per = (size_t)(n1 + n2 + n3) * 2;
+    const size_t budget = (size_t)3 << 30;
+    const int64_t zc = std::min<int64_t>(std::min<int64_t>(std::max<size_t>(1, budget / per), 65535), z);
+    MB_TRY(net->ws.ensure(per * (size_t)zc));
+    __nv_bfloat16* act1 = static_cast<__nv_bfloat16*>(net->ws.ptr);
+    __nv_bfloat16* act2 = act1 + (size_t)zc * n1;
+    __nv_bfloat16* act3 = act2 + (size_t)zc * n2;
+    const float* w1 = net->d_simt;
+    const float* b1 = w1 + 16 * 64;
+    const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
+    for (int64_t z0 = 0; z0 < z; z0 += zc) {
+        const int nz = (int)std::min<int64_t>(zc, z - z0);
+        FmArgs a{};
+        a.in = in + z0 * in_slice;
+        a.in_slice = in_slice;
+        a.in_pitch = in_pitch;
+        a.in_rows = (int)(r1 + 3);
+        a.in_cols = (int)(c1 + 3);
+        a.src_h = (int)h;
+        a.src_w = (int)w;
+        a.off_y = (int)(y0 - 26);
+        a.off_x = (int)(x0 - 26);
+        a.d = 1;
+        a.dm = 0;
+        a.out_h = (int)r1;
+        a.out_w = (int)c1;
+        a.out = act1;
+        a.out_slice = n1;
+        a.out_pitch = c1;
+        a.wt = w1;
+        a.bias = b1;
+        MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT_BF16>(a, nz, st)));
+        MB_TRY(fm_tc_layer(net, 0, act1, n1, c1, (int)(r1 - 1), (int)(c1 - 1), 1, act2, n2, c2, (int)r2, (int)c2, 2,
+                           nz, 0, st));
+        MB_TRY(fm_tc_layer(net, 1, act2, n2, c2, (int)(r2 - 2), (int)(c2 - 2), 2, act3, n3, c3, (int)r3, (int)c3, 4,
+                           nz, 0, st));
+        MB_TRY(fm_tc_layer(net, 2, act3, n3, c3, (int)(r3 - 4), (int)(c3 - 4), 4,
+                           static_cast<uint8_t*>(out) + z0 * out_slice * osz, out_slice, out_pitch, (int)rows,
+                           (int)cols, 8, nz, ot == MB_OUT_U8, st));
+    }
+    return fm_tc_poll_error(net);
 }
 
 }  // namespace mb

@@ -1,0 +1,518 @@
+// fastmemb_tc.cu - FastMemb's dense form (Sec. 2.2) on the 5th-generation tensor cores: the two
+// 32->64 dilated convolutions (+ bias, max-out over channel pairs) and the 32->2 head (+ the
+// 2-class softmax), each over the 2x2 max-filter of the previous stage.
+//
+// Implicit GEMM per output image row y and 128-pixel column strip x0, conv dilation d:
+//   D[128 px][N] = sum over 16 taps (ky, kx) and 2 K-halves of
+//                  A_{ky,kx}[128 px][16 ch] x B_{ky,kx}[N][16 ch]^T
+// A_{ky,kx} is input row y + d ky, pixels x0 + d kx .. x0 + d kx + 127, taken from one staged row
+// in the no-swizzle K-major layout [channel chunk][pixel][16 B]: the column tap is a (d kx x 16)-
+// byte shift of the descriptor's start address, so 4 staged rows feed all 32 MMAs of a row.
+// Output rows are walked in steps of d (one residue class y mod d at a time, the max-pooling
+// fragments of Sec. 2.2), so each staged row serves 4 consecutive output rows and is loaded once.
+//
+// Weights are split W = W_hi + W_lo, both BF16 (W_lo = BF16(W - W_hi)), and stacked along N, so
+// each MMA applies both and the result carries BF16 activation rounding only:
+//   layers: N = 128, columns n (hi) and 64 + n (lo) of conv channel n
+//   head:   N = 16,  columns 0, 1 (hi of classes 0, 1) and 2, 3 (lo); the rest zero
+//
+// Warp roles (512 threads, 1 CTA per SM, persistent over work items):
+//   warp 0      TMEM owner; lane 0 issues the MMAs (BF16 -> FP32 in TMEM)
+//   warps 4-7   epilogue: TMEM -> registers; layers: hi + lo + bias, max-out, BF16 store;
+//               head: z_c = hi + lo + bias, p = 1 / (1 + exp(z0 - z1)), FP32 or uint8 store
+//   warps 8-15  producers: max-filter 4 BF16 pixels of the previous stage into the A rows
+// Every mbarrier wait is bounded (a global-timer limit), after which the CTA records
+// MB_ERR_TIMEOUT in a mapped host word, stops issuing work and frees its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace mb {
+
+namespace {
+
+constexpr int kFThreads = 512;
+constexpr int kFP = 154;                 // pixels per staged row (>= 128 + 3*8); 154 mod 8 = 2 spreads
+                                         // the 4 chunk planes of one pixel pair over distinct banks
+constexpr int kFSlot = 4 * kFP * 16;     // bytes per staged row (4 chunks of 8 BF16 channels)
+constexpr int kFRing = 8;                // staged rows in flight
+constexpr int kFAcc = 4;                 // TMEM accumulators
+constexpr int kFTasks = 3;               // producer tasks per thread and row: ceil(4 * 152 / 256)
+constexpr uint64_t kFWaitNs = 4000000000ull;
+
+template <bool HEAD>
+struct FCfg {
+    static constexpr int N = HEAD ? 16 : 128;          // MMA N
+    static constexpr int kBlock = 2 * N * 16;          // one (tap, K-half) B block: [2 chunks][N][16 B]
+    static constexpr int kBBytes = 32 * kBlock;
+    static constexpr int kTmemCols = HEAD ? 64 : 512;
+    static constexpr int oB = 0;
+    static constexpr int oRing = oB + kBBytes;
+    static constexpr int oBias = oRing + kFRing * kFSlot;
+    static constexpr int oBar = oBias + 64 * 4;
+    static constexpr int kBars = 2 * kFRing + 2 * kFAcc + 1;
+    static constexpr int oMisc = oBar + kBars * 8;
+    static constexpr int kSmem = oMisc + 16;
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+struct FmTcParams {
+    const __nv_bfloat16* in;   // previous stage, [slice][y][x][32], before its max-filter
+    void* out;                 // layers: BF16 [slice][y][x][32]; head: FP32 or uint8 [slice][y][x]
+    const uint8_t* wpack;      // B operands then 64 FP32 biases
+    int* err;
+    int64_t in_slice, in_pitch, out_slice, out_pitch;  // elements / pixels
+    int in_rows, in_cols;      // domain of the max-filtered input
+    int out_h, out_w;
+    int d, dm;                 // conv dilation, max-filter dilation
+    int nz, n_strips, n_chunks, rows_per_item, n_items;
+    int out_u8;                // head: uint8 output round(255 p)
+    int fault_stall;           // test injection: producers withhold their arrivals
+    uint64_t wait_ns;
+};
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                         uint64_t limit_ns) {
+    if (*abort_flag) return false;
+    if (ptx::mbar_test(bar, parity)) return true;
+    const uint64_t t0 = gtime();
+    uint32_t n = 0;
+    while (!ptx::mbar_test(bar, parity)) {
+        __nanosleep(32);
+        if ((++n & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (gtime() - t0 > limit_ns) {
+                *abort_flag = 1;
+                *(volatile int*)err = MB_ERR_TIMEOUT;
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+struct FmItem {
+    int z, ry, x0, m0, rows;  // output rows y = ry + d (m0 + j), j < rows; rows may be 0
+};
+
+__device__ __forceinline__ FmItem fm_item(const FmTcParams& p, int k) {
+    FmItem it;
+    const int chunk = k % p.n_chunks;
+    k /= p.n_chunks;
+    const int strip = k % p.n_strips;
+    k /= p.n_strips;
+    it.ry = k % p.d;
+    it.z = k / p.d;
+    it.x0 = strip * 128;
+    it.m0 = chunk * p.rows_per_item;
+    const int hr = (p.out_h - it.ry + p.d - 1) / p.d;  // rows of this residue class
+    it.rows = max(0, min(p.rows_per_item, hr - it.m0));
+    return it;
+}
+
+__device__ __forceinline__ uint4 bmax(uint4 a, uint4 b) {
+    uint4 r;
+    const __nv_bfloat162* x = reinterpret_cast<const __nv_bfloat162*>(&a);
+    const __nv_bfloat162* y = reinterpret_cast<const __nv_bfloat162*>(&b);
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = __hmax2(x[i], y[i]);
+    return r;
+}
+
+template <bool HEAD>
+__global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant__ FmTcParams p) {
+    using C = FCfg<HEAD>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* row_full = reinterpret_cast<uint64_t*>(smem + C::oBar);
+    uint64_t* row_empty = row_full + kFRing;
+    uint64_t* acc_full = row_empty + kFRing;
+    uint64_t* acc_free = acc_full + kFAcc;
+    uint64_t* fin = acc_free + kFAcc;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::oMisc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::oMisc + 4);
+    const float* bias = reinterpret_cast<const float*>(smem + C::oBias);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < kFRing; ++i) {
+            ptx::mbar_init(&row_full[i], 256);
+            ptx::mbar_init(&row_empty[i], 1);
+        }
+        for (int i = 0; i < kFAcc; ++i) {
+            ptx::mbar_init(&acc_full[i], 1);
+            ptx::mbar_init(&acc_free[i], 128);
+        }
+        ptx::mbar_init(fin, 1);
+        *abort_flag = 0;
+        ptx::mbar_fence_init();
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(p.wpack);
+        uint4* dst = reinterpret_cast<uint4*>(smem + C::oB);
+        for (int i = tid; i < C::kBBytes / 16; i += kFThreads) dst[i] = __ldg(src + i);
+        const uint4* bsrc = reinterpret_cast<const uint4*>(p.wpack + C::kBBytes);
+        uint4* bdst = reinterpret_cast<uint4*>(smem + C::oBias);
+        for (int i = tid; i < 64 * 4 / 16; i += kFThreads) bdst[i] = __ldg(bsrc + i);
+    }
+    if (warp == 0) {
+        ptx::tmem_alloc(tmem_slot, C::kTmemCols);
+        ptx::tmem_relinquish();
+    }
+    ptx::fence_proxy_async_smem();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const uint32_t sbase = ptx::smem_u32(smem);
+    const int d = p.d;
+
+    if (warp == 0) {
+        // ================= MMA issuer ================================================================
+        if (lane == 0) {
+            const uint64_t adesc0 = ptx::smem_desc(sbase + C::oRing, kFP * 16, 128);
+            const uint64_t bdesc0 = ptx::smem_desc(sbase + C::oB, C::N * 16, 128);
+            constexpr uint32_t idesc = ptx::idesc_f32acc(ptx::kFmtBF16, 128, C::N);
+            uint32_t row_seq = 0, acc_seq = 0;
+            bool ok = true;
+            for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+                const FmItem it = fm_item(p, k);
+                if (it.rows == 0) continue;
+                for (int j = 0; j < it.rows; ++j) {
+                    for (int ky = 0; ky < 4; ++ky) {
+                        const uint32_t q = row_seq + j + ky;
+                        ok = ok && wait_bar(&row_full[q % kFRing], (q / kFRing) & 1, abort_flag, p.err, p.wait_ns);
+                    }
+                    const uint32_t qa = acc_seq + j, s = qa % kFAcc;
+                    ok = ok && wait_bar(&acc_free[s], ((qa / kFAcc) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                    ptx::tc_fence_after();
+                    if (ok) {
+                        const uint32_t dcol = tbase + (uint32_t)C::N * s;
+#pragma unroll
+                        for (int ky = 0; ky < 4; ++ky) {
+                            const uint32_t slot = (row_seq + j + ky) % kFRing;
+                            const uint64_t arow = adesc0 + (uint64_t)((slot * kFSlot) >> 4);
+#pragma unroll
+                            for (int kx = 0; kx < 4; ++kx)
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    const uint64_t ad = arow + (uint64_t)((h * 2 * kFP * 16 + d * kx * 16) >> 4);
+                                    const uint64_t bd =
+                                        bdesc0 + (uint64_t)((((ky * 4 + kx) * 2 + h) * C::kBlock) >> 4);
+                                    ptx::mma_bf16(dcol, ad, bd, idesc, (ky | kx | h) ? 1u : 0u);
+                                }
+                        }
+                    }
+                    ptx::mma_commit(&acc_full[s]);
+                    ptx::mma_commit(&row_empty[(row_seq + j) % kFRing]);
+                }
+                // the last three staged rows of the item are free once its MMAs are done
+                for (int u = it.rows; u < it.rows + 3; ++u) ptx::mma_commit(&row_empty[(row_seq + u) % kFRing]);
+                row_seq += it.rows + 3;
+                acc_seq += it.rows;
+            }
+            ptx::mma_commit(fin);
+            const uint64_t t0 = gtime();
+            while (!ptx::mbar_test(fin, 0)) {
+                if (gtime() - t0 > p.wait_ns) {
+                    *(volatile int*)p.err = MB_ERR_TIMEOUT;
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4 && warp < 8) {
+        // ================= epilogue ===================================================================
+        const int px = tid - 128;  // TMEM lane = pixel of the strip
+        const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
+        uint32_t acc_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const FmItem it = fm_item(p, k);
+            const int x = it.x0 + px;
+            for (int j = 0; j < it.rows; ++j) {
+                const uint32_t qa = acc_seq + j, s = qa % kFAcc;
+                wait_bar(&acc_full[s], (qa / kFAcc) & 1, abort_flag, p.err, p.wait_ns);
+                ptx::tc_fence_after();
+                const uint32_t ta = tbase + lanes + (uint32_t)C::N * s;
+                const int y = it.ry + d * (it.m0 + j);
+                const bool store = x < p.out_w && y < p.out_h && !*abort_flag;
+                if constexpr (HEAD) {
+                    float c[4];
+                    ptx::tmem_ld4(ta, c);
+                    ptx::tc_fence_before();
+                    ptx::mbar_arrive(&acc_free[s]);
+                    const float z0 = (c[0] + c[2]) + bias[0], z1 = (c[1] + c[3]) + bias[1];
+                    const float prob = 1.0f / (1.0f + expf(z0 - z1));
+                    if (store) {
+                        const int64_t idx = (int64_t)it.z * p.out_slice + (int64_t)y * p.out_pitch + x;
+                        if (p.out_u8)
+                            static_cast<uint8_t*>(p.out)[idx] = (uint8_t)fminf(floorf(255.0f * prob + 0.5f), 255.0f);
+                        else
+                            static_cast<float*>(p.out)[idx] = prob;
+                    }
+                } else {
+                    uint32_t w[16];
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        // conv channels 32 half .. 32 half + 31: hi in columns n, lo in 64 + n
+                        float hi[32], lo[32];
+                        ptx::tmem_ld32(ta + 32u * half, hi);
+                        ptx::tmem_ld32(ta + 64u + 32u * half, lo);
+#pragma unroll
+                        for (int c = 0; c < 16; c += 2) {
+                            const int n = 32 * half + 2 * c;
+                            const float a0 = fmaxf((hi[2 * c] + lo[2 * c]) + bias[n],
+                                                   (hi[2 * c + 1] + lo[2 * c + 1]) + bias[n + 1]);
+                            const float a1 = fmaxf((hi[2 * c + 2] + lo[2 * c + 2]) + bias[n + 2],
+                                                   (hi[2 * c + 3] + lo[2 * c + 3]) + bias[n + 3]);
+                            __nv_bfloat162 v = __floats2bfloat162_rn(a0, a1);
+                            w[8 * half + c / 2] = *reinterpret_cast<uint32_t*>(&v);
+                        }
+                    }
+                    ptx::tc_fence_before();
+                    ptx::mbar_arrive(&acc_free[s]);
+                    if (store) {
+                        uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(p.out) +
+                                                            (int64_t)it.z * p.out_slice +
+                                                            ((int64_t)y * p.out_pitch + x) * 32);
+                        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        o[2] = make_uint4(w[8], w[9], w[10], w[11]);
+                        o[3] = make_uint4(w[12], w[13], w[14], w[15]);
+                    }
+                }
+            }
+            acc_seq += it.rows;
+        }
+    } else if (warp >= 8) {
+        // ================= producers: max-filtered input rows into the A ring =========================
+        // Thread tasks e = pt + 256 i (chunk e & 3 of pixel e >> 2); all loads of a row are issued
+        // before the slot wait so their latency overlaps the wait.
+        const int pt = tid - 256;
+        const int ntask = 4 * (128 + 3 * d);
+        const int64_t dxo = (int64_t)p.dm * 32, dyo = (int64_t)p.dm * p.in_pitch * 32;
+        uint32_t row_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const FmItem it = fm_item(p, k);
+            if (it.rows == 0) continue;
+            const __nv_bfloat16* src = p.in + (int64_t)it.z * p.in_slice;
+            for (int u = 0; u < it.rows + 3; ++u) {
+                const uint32_t q = row_seq + u, slot = q % kFRing;
+                const int yin = it.ry + d * (it.m0 + u);
+                uint4 v[kFTasks];
+#pragma unroll
+                for (int i = 0; i < kFTasks; ++i) {
+                    const int e = pt + 256 * i;
+                    const int xin = it.x0 + (e >> 2);
+                    v[i] = make_uint4(0, 0, 0, 0);
+                    if (e < ntask && yin < p.in_rows && xin < p.in_cols) {
+                        const __nv_bfloat16* a = src + ((int64_t)yin * p.in_pitch + xin) * 32 + (e & 3) * 8;
+                        const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a));
+                        const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a + dxo));
+                        const uint4 r2 = __ldg(reinterpret_cast<const uint4*>(a + dyo));
+                        const uint4 r3 = __ldg(reinterpret_cast<const uint4*>(a + dyo + dxo));
+                        v[i] = bmax(bmax(r0, r1), bmax(r2, r3));
+                    }
+                }
+                wait_bar(&row_empty[slot], ((q / kFRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                uint8_t* dst = smem + C::oRing + slot * kFSlot;
+#pragma unroll
+                for (int i = 0; i < kFTasks; ++i) {
+                    const int e = pt + 256 * i;
+                    if (e < ntask) *reinterpret_cast<uint4*>(dst + ((e & 3) * kFP + (e >> 2)) * 16) = v[i];
+                }
+                ptx::fence_proxy_async_smem();
+                if (!p.fault_stall) ptx::mbar_arrive(&row_full[slot]);
+            }
+            row_seq += it.rows + 3;
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 0) ptx::tmem_dealloc(tbase, C::kTmemCols);
+}
+
+uint16_t bf16_bits_rn(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// Pack a conv 4x4 32->C layer W[c][ci][ky][kx], b[c] as B operands: block (tap t = 4 ky + kx,
+// K-half h) = [chunk kc][row][8 BF16], ci = 16 h + 8 kc + e. Row of (channel c, part) comes from
+// row_of(c, part): part 0 = BF16(W), part 1 = BF16(W - BF16(W)). Then 64 FP32 biases.
+template <bool HEAD>
+void fm_pack(const float* W, const float* b, int channels, std::vector<uint8_t>& out) {
+    using C = FCfg<HEAD>;
+    out.assign(C::kBBytes + 64 * 4, 0);
+    for (int c = 0; c < channels; ++c)
+        for (int ci = 0; ci < 32; ++ci)
+            for (int ky = 0; ky < 4; ++ky)
+                for (int kx = 0; kx < 4; ++kx) {
+                    const int t = ky * 4 + kx, h = ci / 16, kc = (ci % 16) / 8, e = ci % 8;
+                    const float w = W[((c * 32 + ci) * 4 + ky) * 4 + kx];
+                    const uint16_t whi = bf16_bits_rn(w);
+                    const uint16_t wlo = bf16_bits_rn(w - bf16_value(whi));
+                    const int rhi = c, rlo = HEAD ? 2 + c : 64 + c;
+                    uint8_t* blk = out.data() + (t * 2 + h) * C::kBlock + kc * C::N * 16;
+                    memcpy(blk + rhi * 16 + e * 2, &whi, 2);
+                    memcpy(blk + rlo * 16 + e * 2, &wlo, 2);
+                }
+    std::vector<float> bias(64, 0.f);
+    for (int c = 0; c < channels; ++c) bias[c] = b[c];
+    memcpy(out.data() + C::kBBytes, bias.data(), 64 * 4);
+}
+
+template <bool HEAD>
+mb_status launch_fm_tc(const FmTcParams& p, cudaStream_t st) {
+    using C = FCfg<HEAD>;
+    static int n_sms = 0;
+    if (n_sms == 0) {
+        int dev = 0;
+        MB_CUDA(cudaGetDevice(&dev));
+        MB_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    static bool attr = false;
+    if (!attr) {
+        MB_CUDA(cudaFuncSetAttribute(fm_tc_conv<HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+        attr = true;
+    }
+    const int grid = std::max(1, std::min(p.n_items, n_sms));
+    fm_tc_conv<HEAD><<<grid, kFThreads, C::kSmem, st>>>(p);
+    count_launch();
+    MB_CUDA(cudaGetLastError());
+    return MB_OK;
+}
+
+}  // namespace
+
+struct FmTcState {
+    uint8_t* d_wpack[3] = {nullptr, nullptr, nullptr};  // layers 2, 3 and the head
+    int* h_err = nullptr;
+    int* d_err = nullptr;
+};
+
+mb_status fm_tc_prepare(mb_net* net) {
+    FmTcState* S = reinterpret_cast<FmTcState*>(net->fm_state);
+    if (!S) {
+        S = new (std::nothrow) FmTcState();
+        if (!S) {
+            set_error("host allocation failed");
+            return MB_ERR_OOM;
+        }
+        net->fm_state = S;
+    }
+    // API layout: W1 [64][1][4][4], b1 [64], W2 [64][32][4][4], b2, W3, b3, W4 [2][32][4][4], b4
+    const float* P = net->host_params.data();
+    const float* W2 = P + 64 * 16 + 64;
+    const float* B2 = W2 + 64 * 32 * 16;
+    const float* W3 = B2 + 64;
+    const float* B3 = W3 + 64 * 32 * 16;
+    const float* W4 = B3 + 64;
+    const float* B4 = W4 + 2 * 32 * 16;
+    std::vector<uint8_t> pk;
+    for (int l = 0; l < 3; ++l) {
+        if (l < 2)
+            fm_pack<false>(l == 0 ? W2 : W3, l == 0 ? B2 : B3, 64, pk);
+        else
+            fm_pack<true>(W4, B4, 2, pk);
+        if (!S->d_wpack[l]) MB_TRY(dev_alloc((void**)&S->d_wpack[l], pk.size()));
+        MB_CUDA(cudaMemcpy(S->d_wpack[l], pk.data(), pk.size(), cudaMemcpyHostToDevice));
+    }
+    if (!S->h_err) {
+        if (fault_oom()) {
+            set_error("pinned allocation failed (MB_FAULT_OOM injected)");
+            return MB_ERR_OOM;
+        }
+        MB_CUDA(cudaHostAlloc((void**)&S->h_err, sizeof(int), cudaHostAllocMapped));
+        *S->h_err = 0;
+        MB_CUDA(cudaHostGetDevicePointer((void**)&S->d_err, S->h_err, 0));
+    }
+    return MB_OK;
+}
+
+void fm_tc_release(mb_net* net) {
+    FmTcState* S = reinterpret_cast<FmTcState*>(net->fm_state);
+    if (!S) return;
+    for (uint8_t* w : S->d_wpack) dev_free(w);
+    if (S->h_err) cudaFreeHost(S->h_err);
+    delete S;
+    net->fm_state = nullptr;
+}
+
+mb_status fm_tc_poll_error(mb_net* net) {
+    FmTcState* S = reinterpret_cast<FmTcState*>(net->fm_state);
+    if (S && S->h_err && *(volatile int*)S->h_err) {
+        *(volatile int*)S->h_err = 0;
+        set_error("a FastMemb tensor-core launch gave up waiting (device-side wait limit)");
+        return MB_ERR_TIMEOUT;
+    }
+    return MB_OK;
+}
+
+mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int in_rows,
+                      int in_cols, int dm, void* out, int64_t out_slice, int64_t out_pitch, int out_h, int out_w,
+                      int d, int nz, int out_u8, cudaStream_t st) {
+    FmTcState* S = reinterpret_cast<FmTcState*>(net->fm_state);
+    if (!S || !S->d_wpack[layer]) {
+        set_error("FastMemb tensor-core weights not prepared");
+        return MB_ERR_NOT_READY;
+    }
+    FmTcParams p{};
+    p.in = static_cast<const __nv_bfloat16*>(in);
+    p.out = out;
+    p.wpack = S->d_wpack[layer];
+    p.err = S->d_err;
+    p.in_slice = in_slice;
+    p.in_pitch = in_pitch;
+    p.out_slice = out_slice;
+    p.out_pitch = out_pitch;
+    p.in_rows = in_rows;
+    p.in_cols = in_cols;
+    p.out_h = out_h;
+    p.out_w = out_w;
+    p.d = d;
+    p.dm = dm;
+    p.nz = nz;
+    p.out_u8 = out_u8;
+    p.rows_per_item = 64;
+    p.n_strips = (out_w + 127) / 128;
+    const int hf = (out_h + d - 1) / d;
+    p.n_chunks = (hf + p.rows_per_item - 1) / p.rows_per_item;
+    const int64_t items = (int64_t)nz * d * p.n_strips * p.n_chunks;
+    if (items > 0x7fffffffLL) {
+        set_error("FastMemb: too many work items for one launch");
+        return MB_ERR_SHAPE;
+    }
+    p.n_items = (int)items;
+    const char* stall = getenv("MB_FAULT_STALL");
+    p.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
+    p.wait_ns = p.fault_stall ? 200000000ull : kFWaitNs;
+    return layer == 2 ? launch_fm_tc<true>(p, st) : launch_fm_tc<false>(p, st);
+}
+
+}  // namespace mb

@@ -2,6 +2,7 @@
 volume (the generator of `synth`), so a capture of one kernel stays a few hundred MB on the device.
 
     python -m paper_1612_02120_gb300.profile_case --prec bf16 --z 4 --h 1024 --w 1024 --reps 3
+    python -m paper_1612_02120_gb300.profile_case --net fastmemb --prec bf16 --z 4 --reps 3
 """
 import argparse
 import os
@@ -14,6 +15,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--net", default="teacher", choices=["teacher", "fastmemb"])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp8", "student"])
     ap.add_argument("--z", type=int, default=4)
     ap.add_argument("--h", type=int, default=1024)
@@ -28,7 +30,10 @@ def main():
     v = synth.em_volume(synth.BASE_SEED + 1, a.z, a.h, a.w)
     x = torch.from_numpy(v).cuda()
     out = torch.empty((a.z, a.h, a.w), dtype=torch.float32, device="cuda")
-    if a.prec == "student":
+    if a.net == "fastmemb":
+        prec = {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16}[a.prec]
+        net = m.Net(synth.FASTMEMB, prec, 0, synth.init_params(synth.FASTMEMB, synth.FASTMEMB_WEIGHT_SEED))
+    elif a.prec == "student":
         net = m.Net(synth.STUDENT, m.MB_PREC_BF16, 0, synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED))
     else:
         prec = {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16, "fp8": m.MB_PREC_FP8}[a.prec]
@@ -38,7 +43,7 @@ def main():
     for _ in range(a.reps):
         m.mb_infer_volume(net.handle, x, a.z, a.h, a.w, out)
     torch.cuda.synchronize()
-    print(f"ok {a.prec} {a.z}x{a.h}x{a.w} mean p {float(out.mean()):.6f}")
+    print(f"ok {a.net} {a.prec} {a.z}x{a.h}x{a.w} mean p {float(out.mean()):.6f}")
     net.close()
 
 

@@ -1,7 +1,8 @@
-"""FastMemb in dense form (Sec. 2.2) on the FP32 CUDA-core path vs the FP64 oracle, element by
-element (max-abs <= 1e-5), at sizes that span several fragment tiles at every dilation with
-ragged tails; sampled pixels of a full 1024x1024 slice against the oracle's patch calculation;
-and the path's invariants and error codes. Calls go through the C ABI."""
+"""FastMemb in dense form (Sec. 2.2) vs the FP64 oracle: the FP32 CUDA-core path element by
+element (max-abs <= 1e-5) and the BF16 tensor-core path within the stated BF16 tolerances, at
+sizes that span several tiles at every dilation with ragged tails; sampled pixels of full
+1024x1024 slices against the oracle's patch calculation; the paths' invariants, error codes and
+a timed-out device wait. Calls go through the C ABI."""
 import numpy as np
 import pytest
 
@@ -119,7 +120,7 @@ def test_error_codes():
     from paper_1612_02120_gb300 import membrane as m
     lib = m.load()
     with pytest.raises(m.MembraneError) as e:
-        m.mb_net_create(F, m.MB_PREC_BF16, 0)
+        m.mb_net_create(F, m.MB_PREC_FP8, 0)
     assert e.value.status == m.MB_ERR_UNSUPPORTED
     bad = list(F)
     bad[2] = (synth.CONV, 4, 32, 32, 0, 3, 2)  # dilation 3: no kernel
@@ -132,3 +133,92 @@ def test_error_codes():
     assert lib.mb_infer_volume(n.handle, x.data_ptr(), 1, 26, 64, out.data_ptr(), 0, None) == m.MB_ERR_SHAPE
     assert lib.mb_infer_volume(n.handle, x.data_ptr(), 1, 64, 26, out.data_ptr(), 0, None) == m.MB_ERR_SHAPE
     n.close()
+
+
+# ---- BF16: the two 32->64 convs on the tensor cores --------------------------------------------
+
+@pytest.fixture(scope="module")
+def net_bf16():
+    from paper_1612_02120_gb300 import build, membrane as m
+    build.build()
+    n = make_net(F, m.MB_PREC_BF16, fm_params())
+    yield n
+    n.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 27, 27), (2, 64, 45), (1, 300, 280), (1, 200, 530), (3, 41, 58)])
+def test_bf16_slices_match_oracle(net_bf16, shape):
+    """Sizes span several 128-pixel strips and 64-row chunks of every residue class, ragged.
+    Binarised agreement is a statistic over the map: it is asserted on maps of at least 4096
+    pixels (on a 27x27 map one near-threshold pixel moves it by 0.14 %)."""
+    z, h, w = shape
+    v = synth.em_volume(9500 + h * w, z, h, w)
+    p = infer(net_bf16, v)
+    prm = fm_params()
+    tol = dict(TOL["bf16"])
+    if h * w < 4096:
+        del tol["agreement"]
+    for zi in range(z):
+        met = oracle.metrics(p[zi], oracle.forward_region(F, prm, v[zi]))
+        assert within(met, tol), (shape, zi, met)
+
+
+def test_bf16_full_size_slice_sampled_against_patch_calculation(net_bf16):
+    s = synth.em_slice(synth.slice_seed(synth.BASE_SEED + 5, 0, 1), 1024, 1024)
+    p = infer(net_bf16, s[None])[0]
+    prm = fm_params()
+    rng = np.random.default_rng(12)
+    pix = [(0, 0), (0, 1023), (1023, 0), (1023, 1023), (640, 127), (128, 128), (3, 1020)]
+    pix += [tuple(int(t) for t in rng.integers(0, 1024, 2)) for _ in range(33)]
+    err = [abs(float(p[i, j]) - oracle.patch_pixel(F, prm, s, i, j)) for i, j in pix]
+    assert max(err) <= TOL["bf16"]["max_abs"], max(err)
+    assert np.mean(err) <= TOL["bf16"]["mean_abs"], np.mean(err)
+
+
+def test_bf16_region_and_batch_equal_volume_bitwise(net_bf16):
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    v = synth.em_volume(9600, 2, 180, 300)
+    full = infer(net_bf16, v)
+    x = torch.from_numpy(v).cuda()
+    out = torch.empty((2, 70, 141), dtype=torch.float32, device="cuda")
+    m.mb_infer_region(net_bf16.handle, x, 2, 180, 300, 33, 130, 70, 141, out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), full[:, 33:103, 130:271])
+    o = torch.full((2, 180, 305), -1.0, dtype=torch.float32, device="cuda")
+    m.mb_infer_batch(net_bf16.handle, [(x, 2, 180, 300, 300, 180 * 300, o, 305, 180 * 305)])
+    torch.cuda.synchronize()
+    o = o.cpu().numpy()
+    np.testing.assert_array_equal(o[:, :, :300], full)
+    assert (o[:, :, 300:] == -1.0).all()
+
+
+def test_bf16_u8_output_and_host_buffers(net_bf16):
+    from paper_1612_02120_gb300 import membrane as m
+    v = synth.em_volume(9700, 3, 70, 90)
+    pf = infer(net_bf16, v, 0)
+    pq = infer(net_bf16, v, 1)
+    q = np.minimum(255, np.floor(np.float32(255.0) * pf + np.float32(0.5))).astype(np.uint8)
+    np.testing.assert_array_equal(pq, q)
+    host = np.empty((3, 70, 90), dtype=np.float32)
+    m.mb_infer_volume(net_bf16.handle, np.ascontiguousarray(v), 3, 70, 90, host)
+    np.testing.assert_array_equal(host, pf)
+
+
+def test_bf16_timed_out_device_wait_is_reported_and_context_survives(net_bf16, monkeypatch):
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    lib = m.load()
+    v = synth.em_volume(9800, 1, 64, 80)
+    ref = infer(net_bf16, v)
+    x = torch.from_numpy(v).cuda()
+    out = torch.zeros((1, 64, 80), dtype=torch.float32, device="cuda")
+    monkeypatch.setenv("MB_FAULT_STALL", "1")
+    assert lib.mb_infer_volume(net_bf16.handle, x.data_ptr(), 1, 64, 80, out.data_ptr(), 0, None) == m.MB_OK
+    torch.cuda.synchronize()
+    monkeypatch.delenv("MB_FAULT_STALL")
+    assert lib.mb_infer_volume(net_bf16.handle, x.data_ptr(), 1, 64, 80, out.data_ptr(), 0, None) == m.MB_ERR_TIMEOUT
+    assert "wait limit" in m.last_error()
+    assert lib.mb_infer_volume(net_bf16.handle, x.data_ptr(), 1, 64, 80, out.data_ptr(), 0, None) == m.MB_OK
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
