@@ -20,7 +20,9 @@
 //   warp 0      TMEM owner; lane 0 issues the MMAs (BF16 -> FP32 in TMEM)
 //   warps 4-7   epilogue: TMEM -> registers; layers: hi + lo + bias, max-out, BF16 store;
 //               head: z_c = hi + lo + bias, p = 1 / (1 + exp(z0 - z1)), FP32 or uint8 store
-//   warps 8-15  producers: max-filter 4 BF16 pixels of the previous stage into the A rows
+//   warps 8-15  producers, two groups of 4 warps taking alternate staged rows: max-filter 4 BF16
+//               pixels of the previous stage into the A rows; one thread of each group
+//               bulk-prefetches the source rows of its staged row 4 ahead into L2
 // Every mbarrier wait is bounded (a global-timer limit), after which the CTA records
 // MB_ERR_TIMEOUT in a mapped host word, stops issuing work and frees its TMEM.
 #include <cuda_bf16.h>
@@ -44,7 +46,8 @@ constexpr int kFP = 154;                 // pixels per staged row (>= 128 + 3*8)
 constexpr int kFSlot = 4 * kFP * 16;     // bytes per staged row (4 chunks of 8 BF16 channels)
 constexpr int kFRing = 8;                // staged rows in flight
 constexpr int kFAcc = 4;                 // TMEM accumulators
-constexpr int kFTasks = 3;               // producer tasks per thread and row: ceil(4 * 152 / 256)
+constexpr int kFTasks = 5;               // producer tasks per thread and row: ceil(4 * 152 / 128)
+constexpr int kFPrefetch = 4;            // staged rows between a row's L2 prefetch and its loads
 constexpr uint64_t kFWaitNs = 4000000000ull;
 
 template <bool HEAD>
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
 
     if (tid == 0) {
         for (int i = 0; i < kFRing; ++i) {
-            ptx::mbar_init(&row_full[i], 256);
+            ptx::mbar_init(&row_full[i], 128);
             ptx::mbar_init(&row_empty[i], 1);
         }
         for (int i = 0; i < kFAcc; ++i) {
@@ -188,34 +191,48 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
             constexpr uint32_t idesc = ptx::idesc_f32acc(ptx::kFmtBF16, 128, C::N);
             uint32_t row_seq = 0, acc_seq = 0;
             bool ok = true;
+            // The waits for output row j+1 (its one new staged row and its accumulator) are taken
+            // between the two halves of row j's MMAs, while the first half still queues in the tensor
+            // pipe: at N = 128 the operand reads take the whole shared-memory bandwidth and a poll
+            // costs hundreds of cycles.
+            auto wait_row = [&](uint32_t q) {
+                ok = ok && wait_bar(&row_full[q % kFRing], (q / kFRing) & 1, abort_flag, p.err, p.wait_ns);
+            };
+            auto wait_acc = [&](uint32_t qa) {
+                ok = ok && wait_bar(&acc_free[qa % kFAcc], ((qa / kFAcc) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+            };
+            auto issue_half = [&](uint32_t j, uint32_t s, int ky0) {
+                const uint32_t dcol = tbase + (uint32_t)C::N * s;
+#pragma unroll
+                for (int dky = 0; dky < 2; ++dky) {
+                    const int ky = ky0 + dky;
+                    const uint32_t slot = (row_seq + j + ky) % kFRing;
+                    const uint64_t arow = adesc0 + (uint64_t)((slot * kFSlot) >> 4);
+#pragma unroll
+                    for (int kx = 0; kx < 4; ++kx)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint64_t ad = arow + (uint64_t)((h * 2 * kFP * 16 + d * kx * 16) >> 4);
+                            const uint64_t bd = bdesc0 + (uint64_t)((((ky * 4 + kx) * 2 + h) * C::kBlock) >> 4);
+                            ptx::mma_bf16(dcol, ad, bd, idesc, (ky | kx | h) ? 1u : 0u);
+                        }
+                }
+            };
             for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
                 const FmItem it = fm_item(p, k);
                 if (it.rows == 0) continue;
+                for (int u = 0; u < 4; ++u) wait_row(row_seq + u);
+                wait_acc(acc_seq);
+                ptx::tc_fence_after();
                 for (int j = 0; j < it.rows; ++j) {
-                    for (int ky = 0; ky < 4; ++ky) {
-                        const uint32_t q = row_seq + j + ky;
-                        ok = ok && wait_bar(&row_full[q % kFRing], (q / kFRing) & 1, abort_flag, p.err, p.wait_ns);
+                    const uint32_t s = (acc_seq + j) % kFAcc;
+                    if (ok) issue_half(j, s, 0);
+                    if (j + 1 < it.rows) {
+                        wait_row(row_seq + j + 4);
+                        wait_acc(acc_seq + j + 1);
+                        ptx::tc_fence_after();
                     }
-                    const uint32_t qa = acc_seq + j, s = qa % kFAcc;
-                    ok = ok && wait_bar(&acc_free[s], ((qa / kFAcc) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                    ptx::tc_fence_after();
-                    if (ok) {
-                        const uint32_t dcol = tbase + (uint32_t)C::N * s;
-#pragma unroll
-                        for (int ky = 0; ky < 4; ++ky) {
-                            const uint32_t slot = (row_seq + j + ky) % kFRing;
-                            const uint64_t arow = adesc0 + (uint64_t)((slot * kFSlot) >> 4);
-#pragma unroll
-                            for (int kx = 0; kx < 4; ++kx)
-#pragma unroll
-                                for (int h = 0; h < 2; ++h) {
-                                    const uint64_t ad = arow + (uint64_t)((h * 2 * kFP * 16 + d * kx * 16) >> 4);
-                                    const uint64_t bd =
-                                        bdesc0 + (uint64_t)((((ky * 4 + kx) * 2 + h) * C::kBlock) >> 4);
-                                    ptx::mma_bf16(dcol, ad, bd, idesc, (ky | kx | h) ? 1u : 0u);
-                                }
-                        }
-                    }
+                    if (ok) issue_half(j, s, 2);
                     ptx::mma_commit(&acc_full[s]);
                     ptx::mma_commit(&row_empty[(row_seq + j) % kFRing]);
                 }
@@ -299,9 +316,11 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
         }
     } else if (warp >= 8) {
         // ================= producers: max-filtered input rows into the A ring =========================
-        // Thread tasks e = pt + 256 i (chunk e & 3 of pixel e >> 2); all loads of a row are issued
-        // before the slot wait so their latency overlaps the wait.
-        const int pt = tid - 256;
+        // Group g = warps 8-11 / 12-15 stages the rows u = g mod 2 of every item. Thread tasks
+        // e = pt + 128 i (chunk e & 3 of pixel e >> 2); all loads of a row are issued before the
+        // slot wait so their latency overlaps the wait.
+        const int grp = (warp - 8) >> 2;
+        const int pt = tid - 256 - 128 * grp;
         const int ntask = 4 * (128 + 3 * d);
         const int64_t dxo = (int64_t)p.dm * 32, dyo = (int64_t)p.dm * p.in_pitch * 32;
         uint32_t row_seq = 0;
@@ -309,13 +328,23 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
             const FmItem it = fm_item(p, k);
             if (it.rows == 0) continue;
             const __nv_bfloat16* src = p.in + (int64_t)it.z * p.in_slice;
-            for (int u = 0; u < it.rows + 3; ++u) {
+            const int pf_cols = min(128 + 3 * d + p.dm, p.in_cols + p.dm - it.x0);  // source pixels a row reads
+            for (int u = grp; u < it.rows + 3; u += 2) {
                 const uint32_t q = row_seq + u, slot = q % kFRing;
                 const int yin = it.ry + d * (it.m0 + u);
+                // bulk-prefetch into L2 the two source rows of staged row u + kFPrefetch
+                if (pt == 0 && u + kFPrefetch < it.rows + 3) {
+                    const int yp = it.ry + d * (it.m0 + u + kFPrefetch);
+                    if (yp < p.in_rows && pf_cols > 0) {
+                        const __nv_bfloat16* r0 = src + ((int64_t)yp * p.in_pitch + it.x0) * 32;
+                        ptx::prefetch_l2_bulk(r0, (uint32_t)pf_cols * 64u);
+                        ptx::prefetch_l2_bulk(r0 + dyo, (uint32_t)pf_cols * 64u);
+                    }
+                }
                 uint4 v[kFTasks];
 #pragma unroll
                 for (int i = 0; i < kFTasks; ++i) {
-                    const int e = pt + 256 * i;
+                    const int e = pt + 128 * i;
                     const int xin = it.x0 + (e >> 2);
                     v[i] = make_uint4(0, 0, 0, 0);
                     if (e < ntask && yin < p.in_rows && xin < p.in_cols) {
@@ -331,7 +360,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                 uint8_t* dst = smem + C::oRing + slot * kFSlot;
 #pragma unroll
                 for (int i = 0; i < kFTasks; ++i) {
-                    const int e = pt + 256 * i;
+                    const int e = pt + 128 * i;
                     if (e < ntask) *reinterpret_cast<uint4*>(dst + ((e & 3) * kFP + (e >> 2)) * 16) = v[i];
                 }
                 ptx::fence_proxy_async_smem();

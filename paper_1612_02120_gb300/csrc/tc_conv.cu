@@ -239,13 +239,13 @@ __device__ __forceinline__ void store_half(uint8_t* slot, int c, int h, const fl
     }
 }
 
-// Issue the MMAs of one input row r for one layer: output rows j = r-4+i of the layer for the
-// valid blocks i (0 <= j < n_out). Every MMA accumulates; the epilogue zeroes an accumulator after
+// Issue the MMAs of groups [g_lo, g_hi) of one input row r for one layer: output rows j = r-4+i of
+// the layer for the valid blocks i (0 <= j < n_out). Every MMA accumulates; the epilogue zeroes an accumulator after
 // draining it, so a row's first contribution adds to zero. Blocks go to ring slots
 // (base + r - 4 + i) mod kAcc; runs of contiguous slots are one MMA each.
 template <bool FP8>
 __device__ __forceinline__ void issue_row(uint32_t tcol0, uint32_t acc_base_seq, int r, int n_out, uint64_t adesc0,
-                                          uint64_t bdesc0) {
+                                          uint64_t bdesc0, int g_lo, int g_hi) {
     using C = Cfg<FP8>;
     constexpr int G = C::kGroups;
     constexpr int K = C::kAcc;
@@ -279,6 +279,7 @@ __device__ __forceinline__ void issue_row(uint32_t tcol0, uint32_t acc_base_seq,
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
+        if (g < g_lo || g >= g_hi) continue;
         const int dx = FP8 ? g : (g >> 1);
         const int hk = FP8 ? 0 : (g & 1);
         const uint64_t ad = adesc0 + (uint64_t)((hk * 2 * kPitch * 16 + dx * 16) >> 4);
@@ -365,9 +366,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     const uint32_t tbase = *tmem_slot;
     const uint32_t smem_base = ptx::smem_u32(smem);
     // Register budget per warpgroup (launched with 128 per thread = the whole register file):
-    // MMA issuers + loader 56, layer-2 epilogue 112, layer-3 epilogue 80, layer-1 producers 232.
-    // Sum 480 <= 512 per thread-slot, so the producers' increase is always satisfiable.
-    static_assert(56 + 112 + 80 + 232 <= 4 * 128, "register budget exceeds the launch allocation");
+    // MMA issuers + loader 64, layer-2 epilogue 112, layer-3 epilogue 80, layer-1 producers 232.
+    // Sum 488 <= 512 per thread-slot, so the producers' increase is always satisfiable.
+    static_assert(64 + 112 + 80 + 232 <= 4 * 128, "register budget exceeds the launch allocation");
     if (warp >= 4 && warp < 12) {
         // every accumulator starts at zero (the MMAs only accumulate)
         const uint32_t col0 = warp < 8 ? 0u : 256u;
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     ptx::tc_fence_after();
 
     if (warp < 4) {
-        ptx::setmaxnreg_dec<56>();
+        ptx::setmaxnreg_dec<64>();
         if (warp == 0 || warp == 2) {
         // ================= MMA issuers: warp 0 lane 0 for layer 2, warp 2 lane 0 for layer 3 ======
         // Each issuer commits (and finally drains) only its own MMAs.
@@ -395,23 +396,44 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             uint64_t* empty = l2 ? B.m1_empty : B.m2_empty;
             uint64_t* afree = l2 ? B.a2_free : B.a3_free;
             uint64_t* afull = l2 ? B.a2_full : B.a3_full;
+            // The waits for input row r+1 are taken between the two halves of row r's MMAs, while the
+            // first half still queues in the tensor pipe (a poll competes with the operand reads for
+            // the shared-memory pipe). The accumulator of output row r+1 shares its slot with output
+            // row r+1-kAcc, completed by input row r+5-kAcc: mid-row for the ring of 8 (BF16), but
+            // only at the end of row r itself for the ring of 5 (FP8), where that wait stays after
+            // the row's commits.
+            constexpr int G = C::kGroups;
+            constexpr bool kEarlyAcc = C::kAcc >= 6;
+            auto wait_in = [&](uint32_t q) {
+                ok = ok && wait_phase(&full[q % kRing], (q / kRing) & 1, abort_flag, p.err, p.wait_ns);
+            };
+            auto wait_acc = [&](uint32_t qa) {
+                ok = ok && wait_phase(&afree[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+            };
             for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
                 const ItemInfo it = decode_item(p, k);
                 const int NR = it.rows;
                 const int n_in = l2 ? NR + 9 : NR + 4;   // input rows of this layer
                 const int n_out = l2 ? NR + 5 : NR;      // output rows of this layer
+                wait_in(in_seq);
+                if (n_out > 0) wait_acc(acc_seq);
+                ptx::tc_fence_after();
                 for (int r = 0; r < n_in; ++r) {
                     const uint32_t q = in_seq + r, s = q % kRing;
-                    ok = ok && wait_phase(&full[s], (q / kRing) & 1, abort_flag, p.err, p.wait_ns);
-                    if (r < n_out) {
-                        const uint32_t qa = acc_seq + r;
-                        ok = ok && wait_phase(&afree[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag, p.err,
-                                              p.wait_ns);
+                    const uint64_t arow = ad + (uint64_t)(s * (C::kSlotBytes >> 4));
+                    if (ok) issue_row<FP8>(tcol, acc_seq, r, n_out, arow, bd, 0, G / 2);
+                    if (r + 1 < n_in) {
+                        wait_in(q + 1);
+                        if (kEarlyAcc && r + 1 < n_out) wait_acc(acc_seq + r + 1);
+                        ptx::tc_fence_after();
                     }
-                    ptx::tc_fence_after();
-                    if (ok) issue_row<FP8>(tcol, acc_seq, r, n_out, ad + (uint64_t)(s * (C::kSlotBytes >> 4)), bd);
+                    if (ok) issue_row<FP8>(tcol, acc_seq, r, n_out, arow, bd, G / 2, G);
                     ptx::mma_commit(&empty[s]);
                     if (r >= 4 && r - 4 < n_out) ptx::mma_commit(&afull[(acc_seq + r - 4) % C::kAcc]);
+                    if (!kEarlyAcc && r + 1 < n_in && r + 1 < n_out) {
+                        wait_acc(acc_seq + r + 1);
+                        ptx::tc_fence_after();
+                    }
                 }
                 in_seq += n_in;
                 acc_seq += n_out;

@@ -34,6 +34,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// ---- bulk prefetch of a global range into L2 (16-byte aligned address, size a multiple of 16) ----
+__device__ __forceinline__ void prefetch_l2_bulk(const void* gptr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gptr), "r"(bytes) : "memory");
+}
+
 // ---- proxy / tcgen05 fences ---------------------------------------------------------------------
 // Generic-proxy shared-memory writes become visible to the async proxy (tcgen05.mma operands).
 __device__ __forceinline__ void fence_proxy_async_smem() {
