@@ -236,3 +236,42 @@ def test_fastmemb_output_is_a_probability_map_and_needs_27_pixels():
     assert p.shape == (27, 27) and np.all((p >= 0) & (p <= 1))
     with pytest.raises(RuntimeError):
         oracle.forward_region(F, prm, synth.em_slice(7004, 26, 40))
+
+
+def pruned_fragments_forward(xp, params):
+    """The fragment tree pruned at the first stride-2 pool to its offset (0, 0) branch: 16 of the 64
+    fragments, interleaved after the softmax, give the dense map at even rows and columns."""
+    (W1, b1), (W2, b2), (W3, b3), (W4, b4) = split_params(F, params)
+    m = np_maxout(np_conv(xp[None], W1, b1), 2)
+    m = np.maximum(np.maximum(m[:, :-1, :-1], m[:, 1:, :-1]), np.maximum(m[:, :-1, 1:], m[:, 1:, 1:]))
+    frags = [(0, 0, 2, m[:, 0::2, 0::2])]
+    for W, b in ((W2, b2), (W3, b3)):
+        nxt = []
+        for oy, ox, step, x in frags:
+            m = np_maxout(np_conv(x, W, b), 2)
+            m = np.maximum(np.maximum(m[:, :-1, :-1], m[:, 1:, :-1]), np.maximum(m[:, :-1, 1:], m[:, 1:, 1:]))
+            for sy in (0, 1):
+                for sx in (0, 1):
+                    nxt.append((oy + step * sy, ox + step * sx, 2 * step, m[:, sy::2, sx::2]))
+        frags = nxt
+    assert len(frags) == 16
+    H, W = xp.shape[0] - 52, xp.shape[1] - 52
+    out = np.full(((H + 1) // 2, (W + 1) // 2), np.nan)
+    for oy, ox, step, x in frags:
+        p = np_softmax_class1(np_conv(x, W4, b4))
+        ys, xs = np.arange(p.shape[0]) * step + oy, np.arange(p.shape[1]) * step + ox
+        ky, kx = ys < H, xs < W
+        out[np.ix_(ys[ky] // 2, xs[kx] // 2)] = p[np.ix_(ky, kx)]
+    return out
+
+
+@pytest.mark.parametrize("shape", [(44, 38), (45, 37)])
+def test_subsampled_output_is_the_pruned_fragment_tree(shape):
+    """Sec. 2.2 (Fig. 3a caption): pruning the recursion tree sub-samples the output. The branch of
+    the first pool's offset (0, 0) equals the dense map at even positions."""
+    prm = fm_params(synth.FASTMEMB_WEIGHT_SEED + 4)
+    s = synth.em_slice(7005, *shape)
+    dense = oracle.forward_region(F, prm, s)
+    pruned = pruned_fragments_forward(np.pad(s.astype(np.float64) / 255.0, 26, mode="reflect"), prm)
+    assert not np.isnan(pruned).any() and pruned.shape == dense[::2, ::2].shape
+    np.testing.assert_allclose(pruned, dense[::2, ::2], rtol=0, atol=1e-12)
