@@ -13,8 +13,9 @@ the same through the C ABI with pinned HOST buffers (copies inside the timed reg
         memory; errors on 3 seeded 512x512 crops (true context);
   cfg4  student training (200 x 512^2, batch 32, lr 1e-3, 2000 steps) on FP32-teacher maps, then
         student-only and cascade (teacher fallback on 256^2 tiles) on the cfg3 volume;
-  cfg5  FastMemb in dense form (Sec. 2.2) on the cfg1 volume, with errors against the oracle on 3
-        seeded 384x384 crops (true context).
+  cfg5  FastMemb in dense form (Sec. 2.2) on the cfg1 volume, FP32 and BF16, dense and sub-sampled
+        by 2 (the pruned fragment tree), with errors against the oracle on 3 seeded 384x384 crops
+        (true context; even crop origins, so the sub-sampled crops are the dense crops' even pixels).
 The reference arm (--impl reference) is the FP64 CPU oracle on bounded samples.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--configs 1,2,3,4]
@@ -450,8 +451,8 @@ def main():
     if "5" in configs:
         fm_params = synth.init_params(synth.FASTMEMB, synth.FASTMEMB_WEIGHT_SEED)
         rng = np.random.default_rng(synth.BASE_SEED + 5)
-        crops = [(int(rng.integers(0, Z)), int(rng.integers(0, H - 384)), int(rng.integers(0, W - 384)))
-                 for _ in range(3)]
+        crops = [(int(rng.integers(0, Z)), 2 * int(rng.integers(0, (H - 384) // 2)),
+                  2 * int(rng.integers(0, (W - 384) // 2))) for _ in range(3)]
         refs = [oracle.forward_region(synth.FASTMEMB, fm_params, vol[z], y, x0, 384, 384) for z, y, x0 in crops]
         p = {"crops_384": crops}
         for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16)):
@@ -464,6 +465,19 @@ def main():
             p[name] = {"mvox_s": mv, "ms": statistics.mean(ms),
                        "tflops": FASTMEMB_FLOP_PER_PX * mv * 1e6 / 1e12,
                        "error": err_metrics(got, refs, TOL[name])}
+            # sub-sampled output (factor 2, the pruned fragment tree): every slice's map at even
+            # rows and columns; throughput counted in input voxels (and output voxels)
+            osub = torch.empty((Z, H // 2, W // 2), dtype=torch.float32, device="cuda")
+            with torch.cuda.stream(stream):
+                ms = time_device(lambda: m.mb_infer_volume_subsampled(fm.handle, x, Z, H, W, 2, osub, m.MB_OUT_F32,
+                                                                      stream),
+                                 3 if name == "fp32" else args.steps, 1 if name == "fp32" else 3, stream, flush)
+            got = [osub[z, y // 2:(y + 384) // 2, x0 // 2:(x0 + 384) // 2].cpu().numpy() for z, y, x0 in crops]
+            p[name + "_subsampled2"] = {
+                "input_mvox_s": vox / (statistics.mean(ms) / 1e3) / 1e6,
+                "output_mvox_s": vox / 4 / (statistics.mean(ms) / 1e3) / 1e6, "ms": statistics.mean(ms),
+                "error": err_metrics(got, [r[::2, ::2] for r in refs], TOL[name])}
+            del osub
             fm.close()
         p["bf16"]["speedup_vs_fp32"] = p["bf16"]["mvox_s"] / p["fp32"]["mvox_s"]
         paths["cfg5_fastmemb_1024x1024x32"] = p

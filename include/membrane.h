@@ -142,6 +142,18 @@ mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
                           mb_out_type out_type, void* stream);
 
 /*
+ * Sub-sampled probability maps (Sec. 2.2, "Accelerating dense computation": the recursion tree of
+ * max-pooling fragments can be pruned to sub-sample the image). For factor 2, out[z][h2][w2] with
+ * h2 = ceil(h/2), w2 = ceil(w/2) holds the map of mb_infer_volume at rows 2i and columns 2j:
+ * only the branch of the first stride-2 pool's offset (0, 0) is evaluated (a real 2x2 stride-2
+ * max-pool after the first convolution, the later stages on the half grid), about a quarter of
+ * the dense work. FastMemb nets (FP32, BF16) and factor 2 only, else MB_ERR_UNSUPPORTED. out is
+ * float32 or uint8 as in mb_infer_volume. Device pointers only; asynchronous on `stream`.
+ */
+mb_status mb_infer_volume_subsampled(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
+                                     int32_t factor, void* out, mb_out_type out_type, void* stream);
+
+/*
  * Output rows [y0, y0 + rows) and columns [x0, x0 + cols) of every slice of the volume
  * in[z][h][w] into out[z][rows][cols], computed with the slice's true context (mirror padding
  * only at the slice borders). Values equal the corresponding pixels of mb_infer_volume.

@@ -215,12 +215,12 @@ mb_status teacher_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, i
 
 static mb_status fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
                                  int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
-                                 int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st) {
+                                 int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub = 1) {
     if (net->prec == MB_PREC_BF16)
         return bf16_fastmemb_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch,
-                                    out_slice, ot, st);
+                                    out_slice, ot, st, sub);
     return simt_fastmemb_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch, out_slice,
-                                ot, st);
+                                ot, st, sub);
 }
 
 static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,
@@ -568,6 +568,35 @@ mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
     }
     if (!din) return infer_host_volume(net, in, z, h, w, out, out_type);
     return net_region(net, in, z, h, w, 0, 0, h, w, out, out_type, (cudaStream_t)stream);
+}
+
+mb_status mb_infer_volume_subsampled(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int32_t factor,
+                                     void* out, mb_out_type out_type, void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(net));
+    if ((!in || !out) && z > 0) {
+        set_error("mb_infer_volume_subsampled: null buffer");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (out_type != MB_OUT_F32 && out_type != MB_OUT_U8) {
+        set_error("mb_infer_volume_subsampled: unknown output type %d", (int)out_type);
+        return MB_ERR_INVALID_ARG;
+    }
+    if (net->family != FAMILY_FASTMEMB || factor != 2) {
+        set_error("mb_infer_volume_subsampled: only FastMemb nets with factor 2 (got factor %d)", (int)factor);
+        return MB_ERR_UNSUPPORTED;
+    }
+    MB_TRY(check_slice(z, h, w));
+    MB_TRY(check_net_slice(net, h, w));
+    if (z == 0) return MB_OK;
+    API_GUARD(net)
+    if (!is_device_ptr(in) || !is_device_ptr(out)) {
+        set_error("mb_infer_volume_subsampled: device pointers only");
+        return MB_ERR_INVALID_ARG;
+    }
+    const int64_t h2 = (h + 1) / 2, w2 = (w + 1) / 2;
+    return fastmemb_region(net, in, z, h, w, w, h * w, 0, 0, h, w, out, w2, h2 * w2, out_type, (cudaStream_t)stream,
+                           2);
 }
 
 mb_status mb_infer_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,

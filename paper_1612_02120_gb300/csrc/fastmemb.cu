@@ -21,6 +21,10 @@
 // Domains for an output region rows x cols (radius 26):
 //   conv1 out (rows+49)^2 .. conv2 out (rows+42) .. conv3 out (rows+28) .. head out rows
 //   (each conv removes 3d, each max-filter d).
+// Sub-sampled output (factor 2: the dense map at even rows and columns, the fragment tree of
+// Sec. 2.2 pruned at the first pool): conv1 at full resolution on (2H2+48)^2, then a 2x2
+// stride-2 max-pool (read while staging, source stride 2) and the remaining stages on the half
+// grid with dilations 1, 2, 4: conv2 out H2+21, conv3 out H2+14, head out H2 = ceil(rows/2).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,6 +49,7 @@ struct FmArgs {
     int off_y, off_x;      // u8: input (r, c) reads slice (refl(r + off_y), refl(c + off_x))
     int d;                 // conv dilation = fragment step
     int dm;                // dilation of the 2x2 max-filter applied to the staged input (0: none)
+    int in_stride;         // f32: input (r, c) is the max-filter at source (s r, s c); 0 or 1: s = 1
     int out_h, out_w;
     int fy_tiles, fx_tiles;  // tiles per fragment along y / x
     void* out;
@@ -114,8 +119,9 @@ __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
             } else {
                 float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
                 if (ok) {
+                    const int st = a.in_stride > 1 ? a.in_stride : 1;
                     const float* p = static_cast<const float*>(a.in) + (int64_t)zi * a.in_slice +
-                                     ((int64_t)gy * a.in_pitch + gx) * CIN + c0;
+                                     ((int64_t)(st * gy) * a.in_pitch + st * gx) * CIN + c0;
                     v0 = ld4(p);
                     v1 = ld4(p + 4);
                     if (a.dm > 0) {
@@ -234,23 +240,49 @@ mb_status launch_fm(FmArgs a, int nz, cudaStream_t st) {
 
 }  // namespace
 
-static size_t fm_ws_per_slice(int64_t rows, int64_t cols) {
-    return (size_t)((rows + 49) * (cols + 49) + (rows + 42) * (cols + 42) + (rows + 28) * (cols + 28)) * 32 *
-           sizeof(float);
+// Per-stage geometry of one FastMemb pass: extents of the four conv outputs (conv1 at full
+// resolution; the rest at full resolution for the dense map, on the half grid when sub-sampled),
+// the dilation of each conv, and how each conv reads its input (max-filter dilation, stride).
+struct FmGeom {
+    int64_t r[4], c[4];   // conv outputs: act1, act2, act3, map
+    int d[4], dm[4], st[4];
+};
+
+static FmGeom fm_geom(int64_t rows, int64_t cols, int sub) {
+    FmGeom g{};
+    if (sub == 2) {
+        const int64_t h2 = (rows + 1) / 2, w2 = (cols + 1) / 2;
+        const int64_t r[4] = {2 * h2 + 48, h2 + 21, h2 + 14, h2}, c[4] = {2 * w2 + 48, w2 + 21, w2 + 14, w2};
+        const int d[4] = {1, 1, 2, 4}, dm[4] = {0, 1, 1, 2}, st[4] = {1, 2, 1, 1};
+        for (int i = 0; i < 4; ++i) g.r[i] = r[i], g.c[i] = c[i], g.d[i] = d[i], g.dm[i] = dm[i], g.st[i] = st[i];
+    } else {
+        const int64_t r[4] = {rows + 49, rows + 42, rows + 28, rows}, c[4] = {cols + 49, cols + 42, cols + 28, cols};
+        const int d[4] = {1, 2, 4, 8}, dm[4] = {0, 1, 2, 4}, st[4] = {1, 1, 1, 1};
+        for (int i = 0; i < 4; ++i) g.r[i] = r[i], g.c[i] = c[i], g.d[i] = d[i], g.dm[i] = dm[i], g.st[i] = st[i];
+    }
+    return g;
+}
+
+// Input domain of conv i >= 1: the (max-filtered, strided) view of conv i-1's output: positions r
+// with st r + dm inside the source.
+static inline int64_t fm_in_extent(const FmGeom& g, int i, bool rows) {
+    const int64_t src = rows ? g.r[i - 1] : g.c[i - 1];
+    return (src - 1 - g.dm[i]) / g.st[i] + 1;
 }
 
 mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
                                int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
-                               int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st) {
+                               int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub) {
     if (z == 0 || rows == 0 || cols == 0) return MB_OK;
-    const int64_t r1 = rows + 49, c1 = cols + 49, r2 = rows + 42, c2 = cols + 42, r3 = rows + 28, c3 = cols + 28;
-    const size_t per = fm_ws_per_slice(rows, cols);
+    const FmGeom g = fm_geom(rows, cols, sub);
+    const size_t per = (size_t)(g.r[0] * g.c[0] + g.r[1] * g.c[1] + g.r[2] * g.c[2]) * 32 * sizeof(float);
     const size_t budget = (size_t)3 << 30;
     const int64_t zc = std::min<int64_t>(std::min<int64_t>(std::max<size_t>(1, budget / per), 65535), z);
     MB_TRY(net->ws.ensure(per * (size_t)zc));
-    float* act1 = static_cast<float*>(net->ws.ptr);
-    float* act2 = act1 + (size_t)zc * r1 * c1 * 32;
-    float* act3 = act2 + (size_t)zc * r2 * c2 * 32;
+    float* act[3];
+    act[0] = static_cast<float*>(net->ws.ptr);
+    act[1] = act[0] + (size_t)zc * g.r[0] * g.c[0] * 32;
+    act[2] = act[1] + (size_t)zc * g.r[1] * g.c[1] * 32;
     // SIMT layout: per conv Wt[ci][ky][kx][co] then b[co]; co = 64, 64, 64, 2
     const float* w1 = net->d_simt;
     const float* b1 = w1 + 16 * 64;
@@ -260,83 +292,59 @@ mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
     const float* b3 = w3 + 32 * 16 * 64;
     const float* w4 = b3 + 64;
     const float* b4 = w4 + 32 * 16 * 2;
+    const float* ws[4] = {w1, w2, w3, w4};
+    const float* bs[4] = {b1, b2, b3, b4};
     for (int64_t z0 = 0; z0 < z; z0 += zc) {
         const int nz = (int)std::min<int64_t>(zc, z - z0);
         FmArgs a{};
         a.in = in + z0 * in_slice;
         a.in_slice = in_slice;
         a.in_pitch = in_pitch;
-        a.in_rows = (int)(r1 + 3);
-        a.in_cols = (int)(c1 + 3);
+        a.in_rows = (int)(g.r[0] + 3);
+        a.in_cols = (int)(g.c[0] + 3);
         a.src_h = (int)h;
         a.src_w = (int)w;
         a.off_y = (int)(y0 - 26);
         a.off_x = (int)(x0 - 26);
         a.d = 1;
-        a.dm = 0;
-        a.out_h = (int)r1;
-        a.out_w = (int)c1;
-        a.out = act1;
-        a.out_slice = r1 * c1 * 32;
-        a.out_pitch = c1;
+        a.out_h = (int)g.r[0];
+        a.out_w = (int)g.c[0];
+        a.out = act[0];
+        a.out_slice = g.r[0] * g.c[0] * 32;
+        a.out_pitch = g.c[0];
         a.wt = w1;
         a.bias = b1;
         MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT>(a, nz, st)));
-
-        FmArgs b{};
-        b.in = act1;
-        b.in_slice = r1 * c1 * 32;
-        b.in_pitch = c1;
-        b.in_rows = (int)(r1 - 1);
-        b.in_cols = (int)(c1 - 1);
-        b.d = 2;
-        b.dm = 1;
-        b.out_h = (int)r2;
-        b.out_w = (int)c2;
-        b.out = act2;
-        b.out_slice = r2 * c2 * 32;
-        b.out_pitch = c2;
-        b.wt = w2;
-        b.bias = b2;
-        MB_TRY((launch_fm<32, 8, 64, 8, FM_IN_F32, FM_OUT_MAXOUT>(b, nz, st)));
-
-        FmArgs c = b;
-        c.in = act2;
-        c.in_slice = r2 * c2 * 32;
-        c.in_pitch = c2;
-        c.in_rows = (int)(r2 - 2);
-        c.in_cols = (int)(c2 - 2);
-        c.d = 4;
-        c.dm = 2;
-        c.out_h = (int)r3;
-        c.out_w = (int)c3;
-        c.out = act3;
-        c.out_slice = r3 * c3 * 32;
-        c.out_pitch = c3;
-        c.wt = w3;
-        c.bias = b3;
-        MB_TRY((launch_fm<32, 8, 64, 8, FM_IN_F32, FM_OUT_MAXOUT>(c, nz, st)));
-
-        FmArgs e = c;
-        e.in = act3;
-        e.in_slice = r3 * c3 * 32;
-        e.in_pitch = c3;
-        e.in_rows = (int)(r3 - 4);
-        e.in_cols = (int)(c3 - 4);
-        e.d = 8;
-        e.dm = 4;
-        e.out_h = (int)rows;
-        e.out_w = (int)cols;
-        e.out_slice = out_slice;
-        e.out_pitch = out_pitch;
-        e.wt = w4;
-        e.bias = b4;
-        if (ot == MB_OUT_F32) {
-            e.out = static_cast<float*>(out) + z0 * out_slice;
-            MB_TRY((launch_fm<32, 8, 2, 2, FM_IN_F32, FM_OUT_SOFTMAX_F32>(e, nz, st)));
-        } else {
-            e.out = static_cast<uint8_t*>(out) + z0 * out_slice;
-            MB_TRY((launch_fm<32, 8, 2, 2, FM_IN_F32, FM_OUT_SOFTMAX_U8>(e, nz, st)));
+        for (int i = 1; i < 4; ++i) {
+            FmArgs b{};
+            b.in = act[i - 1];
+            b.in_slice = g.r[i - 1] * g.c[i - 1] * 32;
+            b.in_pitch = g.c[i - 1];
+            b.in_rows = (int)fm_in_extent(g, i, true);
+            b.in_cols = (int)fm_in_extent(g, i, false);
+            b.d = g.d[i];
+            b.dm = g.dm[i];
+            b.in_stride = g.st[i];
+            b.out_h = (int)g.r[i];
+            b.out_w = (int)g.c[i];
+            b.wt = ws[i];
+            b.bias = bs[i];
+            if (i < 3) {
+                b.out = act[i];
+                b.out_slice = g.r[i] * g.c[i] * 32;
+                b.out_pitch = g.c[i];
+                MB_TRY((launch_fm<32, 8, 64, 8, FM_IN_F32, FM_OUT_MAXOUT>(b, nz, st)));
+            } else {
+                b.out_slice = out_slice;
+                b.out_pitch = out_pitch;
+                if (ot == MB_OUT_F32) {
+                    b.out = static_cast<float*>(out) + z0 * out_slice;
+                    MB_TRY((launch_fm<32, 8, 2, 2, FM_IN_F32, FM_OUT_SOFTMAX_F32>(b, nz, st)));
+                } else {
+                    b.out = static_cast<uint8_t*>(out) + z0 * out_slice;
+                    MB_TRY((launch_fm<32, 8, 2, 2, FM_IN_F32, FM_OUT_SOFTMAX_U8>(b, nz, st)));
+                }
+            }
         }
     }
     return MB_OK;
@@ -346,19 +354,20 @@ mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
 // the head on the tensor cores (fastmemb_tc.cu); activations between layers are BF16 [slice][y][x][32].
 mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
                                int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
-                               int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st) {
+                               int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub) {
     if (z == 0 || rows == 0 || cols == 0) return MB_OK;
     MB_TRY(fm_tc_poll_error(net));
-    const int64_t r1 = rows + 49, c1 = cols + 49, r2 = rows + 42, c2 = cols + 42, r3 = rows + 28, c3 = cols + 28;
+    const FmGeom g = fm_geom(rows, cols, sub);
     auto up = [](int64_t n) { return (n + 127) & ~(int64_t)127; };  // 256-byte aligned sub-buffers
-    const int64_t n1 = up(r1 * c1 * 32), n2 = up(r2 * c2 * 32), n3 = up(r3 * c3 * 32);
-    const size_t per = (size_t)(n1 + n2 + n3) * 2;
+    const int64_t n[3] = {up(g.r[0] * g.c[0] * 32), up(g.r[1] * g.c[1] * 32), up(g.r[2] * g.c[2] * 32)};
+    const size_t per = (size_t)(n[0] + n[1] + n[2]) * 2;
     const size_t budget = (size_t)3 << 30;
     const int64_t zc = std::min<int64_t>(std::min<int64_t>(std::max<size_t>(1, budget / per), 65535), z);
     MB_TRY(net->ws.ensure(per * (size_t)zc));
-    __nv_bfloat16* act1 = static_cast<__nv_bfloat16*>(net->ws.ptr);
-    __nv_bfloat16* act2 = act1 + (size_t)zc * n1;
-    __nv_bfloat16* act3 = act2 + (size_t)zc * n2;
+    __nv_bfloat16* act[3];
+    act[0] = static_cast<__nv_bfloat16*>(net->ws.ptr);
+    act[1] = act[0] + (size_t)zc * n[0];
+    act[2] = act[1] + (size_t)zc * n[1];
     const float* w1 = net->d_simt;
     const float* b1 = w1 + 16 * 64;
     const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
@@ -368,29 +377,29 @@ mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
         a.in = in + z0 * in_slice;
         a.in_slice = in_slice;
         a.in_pitch = in_pitch;
-        a.in_rows = (int)(r1 + 3);
-        a.in_cols = (int)(c1 + 3);
+        a.in_rows = (int)(g.r[0] + 3);
+        a.in_cols = (int)(g.c[0] + 3);
         a.src_h = (int)h;
         a.src_w = (int)w;
         a.off_y = (int)(y0 - 26);
         a.off_x = (int)(x0 - 26);
         a.d = 1;
-        a.dm = 0;
-        a.out_h = (int)r1;
-        a.out_w = (int)c1;
-        a.out = act1;
-        a.out_slice = n1;
-        a.out_pitch = c1;
+        a.out_h = (int)g.r[0];
+        a.out_w = (int)g.c[0];
+        a.out = act[0];
+        a.out_slice = n[0];
+        a.out_pitch = g.c[0];
         a.wt = w1;
         a.bias = b1;
         MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT_BF16>(a, nz, st)));
-        MB_TRY(fm_tc_layer(net, 0, act1, n1, c1, (int)(r1 - 1), (int)(c1 - 1), 1, act2, n2, c2, (int)r2, (int)c2, 2,
-                           nz, 0, st));
-        MB_TRY(fm_tc_layer(net, 1, act2, n2, c2, (int)(r2 - 2), (int)(c2 - 2), 2, act3, n3, c3, (int)r3, (int)c3, 4,
-                           nz, 0, st));
-        MB_TRY(fm_tc_layer(net, 2, act3, n3, c3, (int)(r3 - 4), (int)(c3 - 4), 4,
-                           static_cast<uint8_t*>(out) + z0 * out_slice * osz, out_slice, out_pitch, (int)rows,
-                           (int)cols, 8, nz, ot == MB_OUT_U8, st));
+        for (int i = 1; i < 4; ++i) {
+            const bool head = i == 3;
+            void* o = head ? static_cast<void*>(static_cast<uint8_t*>(out) + z0 * out_slice * osz) : act[i];
+            MB_TRY(fm_tc_layer(net, i - 1, act[i - 1], n[i - 1], g.c[i - 1], g.r[i - 1], g.c[i - 1],
+                               (int)fm_in_extent(g, i, true), (int)fm_in_extent(g, i, false), g.dm[i], g.st[i], o,
+                               head ? out_slice : n[i], head ? out_pitch : g.c[i], (int)g.r[i], (int)g.c[i], g.d[i],
+                               nz, head && ot == MB_OUT_U8, st));
+        }
     }
     return fm_tc_poll_error(net);
 }

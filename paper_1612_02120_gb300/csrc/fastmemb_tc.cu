@@ -72,7 +72,9 @@ struct FmTcParams {
     const uint8_t* wpack;      // B operands then 64 FP32 biases
     int* err;
     int64_t in_slice, in_pitch, out_slice, out_pitch;  // elements / pixels
-    int in_rows, in_cols;      // domain of the max-filtered input
+    int in_rows, in_cols;      // domain of the (max-filtered, strided) input
+    int stride;                // input (r, c) is the max-filter at source (stride r, stride c)
+    int64_t src_cols;          // source pixels per row that may be read (prefetch bound)
     int out_h, out_w;
     int d, dm;                 // conv dilation, max-filter dilation
     int nz, n_strips, n_chunks, rows_per_item, n_items;
@@ -328,7 +330,9 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
             const FmItem it = fm_item(p, k);
             if (it.rows == 0) continue;
             const __nv_bfloat16* src = p.in + (int64_t)it.z * p.in_slice;
-            const int pf_cols = min(128 + 3 * d + p.dm, p.in_cols + p.dm - it.x0);  // source pixels a row reads
+            // source pixels one staged row reads: stride (npix - 1) + dm + 1 from stride x0, clipped
+            const int sx0 = p.stride * it.x0;
+            const int pf_cols = (int)min((int64_t)(p.stride * (127 + 3 * d) + p.dm + 1), p.src_cols - sx0);
             for (int u = grp; u < it.rows + 3; u += 2) {
                 const uint32_t q = row_seq + u, slot = q % kFRing;
                 const int yin = it.ry + d * (it.m0 + u);
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                 if (pt == 0 && u + kFPrefetch < it.rows + 3) {
                     const int yp = it.ry + d * (it.m0 + u + kFPrefetch);
                     if (yp < p.in_rows && pf_cols > 0) {
-                        const __nv_bfloat16* r0 = src + ((int64_t)yp * p.in_pitch + it.x0) * 32;
+                        const __nv_bfloat16* r0 = src + ((int64_t)(p.stride * yp) * p.in_pitch + sx0) * 32;
                         ptx::prefetch_l2_bulk(r0, (uint32_t)pf_cols * 64u);
                         ptx::prefetch_l2_bulk(r0 + dyo, (uint32_t)pf_cols * 64u);
                     }
@@ -348,7 +352,8 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                     const int xin = it.x0 + (e >> 2);
                     v[i] = make_uint4(0, 0, 0, 0);
                     if (e < ntask && yin < p.in_rows && xin < p.in_cols) {
-                        const __nv_bfloat16* a = src + ((int64_t)yin * p.in_pitch + xin) * 32 + (e & 3) * 8;
+                        const __nv_bfloat16* a =
+                            src + ((int64_t)(p.stride * yin) * p.in_pitch + p.stride * xin) * 32 + (e & 3) * 8;
                         const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a));
                         const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a + dxo));
                         const uint4 r2 = __ldg(reinterpret_cast<const uint4*>(a + dyo));
@@ -503,9 +508,9 @@ mb_status fm_tc_poll_error(mb_net* net) {
     return MB_OK;
 }
 
-mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int in_rows,
-                      int in_cols, int dm, void* out, int64_t out_slice, int64_t out_pitch, int out_h, int out_w,
-                      int d, int nz, int out_u8, cudaStream_t st) {
+mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int64_t src_rows,
+                      int64_t src_cols, int in_rows, int in_cols, int dm, int stride, void* out, int64_t out_slice,
+                      int64_t out_pitch, int out_h, int out_w, int d, int nz, int out_u8, cudaStream_t st) {
     FmTcState* S = reinterpret_cast<FmTcState*>(net->fm_state);
     if (!S || !S->d_wpack[layer]) {
         set_error("FastMemb tensor-core weights not prepared");
@@ -522,6 +527,12 @@ mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, 
     p.out_pitch = out_pitch;
     p.in_rows = in_rows;
     p.in_cols = in_cols;
+    p.stride = stride;
+    p.src_cols = src_cols;
+    if ((int64_t)stride * (in_rows - 1) + dm >= src_rows || (int64_t)stride * (in_cols - 1) + dm >= src_cols) {
+        set_error("FastMemb: input domain exceeds its source");
+        return MB_ERR_INVALID_ARG;
+    }
     p.out_h = out_h;
     p.out_w = out_w;
     p.d = d;

@@ -94,23 +94,27 @@ mb_status simt_student_region(mb_net* net, const uint8_t* in, int64_t z, int64_t
                               int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
                               int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
                               mb_out_type ot, cudaStream_t st);
+// FastMemb region (FP32 / BF16); sub = 1: the dense map, sub = 2: the map at even rows and columns
+// of the region (out is ceil(rows/2) x ceil(cols/2)).
 mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
                                int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
                                int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
-                               mb_out_type ot, cudaStream_t st);
+                               mb_out_type ot, cudaStream_t st, int sub);
 mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
                                int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
                                int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
-                               mb_out_type ot, cudaStream_t st);
+                               mb_out_type ot, cudaStream_t st, int sub);
 // FastMemb tensor-core layers (fastmemb_tc.cu): pack split BF16 B operands of the two 32->64 convs
 // and the head, launch one (0: conv dilation 2, 1: conv dilation 4, 2: head dilation 8 with the
 // softmax, FP32 or uint8 out), poll the device-side wait error word.
 mb_status fm_tc_prepare(mb_net* net);
 void fm_tc_release(mb_net* net);
 mb_status fm_tc_poll_error(mb_net* net);
-mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int in_rows,
-                      int in_cols, int dm, void* out, int64_t out_slice, int64_t out_pitch, int out_h, int out_w,
-                      int d, int nz, int out_u8, cudaStream_t st);
+// in: [slice][src_rows][src_cols(pitch)][32] BF16; the conv reads input (r, c) = 2x2 max (dilation
+// dm) at source (stride r, stride c), for r < in_rows, c < in_cols.
+mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int64_t src_rows,
+                      int64_t src_cols, int in_rows, int in_cols, int dm, int stride, void* out, int64_t out_slice,
+                      int64_t out_pitch, int out_h, int out_w, int d, int nz, int out_u8, cudaStream_t st);
 // FP32 teacher activations after the two max-filters: per-channel amax over n slices (device out[64]).
 mb_status simt_teacher_amax(mb_net* net, const uint8_t* in, int64_t n, int64_t h, int64_t w, float* d_amax,
                             cudaStream_t st);

@@ -22,7 +22,7 @@ EXPORTED = (
     "mb_net_create", "mb_net_destroy", "mb_net_param_count", "mb_load_weights", "mb_get_weights",
     "mb_calibrate_fp8", "mb_infer_volume", "mb_infer_region", "mb_infer_batch", "mb_infer_batch_per_block",
     "mb_autotune", "mb_student_loss_grad", "mb_student_train", "mb_infer_cascade", "mb_status_string",
-    "mb_last_error", "mb_launch_count", "mb_infer_volume_noalloc",
+    "mb_last_error", "mb_launch_count", "mb_infer_volume_noalloc", "mb_infer_volume_subsampled",
 )
 
 
@@ -81,6 +81,7 @@ def load() -> ctypes.CDLL:
         "mb_last_error": ([], ctypes.c_char_p),
         "mb_launch_count": ([], i64),
         "mb_infer_volume_noalloc": ([p, p, i64, i64, i64, p, i32, p], st),
+        "mb_infer_volume_subsampled": ([p, p, i64, i64, i64, i32, p, i32, p], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -176,6 +177,12 @@ def mb_calibrate_fp8(net, slices, n, h, w, amax_out=None, stream=None) -> None:
 def mb_infer_volume(net, inp, z, h, w, out, out_type=MB_OUT_F32, stream=None) -> None:
     check(load().mb_infer_volume(net, ptr(inp), z, h, w, ptr(out), out_type, stream_handle(stream)),
           "mb_infer_volume")
+
+
+def mb_infer_volume_subsampled(net, inp, z, h, w, factor, out, out_type=MB_OUT_F32, stream=None) -> None:
+    """FastMemb map at even rows and columns: out is z x ceil(h/2) x ceil(w/2)."""
+    check(load().mb_infer_volume_subsampled(net, ptr(inp), z, h, w, factor, ptr(out), out_type,
+                                            stream_handle(stream)), "mb_infer_volume_subsampled")
 
 
 def mb_infer_volume_noalloc(net, inp, z, h, w, out, out_type=MB_OUT_F32, stream=None) -> None:

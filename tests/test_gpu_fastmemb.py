@@ -222,3 +222,57 @@ def test_bf16_timed_out_device_wait_is_reported_and_context_survives(net_bf16, m
     assert lib.mb_infer_volume(net_bf16.handle, x.data_ptr(), 1, 64, 80, out.data_ptr(), 0, None) == m.MB_OK
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy(), ref)
+
+
+# ---- sub-sampled output (factor 2): the pruned fragment tree ------------------------------------
+
+def infer_sub(net, vol_u8, out_type=0):
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    z, h, w = vol_u8.shape
+    x = torch.from_numpy(np.ascontiguousarray(vol_u8)).cuda()
+    out = torch.empty((z, (h + 1) // 2, (w + 1) // 2), dtype=torch.float32 if out_type == 0 else torch.uint8,
+                      device="cuda")
+    m.mb_infer_volume_subsampled(net.handle, x, z, h, w, 2, out, out_type)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", [(1, 27, 27), (2, 64, 45), (1, 301, 283), (1, 200, 530)])
+def test_subsampled_equals_dense_at_even_positions_bitwise(net, net_bf16, shape):
+    """Each kept pixel is computed with the same arithmetic as in the dense map, so both FP32 and
+    BF16 sub-sampled maps equal the dense maps at even rows and columns bitwise."""
+    z, h, w = shape
+    v = synth.em_volume(9900 + h * w, z, h, w)
+    for n in (net, net_bf16):
+        np.testing.assert_array_equal(infer_sub(n, v), infer(n, v)[:, ::2, ::2])
+
+
+def test_subsampled_matches_oracle(net, net_bf16):
+    v = synth.em_volume(9950, 2, 150, 133)
+    prm = fm_params()
+    p32, p16 = infer_sub(net, v), infer_sub(net_bf16, v)
+    for zi in range(2):
+        ref = oracle.forward_region(F, prm, v[zi])[::2, ::2]
+        assert within(oracle.metrics(p32[zi], ref), TOL["fp32"])
+        assert within(oracle.metrics(p16[zi], ref), TOL["bf16"])
+    np.testing.assert_array_equal(infer_sub(net, v, 1), infer(net, v, 1)[:, ::2, ::2])
+
+
+def test_subsampled_error_codes(net):
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    lib = m.load()
+    x = torch.zeros((1, 64, 64), dtype=torch.uint8, device="cuda")
+    out = torch.empty((1, 32, 32), dtype=torch.float32, device="cuda")
+    assert lib.mb_infer_volume_subsampled(net.handle, x.data_ptr(), 1, 64, 64, 3, out.data_ptr(), 0,
+                                          None) == m.MB_ERR_UNSUPPORTED
+    host = np.zeros((1, 32, 32), dtype=np.float32)
+    assert lib.mb_infer_volume_subsampled(net.handle, x.data_ptr(), 1, 64, 64, 2, host.ctypes.data, 0,
+                                          None) == m.MB_ERR_INVALID_ARG
+    assert lib.mb_infer_volume_subsampled(net.handle, x.data_ptr(), 1, 26, 64, 2, out.data_ptr(), 0,
+                                          None) == m.MB_ERR_SHAPE
+    t = make_net(synth.TEACHER, m.MB_PREC_FP32, synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED))
+    assert lib.mb_infer_volume_subsampled(t.handle, x.data_ptr(), 1, 64, 64, 2, out.data_ptr(), 0,
+                                          None) == m.MB_ERR_UNSUPPORTED
+    t.close()
