@@ -54,9 +54,25 @@ FASTMEMB = (
     (HEAD_SOFTMAX2, 4, 32, 2, 0, 8, 1),
 )
 
+# FastMemb_3nm (Sec. 2.2, "A subsampling CNN for 3 nm data"): FastMemb with one more [conv4x4 ->
+# max-out 2 -> pool] stage, for 3 nm images: dilations 1, 2, 4, 8 and the head at 16. Field of view
+# 109x109 (the four-pair structure Sec. 3.2 gives 109 for), 100,610 parameters.
+FASTMEMB_3NM = (
+    (CONV, 4, 1, 32, 0, 1, 2),
+    (MAXFILTER, 2, 32, 32, 0, 1, 1),
+    (CONV, 4, 32, 32, 0, 2, 2),
+    (MAXFILTER, 2, 32, 32, 0, 2, 1),
+    (CONV, 4, 32, 32, 0, 4, 2),
+    (MAXFILTER, 2, 32, 32, 0, 4, 1),
+    (CONV, 4, 32, 32, 0, 8, 2),
+    (MAXFILTER, 2, 32, 32, 0, 8, 1),
+    (HEAD_SOFTMAX2, 4, 32, 2, 0, 16, 1),
+)
+
 TEACHER_WEIGHT_SEED = 20161206
 STUDENT_WEIGHT_SEED = 20161207
 FASTMEMB_WEIGHT_SEED = 20161208
+FASTMEMB_3NM_WEIGHT_SEED = 20161209
 BASE_SEED = 1612021200  # + workload index
 
 

@@ -275,3 +275,42 @@ def test_subsampled_output_is_the_pruned_fragment_tree(shape):
     pruned = pruned_fragments_forward(np.pad(s.astype(np.float64) / 255.0, 26, mode="reflect"), prm)
     assert not np.isnan(pruned).any() and pruned.shape == dense[::2, ::2].shape
     np.testing.assert_allclose(pruned, dense[::2, ::2], rtol=0, atol=1e-12)
+
+
+# ---- FastMemb_3nm (Sec. 2.2, "A subsampling CNN for 3 nm data") ------------------------------------
+
+F3 = synth.FASTMEMB_3NM
+
+
+def test_fastmemb_3nm_field_of_view_parameters_and_flop_ratio():
+    """One more conv/pool pair: field of view 109 by the arithmetic of the architecture, the value
+    Sec. 3.2 prints for the same four-pair structure (this section prints 105); 100,610
+    parameters; 4x the pixels at 100,352 vs 67,584 multiplications per pixel = 5.94x the FLOPs
+    of FastMemb_6nm, against the printed 5.86x (text, "486 % more") and 5.68x (table)."""
+    assert oracle.net_radius(F3) == 54
+    assert oracle.param_count(F3) == synth.param_count(F3) == 100610
+    per_px = lambda layers: sum(l[3] * l[6] * l[2] * l[1] ** 2 for l in layers if l[0] != synth.MAXFILTER)
+    assert per_px(F) == 67584 and per_px(F3) == 100352
+    ratio = 4 * per_px(F3) / per_px(F)
+    assert abs(ratio - 5.86) / 5.86 < 0.02 and abs(ratio - 5.68) / 5.68 < 0.05, ratio
+    n = 109
+    for _ in range(4):
+        n = (n - 3) // 2
+    assert n - 3 == 1
+
+
+def test_fastmemb_3nm_dense_equals_patch_calculation():
+    prm = synth.init_params(F3, synth.FASTMEMB_3NM_WEIGHT_SEED).astype(np.float64)
+    parts = split_params(F3, prm)
+    s = synth.em_slice(7006, 70, 64)
+    dense = oracle.forward_region(F3, prm, s)
+    padded = np.pad(s.astype(np.float64) / 255.0, 54, mode="reflect")
+    rng = np.random.default_rng(80)
+    pix = [(0, 0), (69, 63), (0, 63), (35, 31)] + [tuple(int(v) for v in rng.integers(0, (70, 64))) for _ in range(6)]
+    for i, j in pix:
+        x = padded[i:i + 109, j:j + 109][None]
+        for W, b in parts[:-1]:
+            x = np_maxpool2_stride2(np_maxout(np_conv(x, W, b), 2))
+        z = np_conv(x, *parts[-1])
+        assert z.shape == (2, 1, 1)
+        assert abs(float(np_softmax_class1(z)[0, 0]) - dense[i, j]) < 1e-12
