@@ -13,6 +13,8 @@ the same through the C ABI with pinned HOST buffers (copies inside the timed reg
         memory; errors on 3 seeded 512x512 crops (true context);
   cfg4  student training (200 x 512^2, batch 32, lr 1e-3, 2000 steps) on FP32-teacher maps, then
         student-only and cascade (teacher fallback on 256^2 tiles) on the cfg3 volume;
+  cfg6  FastMemb_3nm (one more stage, 109 field of view) on 2048x2048x8 (3 nm images), FP32 and
+        BF16, dense and sub-sampled by 2 (a 6 nm output map), errors on 2 seeded 256x256 crops;
   cfg5  FastMemb in dense form (Sec. 2.2) on the cfg1 volume, FP32 and BF16, dense and sub-sampled
         by 2 (the pruned fragment tree), with errors against the oracle on 3 seeded 384x384 crops
         (true context; even crop origins, so the sub-sampled crops are the dense crops' even pixels).
@@ -41,6 +43,7 @@ FLOP_PER_PX = 2 * (25 * 32 + 2 * 25 * 32 * 32 + 32)        # 104,064
 TENSOR_FLOP_PER_PX = 2 * 2 * 25 * 32 * 32                   # 102,400 (layers 2 and 3)
 STUDENT_FLOP_PER_PX = 2 * (9 * 16 + 9 * 16 * 16 + 16)       # 4,928
 FASTMEMB_FLOP_PER_PX = 2 * (16 * 64 + 2 * 16 * 32 * 64 + 16 * 32 * 2)  # 135,168
+FASTMEMB3_FLOP_PER_PX = 2 * (16 * 64 + 3 * 16 * 32 * 64 + 16 * 32 * 2)  # 200,704
 # DRAM bytes per output voxel of tc_fused_teacher (BF16), from the ncu capture summarised in
 # profiles/tc_fused_teacher_bf16_1024x1024x4.md; None when the kernel changed since.
 TC_TRAFFIC_PER_VOX = None
@@ -193,7 +196,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--configs", default="1,2,3,4,5", help="extra configurations measured after the headline")
+    ap.add_argument("--configs", default="1,2,3,4,5,6", help="extra configurations measured after the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -481,6 +484,41 @@ def main():
             fm.close()
         p["bf16"]["speedup_vs_fp32"] = p["bf16"]["mvox_s"] / p["fp32"]["mvox_s"]
         paths["cfg5_fastmemb_1024x1024x32"] = p
+    # ---- cfg6: FastMemb_3nm on 2048x2048x8 ----------------------------------------------------------
+    if "6" in configs:
+        Z6, H6, W6 = 8, 2048, 2048
+        f3 = synth.FASTMEMB_3NM
+        f3_params = synth.init_params(f3, synth.FASTMEMB_3NM_WEIGHT_SEED, center_head=True)
+        vol6 = synth.em_volume(synth.BASE_SEED + 6, Z6, H6, W6)
+        x6 = torch.from_numpy(vol6).cuda()
+        o6 = torch.empty((Z6, H6, W6), dtype=torch.float32, device="cuda")
+        s6 = torch.empty((Z6, H6 // 2, W6 // 2), dtype=torch.float32, device="cuda")
+        v6 = Z6 * H6 * W6
+        rng = np.random.default_rng(synth.BASE_SEED + 6)
+        crops = [(int(rng.integers(0, Z6)), 2 * int(rng.integers(0, (H6 - 256) // 2)),
+                  2 * int(rng.integers(0, (W6 - 256) // 2))) for _ in range(2)]
+        refs = [oracle.forward_region(f3, f3_params, vol6[z], y, x0, 256, 256) for z, y, x0 in crops]
+        p = {"crops_256": crops, "flop_per_px": FASTMEMB3_FLOP_PER_PX}
+        for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16)):
+            fm = m.Net(f3, prec, local, f3_params)
+            k, w0 = (2, 1) if name == "fp32" else (args.steps, 3)
+            with torch.cuda.stream(stream):
+                ms = time_device(lambda: m.mb_infer_volume(fm.handle, x6, Z6, H6, W6, o6, m.MB_OUT_F32, stream),
+                                 k, w0, stream, flush)
+                ms_s = time_device(lambda: m.mb_infer_volume_subsampled(fm.handle, x6, Z6, H6, W6, 2, s6,
+                                                                        m.MB_OUT_F32, stream), k, w0, stream, flush)
+            mv = v6 / (statistics.mean(ms) / 1e3) / 1e6
+            p[name] = {"mvox_s": mv, "ms": statistics.mean(ms), "tflops": FASTMEMB3_FLOP_PER_PX * mv * 1e6 / 1e12,
+                       "error": err_metrics([o6[z, y:y + 256, x0:x0 + 256].cpu().numpy() for z, y, x0 in crops],
+                                            refs, TOL[name])}
+            p[name + "_subsampled2"] = {
+                "input_mvox_s": v6 / (statistics.mean(ms_s) / 1e3) / 1e6,
+                "output_mvox_s": v6 / 4 / (statistics.mean(ms_s) / 1e3) / 1e6, "ms": statistics.mean(ms_s),
+                "error": err_metrics([s6[z, y // 2:(y + 256) // 2, x0 // 2:(x0 + 256) // 2].cpu().numpy()
+                                      for z, y, x0 in crops], [r[::2, ::2] for r in refs], TOL[name])}
+            fm.close()
+        paths["cfg6_fastmemb3nm_2048x2048x8"] = p
+        del x6, o6, s6
     if paths:
         line["paths"] = paths
     if rank == 0 and not args.no_cpu_baseline:

@@ -22,7 +22,7 @@
  *    host pointers are synchronous on return.
  *  - Sizes are element counts; pitches are in elements of the buffer's type.
  *  - Slices need h and w above the net's radius so reflect-101 padding is defined (>= 8 for the
- *    teacher and student, >= 27 for FastMemb); else MB_ERR_SHAPE.
+ *    teacher and student, >= 27 for FastMemb, >= 55 for FastMemb_3nm); else MB_ERR_SHAPE.
  *  - A net/precision combination without a kernel returns MB_ERR_UNSUPPORTED.
  *  - Host-side fault injection for tests: environment MB_FAULT_OOM=1 makes every library
  *    allocation fail with MB_ERR_OOM.
@@ -72,7 +72,9 @@ typedef enum { MB_CONV = 0, MB_MAXFILTER = 1, MB_HEAD_SIGMOID = 2, MB_HEAD_SOFTM
  * 1->16 ReLU, conv3x3 16->16 ReLU, head 16->1) in FP32 and BF16; and FastMemb in dense form
  * (Sec. 2.2: conv4x4 1->32 G=2 d=1, maxfilter d=1, conv4x4 32->32 G=2 d=2, maxfilter d=2,
  * conv4x4 32->32 G=2 d=4, maxfilter d=4, softmax head conv4x4 32->2 d=8; no ReLU; radius 26,
- * so its slices need h, w >= 27) in FP32.
+ * so its slices need h, w >= 27) and FastMemb_3nm (Sec. 2.2, "A subsampling CNN for 3 nm data":
+ * one more stage, conv4x4 32->32 G=2 d=8 and maxfilter d=8, then the head at d=16; radius 54,
+ * slices h, w >= 55), both in FP32 and BF16.
  */
 typedef struct {
     int32_t kind, ksize, dilation, cin, cout, relu, maxout_groups;

@@ -121,6 +121,12 @@ static int detect_family(const mb_layer_desc* L, int n) {
         same_layer_dm(L[4], MB_CONV, 4, 32, 32, 4, 2) && same_layer_dm(L[5], MB_MAXFILTER, 2, 32, 32, 4, 1) &&
         same_layer_dm(L[6], MB_HEAD_SOFTMAX2, 4, 32, 2, 8, 1))
         return FAMILY_FASTMEMB;
+    if (n == 9 && same_layer_dm(L[0], MB_CONV, 4, 1, 32, 1, 2) && same_layer_dm(L[1], MB_MAXFILTER, 2, 32, 32, 1, 1) &&
+        same_layer_dm(L[2], MB_CONV, 4, 32, 32, 2, 2) && same_layer_dm(L[3], MB_MAXFILTER, 2, 32, 32, 2, 1) &&
+        same_layer_dm(L[4], MB_CONV, 4, 32, 32, 4, 2) && same_layer_dm(L[5], MB_MAXFILTER, 2, 32, 32, 4, 1) &&
+        same_layer_dm(L[6], MB_CONV, 4, 32, 32, 8, 2) && same_layer_dm(L[7], MB_MAXFILTER, 2, 32, 32, 8, 1) &&
+        same_layer_dm(L[8], MB_HEAD_SOFTMAX2, 4, 32, 2, 16, 1))
+        return FAMILY_FASTMEMB_3NM;
     if (n == 6 && same_layer(L[0], MB_CONV, 5, 1, 32, 1) && same_layer(L[1], MB_MAXFILTER, 2, 32, 32, 0) &&
         same_layer(L[2], MB_CONV, 5, 32, 32, 1) && same_layer(L[3], MB_MAXFILTER, 2, 32, 32, 0) &&
         same_layer(L[4], MB_CONV, 5, 32, 32, 1) && same_layer(L[5], MB_HEAD_SIGMOID, 1, 32, 1, 0))
@@ -161,6 +167,7 @@ static int net_radius(const mb_net* net) {
     switch (net->family) {
         case FAMILY_STUDENT: return kStudentRadius;
         case FAMILY_FASTMEMB: return kFastMembRadius;
+        case FAMILY_FASTMEMB_3NM: return kFastMemb3nmRadius;
         default: return kTeacherRadius;
     }
 }
@@ -225,7 +232,7 @@ static mb_status fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int6
 
 static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t y0,
                             int64_t x0, int64_t rows, int64_t cols, void* out, mb_out_type ot, cudaStream_t st) {
-    if (net->family == FAMILY_FASTMEMB)
+    if (is_fastmemb(net->family))
         return fastmemb_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
     if (net->family == FAMILY_TEACHER)
         return teacher_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
@@ -370,14 +377,15 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
     }
     const int fam = detect_family(layers, n_layers);
     if (!fam) {
-        set_error("mb_net_create: no kernel for this layer stack (teacher 5x5/32, student 3x3/16 or FastMemb only)");
+        set_error("mb_net_create: no kernel for this layer stack (teacher 5x5/32, student 3x3/16, FastMemb or "
+                  "FastMemb_3nm only)");
         return MB_ERR_UNSUPPORTED;
     }
     if (fam == FAMILY_STUDENT && prec == MB_PREC_FP8) {
         set_error("mb_net_create: the student runs in FP32 or BF16");
         return MB_ERR_UNSUPPORTED;
     }
-    if (fam == FAMILY_FASTMEMB && prec == MB_PREC_FP8) {
+    if (is_fastmemb(fam) && prec == MB_PREC_FP8) {
         set_error("mb_net_create: FastMemb runs in FP32 or BF16");
         return MB_ERR_UNSUPPORTED;
     }
@@ -480,7 +488,7 @@ mb_status mb_load_weights(mb_net* net, const float* params, int64_t n_params) {
     net->calibrated = false;
     net->loaded = true;
     if (net->family == FAMILY_TEACHER && net->prec == MB_PREC_BF16) MB_TRY(tc_prepare(net));
-    if (net->family == FAMILY_FASTMEMB && net->prec == MB_PREC_BF16) MB_TRY(fm_tc_prepare(net));
+    if (is_fastmemb(net->family) && net->prec == MB_PREC_BF16) MB_TRY(fm_tc_prepare(net));
     return MB_OK;
 }
 
@@ -582,7 +590,7 @@ mb_status mb_infer_volume_subsampled(mb_net* net, const uint8_t* in, int64_t z, 
         set_error("mb_infer_volume_subsampled: unknown output type %d", (int)out_type);
         return MB_ERR_INVALID_ARG;
     }
-    if (net->family != FAMILY_FASTMEMB || factor != 2) {
+    if (!is_fastmemb(net->family) || factor != 2) {
         set_error("mb_infer_volume_subsampled: only FastMemb nets with factor 2 (got factor %d)", (int)factor);
         return MB_ERR_UNSUPPORTED;
     }
@@ -673,7 +681,7 @@ mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t 
         if (net->family == FAMILY_TEACHER) {
             MB_TRY(teacher_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w, b.out,
                                   b.out_pitch, b.out_slice_pitch, out_type, st));
-        } else if (net->family == FAMILY_FASTMEMB) {
+        } else if (is_fastmemb(net->family)) {
             MB_TRY(fastmemb_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w, b.out,
                                    b.out_pitch, b.out_slice_pitch, out_type, st));
         } else if (b.z > 0) {

@@ -240,25 +240,42 @@ mb_status launch_fm(FmArgs a, int nz, cudaStream_t st) {
 
 }  // namespace
 
-// Per-stage geometry of one FastMemb pass: extents of the four conv outputs (conv1 at full
-// resolution; the rest at full resolution for the dense map, on the half grid when sub-sampled),
-// the dilation of each conv, and how each conv reads its input (max-filter dilation, stride).
+// Per-stage geometry of one FastMemb pass with NC convolutions (4 for FastMemb, 5 for
+// FastMemb_3nm): extents of the conv outputs (conv1 at full resolution; the rest at full resolution
+// for the dense map, on the half grid when sub-sampled), the dilation of each conv, and how each
+// conv reads its input (max-filter dilation dm, stride st). Walking back from the map, conv k's
+// input needs 3 d_k + dm_k more rows than its output.
+constexpr int kFmMaxConvs = 5;
 struct FmGeom {
-    int64_t r[4], c[4];   // conv outputs: act1, act2, act3, map
-    int d[4], dm[4], st[4];
+    int nc;
+    int64_t r[kFmMaxConvs], c[kFmMaxConvs];
+    int d[kFmMaxConvs], dm[kFmMaxConvs], st[kFmMaxConvs];
 };
 
-static FmGeom fm_geom(int64_t rows, int64_t cols, int sub) {
+static FmGeom fm_geom(int nc, int64_t rows, int64_t cols, int sub) {
     FmGeom g{};
-    if (sub == 2) {
-        const int64_t h2 = (rows + 1) / 2, w2 = (cols + 1) / 2;
-        const int64_t r[4] = {2 * h2 + 48, h2 + 21, h2 + 14, h2}, c[4] = {2 * w2 + 48, w2 + 21, w2 + 14, w2};
-        const int d[4] = {1, 1, 2, 4}, dm[4] = {0, 1, 1, 2}, st[4] = {1, 2, 1, 1};
-        for (int i = 0; i < 4; ++i) g.r[i] = r[i], g.c[i] = c[i], g.d[i] = d[i], g.dm[i] = dm[i], g.st[i] = st[i];
-    } else {
-        const int64_t r[4] = {rows + 49, rows + 42, rows + 28, rows}, c[4] = {cols + 49, cols + 42, cols + 28, cols};
-        const int d[4] = {1, 2, 4, 8}, dm[4] = {0, 1, 2, 4}, st[4] = {1, 1, 1, 1};
-        for (int i = 0; i < 4; ++i) g.r[i] = r[i], g.c[i] = c[i], g.d[i] = d[i], g.dm[i] = dm[i], g.st[i] = st[i];
+    g.nc = nc;
+    for (int k = 0; k < nc; ++k) {
+        g.st[k] = 1;
+        if (sub == 2) {
+            g.d[k] = k == 0 ? 1 : 1 << (k - 1);
+            g.dm[k] = k == 0 ? 0 : (k == 1 ? 1 : g.d[k - 1]);
+            if (k == 1) g.st[k] = 2;
+        } else {
+            g.d[k] = 1 << k;
+            g.dm[k] = k == 0 ? 0 : g.d[k - 1];
+        }
+    }
+    g.r[nc - 1] = sub == 2 ? (rows + 1) / 2 : rows;
+    g.c[nc - 1] = sub == 2 ? (cols + 1) / 2 : cols;
+    for (int k = nc - 1; k >= 1; --k) {
+        const int64_t in_r = g.r[k] + 3 * g.d[k], in_c = g.c[k] + 3 * g.d[k];  // conv k's input domain
+        g.r[k - 1] = (in_r - 1) * g.st[k] + g.dm[k] + 1;
+        g.c[k - 1] = (in_c - 1) * g.st[k] + g.dm[k] + 1;
+    }
+    if (sub == 2) {  // conv1 covers whole 2x2 pooling windows
+        g.r[0] += g.r[0] & 1;
+        g.c[0] += g.c[0] & 1;
     }
     return g;
 }
@@ -270,30 +287,32 @@ static inline int64_t fm_in_extent(const FmGeom& g, int i, bool rows) {
     return (src - 1 - g.dm[i]) / g.st[i] + 1;
 }
 
+// Offsets of the SIMT-layout weights of conv k (Wt[ci][ky][kx][co] then b[co]; co = 64 except the
+// head's 2; ci = 1 for conv1 and 32 after).
+static const float* fm_simt_w(const mb_net* net, int k, int nc, const float** bias) {
+    size_t off = 0;
+    for (int i = 0; i < k; ++i) off += i == 0 ? 16 * 64 + 64 : 32 * 16 * 64 + 64;
+    const float* w = net->d_simt + off;
+    const int co = k == nc - 1 ? 2 : 64, ci = k == 0 ? 1 : 32;
+    *bias = w + (size_t)ci * 16 * co;
+    return w;
+}
+
 mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
                                int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
                                int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub) {
     if (z == 0 || rows == 0 || cols == 0) return MB_OK;
-    const FmGeom g = fm_geom(rows, cols, sub);
-    const size_t per = (size_t)(g.r[0] * g.c[0] + g.r[1] * g.c[1] + g.r[2] * g.c[2]) * 32 * sizeof(float);
+    const int nc = fastmemb_convs(net->family);
+    const int R = nc == 5 ? kFastMemb3nmRadius : kFastMembRadius;
+    const FmGeom g = fm_geom(nc, rows, cols, sub);
+    size_t per = 0;
+    for (int k = 0; k < nc - 1; ++k) per += (size_t)(g.r[k] * g.c[k]) * 32 * sizeof(float);
     const size_t budget = (size_t)3 << 30;
     const int64_t zc = std::min<int64_t>(std::min<int64_t>(std::max<size_t>(1, budget / per), 65535), z);
     MB_TRY(net->ws.ensure(per * (size_t)zc));
-    float* act[3];
+    float* act[kFmMaxConvs - 1];
     act[0] = static_cast<float*>(net->ws.ptr);
-    act[1] = act[0] + (size_t)zc * g.r[0] * g.c[0] * 32;
-    act[2] = act[1] + (size_t)zc * g.r[1] * g.c[1] * 32;
-    // SIMT layout: per conv Wt[ci][ky][kx][co] then b[co]; co = 64, 64, 64, 2
-    const float* w1 = net->d_simt;
-    const float* b1 = w1 + 16 * 64;
-    const float* w2 = b1 + 64;
-    const float* b2 = w2 + 32 * 16 * 64;
-    const float* w3 = b2 + 64;
-    const float* b3 = w3 + 32 * 16 * 64;
-    const float* w4 = b3 + 64;
-    const float* b4 = w4 + 32 * 16 * 2;
-    const float* ws[4] = {w1, w2, w3, w4};
-    const float* bs[4] = {b1, b2, b3, b4};
+    for (int k = 1; k < nc - 1; ++k) act[k] = act[k - 1] + (size_t)zc * g.r[k - 1] * g.c[k - 1] * 32;
     for (int64_t z0 = 0; z0 < z; z0 += zc) {
         const int nz = (int)std::min<int64_t>(zc, z - z0);
         FmArgs a{};
@@ -304,35 +323,33 @@ mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
         a.in_cols = (int)(g.c[0] + 3);
         a.src_h = (int)h;
         a.src_w = (int)w;
-        a.off_y = (int)(y0 - 26);
-        a.off_x = (int)(x0 - 26);
+        a.off_y = (int)(y0 - R);
+        a.off_x = (int)(x0 - R);
         a.d = 1;
         a.out_h = (int)g.r[0];
         a.out_w = (int)g.c[0];
         a.out = act[0];
         a.out_slice = g.r[0] * g.c[0] * 32;
         a.out_pitch = g.c[0];
-        a.wt = w1;
-        a.bias = b1;
+        a.wt = fm_simt_w(net, 0, nc, &a.bias);
         MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT>(a, nz, st)));
-        for (int i = 1; i < 4; ++i) {
+        for (int k = 1; k < nc; ++k) {
             FmArgs b{};
-            b.in = act[i - 1];
-            b.in_slice = g.r[i - 1] * g.c[i - 1] * 32;
-            b.in_pitch = g.c[i - 1];
-            b.in_rows = (int)fm_in_extent(g, i, true);
-            b.in_cols = (int)fm_in_extent(g, i, false);
-            b.d = g.d[i];
-            b.dm = g.dm[i];
-            b.in_stride = g.st[i];
-            b.out_h = (int)g.r[i];
-            b.out_w = (int)g.c[i];
-            b.wt = ws[i];
-            b.bias = bs[i];
-            if (i < 3) {
-                b.out = act[i];
-                b.out_slice = g.r[i] * g.c[i] * 32;
-                b.out_pitch = g.c[i];
+            b.in = act[k - 1];
+            b.in_slice = g.r[k - 1] * g.c[k - 1] * 32;
+            b.in_pitch = g.c[k - 1];
+            b.in_rows = (int)fm_in_extent(g, k, true);
+            b.in_cols = (int)fm_in_extent(g, k, false);
+            b.d = g.d[k];
+            b.dm = g.dm[k];
+            b.in_stride = g.st[k];
+            b.out_h = (int)g.r[k];
+            b.out_w = (int)g.c[k];
+            b.wt = fm_simt_w(net, k, nc, &b.bias);
+            if (k < nc - 1) {
+                b.out = act[k];
+                b.out_slice = g.r[k] * g.c[k] * 32;
+                b.out_pitch = g.c[k];
                 MB_TRY((launch_fm<32, 8, 64, 8, FM_IN_F32, FM_OUT_MAXOUT>(b, nz, st)));
             } else {
                 b.out_slice = out_slice;
@@ -357,19 +374,22 @@ mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
                                int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub) {
     if (z == 0 || rows == 0 || cols == 0) return MB_OK;
     MB_TRY(fm_tc_poll_error(net));
-    const FmGeom g = fm_geom(rows, cols, sub);
+    const int nc = fastmemb_convs(net->family);
+    const int R = nc == 5 ? kFastMemb3nmRadius : kFastMembRadius;
+    const FmGeom g = fm_geom(nc, rows, cols, sub);
     auto up = [](int64_t n) { return (n + 127) & ~(int64_t)127; };  // 256-byte aligned sub-buffers
-    const int64_t n[3] = {up(g.r[0] * g.c[0] * 32), up(g.r[1] * g.c[1] * 32), up(g.r[2] * g.c[2] * 32)};
-    const size_t per = (size_t)(n[0] + n[1] + n[2]) * 2;
+    int64_t n[kFmMaxConvs - 1];
+    size_t per = 0;
+    for (int k = 0; k < nc - 1; ++k) {
+        n[k] = up(g.r[k] * g.c[k] * 32);
+        per += (size_t)n[k] * 2;
+    }
     const size_t budget = (size_t)3 << 30;
     const int64_t zc = std::min<int64_t>(std::min<int64_t>(std::max<size_t>(1, budget / per), 65535), z);
     MB_TRY(net->ws.ensure(per * (size_t)zc));
-    __nv_bfloat16* act[3];
+    __nv_bfloat16* act[kFmMaxConvs - 1];
     act[0] = static_cast<__nv_bfloat16*>(net->ws.ptr);
-    act[1] = act[0] + (size_t)zc * n[0];
-    act[2] = act[1] + (size_t)zc * n[1];
-    const float* w1 = net->d_simt;
-    const float* b1 = w1 + 16 * 64;
+    for (int k = 1; k < nc - 1; ++k) act[k] = act[k - 1] + (size_t)zc * n[k - 1];
     const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
     for (int64_t z0 = 0; z0 < z; z0 += zc) {
         const int nz = (int)std::min<int64_t>(zc, z - z0);
@@ -381,23 +401,22 @@ mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
         a.in_cols = (int)(g.c[0] + 3);
         a.src_h = (int)h;
         a.src_w = (int)w;
-        a.off_y = (int)(y0 - 26);
-        a.off_x = (int)(x0 - 26);
+        a.off_y = (int)(y0 - R);
+        a.off_x = (int)(x0 - R);
         a.d = 1;
         a.out_h = (int)g.r[0];
         a.out_w = (int)g.c[0];
         a.out = act[0];
         a.out_slice = n[0];
         a.out_pitch = g.c[0];
-        a.wt = w1;
-        a.bias = b1;
+        a.wt = fm_simt_w(net, 0, nc, &a.bias);
         MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT_BF16>(a, nz, st)));
-        for (int i = 1; i < 4; ++i) {
-            const bool head = i == 3;
-            void* o = head ? static_cast<void*>(static_cast<uint8_t*>(out) + z0 * out_slice * osz) : act[i];
-            MB_TRY(fm_tc_layer(net, i - 1, act[i - 1], n[i - 1], g.c[i - 1], g.r[i - 1], g.c[i - 1],
-                               (int)fm_in_extent(g, i, true), (int)fm_in_extent(g, i, false), g.dm[i], g.st[i], o,
-                               head ? out_slice : n[i], head ? out_pitch : g.c[i], (int)g.r[i], (int)g.c[i], g.d[i],
+        for (int k = 1; k < nc; ++k) {
+            const bool head = k == nc - 1;
+            void* o = head ? static_cast<void*>(static_cast<uint8_t*>(out) + z0 * out_slice * osz) : act[k];
+            MB_TRY(fm_tc_layer(net, k - 1, act[k - 1], n[k - 1], g.c[k - 1], g.r[k - 1], g.c[k - 1],
+                               (int)fm_in_extent(g, k, true), (int)fm_in_extent(g, k, false), g.dm[k], g.st[k], o,
+                               head ? out_slice : n[k], head ? out_pitch : g.c[k], (int)g.r[k], (int)g.c[k], g.d[k],
                                nz, head && ot == MB_OUT_U8, st));
         }
     }

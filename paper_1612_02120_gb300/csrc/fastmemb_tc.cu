@@ -41,12 +41,12 @@ namespace mb {
 namespace {
 
 constexpr int kFThreads = 512;
-constexpr int kFP = 154;                 // pixels per staged row (>= 128 + 3*8); 154 mod 8 = 2 spreads
+constexpr int kFP = 178;                 // pixels per staged row (>= 128 + 3*16); 178 mod 8 = 2 spreads
                                          // the 4 chunk planes of one pixel pair over distinct banks
 constexpr int kFSlot = 4 * kFP * 16;     // bytes per staged row (4 chunks of 8 BF16 channels)
 constexpr int kFRing = 8;                // staged rows in flight
 constexpr int kFAcc = 4;                 // TMEM accumulators
-constexpr int kFTasks = 5;               // producer tasks per thread and row: ceil(4 * 152 / 128)
+constexpr int kFTasks = 6;               // producer tasks per thread and row: ceil(4 * 176 / 128)
 constexpr int kFPrefetch = 4;            // staged rows between a row's L2 prefetch and its loads
 constexpr uint64_t kFWaitNs = 4000000000ull;
 
@@ -445,7 +445,7 @@ mb_status launch_fm_tc(const FmTcParams& p, cudaStream_t st) {
 }  // namespace
 
 struct FmTcState {
-    uint8_t* d_wpack[3] = {nullptr, nullptr, nullptr};  // layers 2, 3 and the head
+    uint8_t* d_wpack[4] = {nullptr, nullptr, nullptr, nullptr};  // the 32->64 convs, then the head
     int* h_err = nullptr;
     int* d_err = nullptr;
 };
@@ -460,20 +460,19 @@ mb_status fm_tc_prepare(mb_net* net) {
         }
         net->fm_state = S;
     }
-    // API layout: W1 [64][1][4][4], b1 [64], W2 [64][32][4][4], b2, W3, b3, W4 [2][32][4][4], b4
-    const float* P = net->host_params.data();
-    const float* W2 = P + 64 * 16 + 64;
-    const float* B2 = W2 + 64 * 32 * 16;
-    const float* W3 = B2 + 64;
-    const float* B3 = W3 + 64 * 32 * 16;
-    const float* W4 = B3 + 64;
-    const float* B4 = W4 + 2 * 32 * 16;
+    // API layout: W1 [64][1][4][4], b1 [64], then per 32->64 conv W [64][32][4][4], b [64], then the
+    // head W [2][32][4][4], b [2]
+    const int nc = fastmemb_convs(net->family);
+    const float* P = net->host_params.data() + 64 * 16 + 64;
     std::vector<uint8_t> pk;
-    for (int l = 0; l < 3; ++l) {
-        if (l < 2)
-            fm_pack<false>(l == 0 ? W2 : W3, l == 0 ? B2 : B3, 64, pk);
+    for (int l = 0; l < nc - 1; ++l) {
+        const bool head = l == nc - 2;
+        const int co = head ? 2 : 64;
+        if (!head)
+            fm_pack<false>(P, P + co * 32 * 16, co, pk);
         else
-            fm_pack<true>(W4, B4, 2, pk);
+            fm_pack<true>(P, P + co * 32 * 16, co, pk);
+        P += co * 32 * 16 + co;
         if (!S->d_wpack[l]) MB_TRY(dev_alloc((void**)&S->d_wpack[l], pk.size()));
         MB_CUDA(cudaMemcpy(S->d_wpack[l], pk.data(), pk.size(), cudaMemcpyHostToDevice));
     }
@@ -552,7 +551,7 @@ mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, 
     const char* stall = getenv("MB_FAULT_STALL");
     p.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
     p.wait_ns = p.fault_stall ? 200000000ull : kFWaitNs;
-    return layer == 2 ? launch_fm_tc<true>(p, st) : launch_fm_tc<false>(p, st);
+    return layer == fastmemb_convs(net->family) - 2 ? launch_fm_tc<true>(p, st) : launch_fm_tc<false>(p, st);
 }
 
 }  // namespace mb

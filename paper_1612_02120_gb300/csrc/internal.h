@@ -12,7 +12,7 @@
 
 namespace mb {
 
-enum Family { FAMILY_TEACHER = 1, FAMILY_STUDENT = 2, FAMILY_FASTMEMB = 3 };
+enum Family { FAMILY_TEACHER = 1, FAMILY_STUDENT = 2, FAMILY_FASTMEMB = 3, FAMILY_FASTMEMB_3NM = 4 };
 
 // Teacher geometry: conv5x5 x3 with two 2x2 max-filters -> receptive radius 7.
 constexpr int kTeacherRadius = 7;
@@ -23,6 +23,11 @@ constexpr int kStudentC = 16;
 // FastMemb dense form: conv4x4 (dilation 1, 2, 4) with max-out 2, max-filters (1, 2, 4), conv4x4
 // dilation 8 -> radius 26 (53x53 field of view).
 constexpr int kFastMembRadius = 26;
+// FastMemb_3nm: one more stage (dilation 8 conv and max-filter, head at 16) -> radius 54 (109x109).
+constexpr int kFastMemb3nmRadius = 54;
+inline bool is_fastmemb(int family) { return family == FAMILY_FASTMEMB || family == FAMILY_FASTMEMB_3NM; }
+// convolutions of a FastMemb family (conv1, the 32->64 middle convs, the head)
+inline int fastmemb_convs(int family) { return family == FAMILY_FASTMEMB_3NM ? 5 : 4; }
 
 void set_error(const char* fmt, ...);
 void clear_error();
@@ -104,14 +109,15 @@ mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
                                int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
                                int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
                                mb_out_type ot, cudaStream_t st, int sub);
-// FastMemb tensor-core layers (fastmemb_tc.cu): pack split BF16 B operands of the two 32->64 convs
-// and the head, launch one (0: conv dilation 2, 1: conv dilation 4, 2: head dilation 8 with the
-// softmax, FP32 or uint8 out), poll the device-side wait error word.
+// FastMemb tensor-core layers (fastmemb_tc.cu): pack split BF16 B operands of the 32->64 convs and
+// the head, launch one (the head ends with the softmax, FP32 or uint8 out), poll the device-side
+// wait error word.
 mb_status fm_tc_prepare(mb_net* net);
 void fm_tc_release(mb_net* net);
 mb_status fm_tc_poll_error(mb_net* net);
 // in: [slice][src_rows][src_cols(pitch)][32] BF16; the conv reads input (r, c) = 2x2 max (dilation
-// dm) at source (stride r, stride c), for r < in_rows, c < in_cols.
+// dm) at source (stride r, stride c), for r < in_rows, c < in_cols. layer: 0-based index of the
+// conv after conv1; the last one is the head.
 mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int64_t src_rows,
                       int64_t src_cols, int in_rows, int in_cols, int dm, int stride, void* out, int64_t out_slice,
                       int64_t out_pitch, int out_h, int out_w, int d, int nz, int out_u8, cudaStream_t st);

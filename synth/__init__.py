@@ -174,17 +174,23 @@ def param_count(layers) -> int:
     return n
 
 
-def init_params(layers, seed: int, bias_std: float = 0.01) -> np.ndarray:
+def init_params(layers, seed: int, bias_std: float = 0.01, center_head: bool = False) -> np.ndarray:
     """He-normal FP32 parameters for `layers`, packed per parameterised layer as
     W[cout*G][cin][k][k] then b[cout*G] (G max-out groups); parameterised layer number l draws
-    from seed + l. bias_std 0 gives zero biases."""
+    from seed + l. bias_std 0 gives zero biases. center_head: the last layer's filters are
+    shifted to zero mean over their input channels at every tap (a distribution choice that keeps
+    a deep max-out stack's map away from saturation)."""
     parts = []
     l = 0
+    n_par = sum(1 for layer in layers if layer[0] in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2))
     for layer in layers:
         kind, k, cin, cout = layer[:4]
         if kind in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2):
             co = cout * _groups(layer)
             w, b = he_normal(seed + l, cin * k * k, co * cin * k * k, co, bias_std)
+            if center_head and l == n_par - 1:
+                w4 = w.reshape(co, cin, k * k)
+                w = (w4 - w4.mean(axis=1, keepdims=True)).reshape(-1)
             parts += [w, b]
             l += 1
     return np.concatenate(parts).astype(np.float32)

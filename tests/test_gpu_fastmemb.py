@@ -276,3 +276,53 @@ def test_subsampled_error_codes(net):
     assert lib.mb_infer_volume_subsampled(t.handle, x.data_ptr(), 1, 64, 64, 2, out.data_ptr(), 0,
                                           None) == m.MB_ERR_UNSUPPORTED
     t.close()
+
+
+# ---- FastMemb_3nm (one more stage, field of view 109) -------------------------------------------
+
+F3 = synth.FASTMEMB_3NM
+
+
+def fm3_params():
+    return synth.init_params(F3, synth.FASTMEMB_3NM_WEIGHT_SEED, center_head=True)
+
+
+@pytest.fixture(scope="module")
+def nets3():
+    from paper_1612_02120_gb300 import build, membrane as m
+    build.build()
+    a = make_net(F3, m.MB_PREC_FP32, fm3_params())
+    b = make_net(F3, m.MB_PREC_BF16, fm3_params())
+    yield a, b
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 55, 55), (1, 160, 300), (2, 90, 130)])
+def test_3nm_slices_match_oracle(nets3, shape):
+    z, h, w = shape
+    v = synth.em_volume(9960 + h * w, z, h, w)
+    p32, p16 = infer(nets3[0], v), infer(nets3[1], v)
+    tol16 = dict(TOL["bf16"])
+    if h * w < 4096:
+        del tol16["agreement"]
+    for zi in range(z):
+        ref = oracle.forward_region(F3, fm3_params(), v[zi])
+        assert within(oracle.metrics(p32[zi], ref), TOL["fp32"]), (shape, zi)
+        assert within(oracle.metrics(p16[zi], ref), tol16), (shape, zi, oracle.metrics(p16[zi], ref))
+
+
+def test_3nm_subsampled_equals_dense_at_even_positions_bitwise(nets3):
+    v = synth.em_volume(9970, 1, 160, 301)
+    for n in nets3:
+        np.testing.assert_array_equal(infer_sub(n, v), infer(n, v)[:, ::2, ::2])
+
+
+def test_3nm_parameters_and_minimum_slice(nets3):
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    assert nets3[0].n_params == 100610 == oracle.param_count(F3)
+    lib = m.load()
+    x = torch.zeros((1, 54, 80), dtype=torch.uint8, device="cuda")
+    out = torch.empty((1, 54, 80), dtype=torch.float32, device="cuda")
+    assert lib.mb_infer_volume(nets3[0].handle, x.data_ptr(), 1, 54, 80, out.data_ptr(), 0, None) == m.MB_ERR_SHAPE

@@ -49,3 +49,13 @@ def test_block_shapes_ranges():
     for d, h, w in shapes:
         assert 1 <= d <= 16 and 256 <= h <= 1536 and 256 <= w <= 1536
     assert synth.block_shapes(9, 64) == shapes
+
+
+def test_centred_head_has_zero_channel_mean_and_leaves_other_layers():
+    a = synth.init_params(synth.FASTMEMB_3NM, 5)
+    b = synth.init_params(synth.FASTMEMB_3NM, 5, center_head=True)
+    n_head = 2 * 32 * 16 + 2
+    np.testing.assert_array_equal(a[:-n_head], b[:-n_head])
+    np.testing.assert_array_equal(a[-2:], b[-2:])
+    w = b[-n_head:-2].reshape(2, 32, 16).astype(np.float64)
+    assert np.abs(w.mean(axis=1)).max() < 1e-6
