@@ -246,33 +246,34 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
                                    mb_out_type ot) {
     const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
     const size_t in_slice = (size_t)h * w, out_slice = (size_t)h * w * osz;
-    int64_t slab = std::max<int64_t>(1, (int64_t)((256ull << 20) / (in_slice + out_slice)));
+    // Slabs of about 8 Mvox: large enough that one launch fills every SM, small enough that the
+    // copies of neighbouring slabs overlap the compute (a 1024x1024x32 volume becomes 4 slabs);
+    // at most 256 MB of device buffers per slab.
+    int64_t slab = std::max<int64_t>(1, (int64_t)((8ll << 20) + h * w - 1) / (h * w));
+    slab = std::min<int64_t>(slab, std::max<int64_t>(1, (int64_t)((256ull << 20) / (in_slice + out_slice))));
     slab = std::min<int64_t>(slab, z);
     if (z == 0) return MB_OK;
-    const int NB = 2;
-    void* dbuf[NB] = {nullptr, nullptr};
-    cudaStream_t s[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t ev_in[NB] = {}, ev_comp[NB] = {}, ev_out[NB] = {};
+    constexpr int NB = 2;
+    // device slabs, streams and events live with the net and are reused by later calls
+    const size_t slab_bytes = (in_slice + out_slice) * (size_t)slab;
+    MB_TRY(net->slab_ws.ensure(NB * slab_bytes));
+    cudaStream_t* s = net->slab_streams;
+    for (int i = 0; i < 3; ++i)
+        if (!s[i]) MB_CUDA(cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking));
+    cudaEvent_t* ev_in = net->slab_events;
+    cudaEvent_t* ev_comp = ev_in + NB;
+    cudaEvent_t* ev_out = ev_comp + NB;
+    for (int i = 0; i < 3 * NB; ++i)
+        if (!net->slab_events[i]) MB_CUDA(cudaEventCreateWithFlags(&net->slab_events[i], cudaEventDisableTiming));
     mb_status rc = MB_OK;
     auto fail = [&](cudaError_t e, const char* what) {
         rc = cuda_fail(e, what, __FILE__, __LINE__);
     };
-    for (int b = 0; b < NB && rc == MB_OK; ++b) rc = dev_alloc(&dbuf[b], (in_slice + out_slice) * slab);
-    for (int i = 0; i < 3 && rc == MB_OK; ++i) {
-        cudaError_t e = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
-        if (e != cudaSuccess) fail(e, "cudaStreamCreate");
-    }
-    for (int b = 0; b < NB && rc == MB_OK; ++b) {
-        cudaError_t e = cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_comp[b], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out[b], cudaEventDisableTiming);
-        if (e != cudaSuccess) fail(e, "cudaEventCreate");
-    }
     const int64_t nslab = (z + slab - 1) / slab;
     for (int64_t k = 0; k < nslab && rc == MB_OK; ++k) {
         const int b = (int)(k % NB);
         const int64_t z0 = k * slab, nz = std::min<int64_t>(slab, z - z0);
-        uint8_t* din = static_cast<uint8_t*>(dbuf[b]);
+        uint8_t* din = static_cast<uint8_t*>(net->slab_ws.ptr) + b * slab_bytes;
         uint8_t* dout = din + in_slice * slab;
         cudaError_t e = cudaSuccess;
         if (k >= NB) e = cudaStreamWaitEvent(s[0], ev_comp[b], 0);  // input buffer free
@@ -294,19 +295,10 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
         if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], s[2]);
         if (e != cudaSuccess) fail(e, "slab D2H");
     }
-    for (int i = 0; i < 3; ++i)
-        if (s[i]) {
-            cudaError_t e = cudaStreamSynchronize(s[i]);
-            if (e != cudaSuccess && rc == MB_OK) fail(e, "cudaStreamSynchronize");
-        }
-    for (int b = 0; b < NB; ++b) {
-        if (ev_in[b]) cudaEventDestroy(ev_in[b]);
-        if (ev_comp[b]) cudaEventDestroy(ev_comp[b]);
-        if (ev_out[b]) cudaEventDestroy(ev_out[b]);
-        dev_free(dbuf[b]);
+    for (int i = 0; i < 3; ++i) {
+        cudaError_t e = cudaStreamSynchronize(s[i]);
+        if (e != cudaSuccess && rc == MB_OK) fail(e, "cudaStreamSynchronize");
     }
-    for (int i = 0; i < 3; ++i)
-        if (s[i]) cudaStreamDestroy(s[i]);
     return rc;
 }
 
@@ -442,6 +434,11 @@ mb_status mb_net_destroy(mb_net* net) {
         dev_free(net->d_queue);
         net->ws.release();
         net->ws2.release();
+        net->slab_ws.release();
+        for (cudaStream_t& st : net->slab_streams)
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t& ev : net->slab_events)
+            if (ev) cudaEventDestroy(ev);
     }
     delete net;
     return MB_OK;
