@@ -239,6 +239,35 @@ __device__ __forceinline__ void store_half(uint8_t* slot, int c, int h, const fl
     }
 }
 
+// Store channels 8h .. 8h+7 of one pixel: BF16 chunk h (16 B), or the half h & 1 of E4M3 chunk h >> 1.
+template <bool FP8>
+__device__ __forceinline__ void store_eighth(uint8_t* slot, int c, int h, const float (&m)[8], const float* q) {
+    if (!FP8) {
+        uint4 u;
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(m[0], m[1]);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(m[2], m[3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(m[4], m[5]);
+        __nv_bfloat162 h3 = __floats2bfloat162_rn(m[6], m[7]);
+        u.x = *reinterpret_cast<uint32_t*>(&h0);
+        u.y = *reinterpret_cast<uint32_t*>(&h1);
+        u.z = *reinterpret_cast<uint32_t*>(&h2);
+        u.w = *reinterpret_cast<uint32_t*>(&h3);
+        *reinterpret_cast<uint4*>(slot + (h * kPitch + c) * 16) = u;
+    } else {
+        uint32_t w[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int ch = 4 * j;
+            __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(m[ch] * q[ch], m[ch + 1] * q[ch + 1]),
+                                                               __NV_SATFINITE, __NV_E4M3);
+            __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(m[ch + 2] * q[ch + 2], m[ch + 3] * q[ch + 3]), __NV_SATFINITE, __NV_E4M3);
+            w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        *reinterpret_cast<uint2*>(slot + ((h >> 1) * kPitch + c) * 16 + (h & 1) * 8) = make_uint2(w[0], w[1]);
+    }
+}
+
 // Issue the MMAs of groups [g_lo, g_hi) of one input row r for one layer: output rows j = r-4+i of
 // the layer for the valid blocks i (0 <= j < n_out). Every MMA accumulates; the epilogue zeroes an accumulator after
 // draining it, so a row's first contribution adds to zero. Blocks go to ring slots
@@ -563,15 +592,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     } else {
         ptx::setmaxnreg_inc<232>();
         // ================= layer 1 + max-filter producer ======================================
-        // Thread = (channel half h, column pair cp): columns c0 = 2 cp and c0 + 1, channels
-        // 16h .. 16h+15. Warps 12,13 hold half 0 (columns 0-63, 64-127), warps 14,15 half 1, so
-        // every weight load is a warp-wide broadcast feeding two columns.
-        const int pw = warp - 12;
-        const int h = pw >> 1;
-        const int c0 = 2 * ((pw & 1) * 32 + lane);
-        float* stage = reinterpret_cast<float*>(smem + C::oSt1);
+        // Thread = (channel group h = warp - 12, column quad): columns c0 = 4 lane .. c0 + 3,
+        // channels 8h .. 8h+7. Every weight load is a warp-wide broadcast feeding four columns, and
+        // a warp holds all 128 columns, so the max-filter's right neighbour is in the next lane.
+        const int h = warp - 12;
+        const int c0 = 4 * lane;
         uint32_t in_seq = 0, m1_seq = 0;
-        float prev[2][16], cur[2][16];
+        float prev[4][8], cur[4][8];
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const ItemInfo it = decode_item(p, k);
             const int NR = it.rows;
@@ -587,87 +614,89 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                     wait_phase(&B.in_full[qi % kInRing], (qi / kInRing) & 1, abort_flag, p.err, p.wait_ns);
                 }
                 // layer 1 at input-frame row t+1: FP32 packed two-channel FMAs, weights broadcast
-                float2 a0[8], a1[8];
+                float2 acc[4][4];
+                {
+                    const float4 b0 = *reinterpret_cast<const float4*>(cst + kCB1 + 8 * h);
+                    const float4 b1 = *reinterpret_cast<const float4*>(cst + kCB1 + 8 * h + 4);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 b = *reinterpret_cast<const float4*>(cst + kCB1 + 16 * h + 4 * j);
-                    a0[2 * j] = make_float2(b.x, b.y);
-                    a0[2 * j + 1] = make_float2(b.z, b.w);
-                    a1[2 * j] = a0[2 * j];
-                    a1[2 * j + 1] = a0[2 * j + 1];
+                    for (int c = 0; c < 4; ++c) {
+                        acc[c][0] = make_float2(b0.x, b0.y);
+                        acc[c][1] = make_float2(b0.z, b0.w);
+                        acc[c][2] = make_float2(b1.x, b1.y);
+                        acc[c][3] = make_float2(b1.z, b1.w);
+                    }
                 }
 #pragma unroll 1
                 for (int ky = 0; ky < 5; ++ky) {
-                    // all loads of this row tap first (20 broadcast weight vectors, 6 inputs), then
+                    // all loads of this row tap first (10 broadcast weight vectors, 8 inputs), then
                     // 80 packed FMAs
                     const float* ir = in_ring + ((in_seq + t + 1 + ky) % kInRing) * kPitch + c0;
-                    const float2 x01 = *reinterpret_cast<const float2*>(ir);
-                    const float2 x23 = *reinterpret_cast<const float2*>(ir + 2);
-                    const float2 x45 = *reinterpret_cast<const float2*>(ir + 4);
-                    const float x[6] = {x01.x, x01.y, x23.x, x23.y, x45.x, x45.y};
-                    const float4* wrow = reinterpret_cast<const float4*>(cst + kCW1 + ky * 5 * 32 + 16 * h);
-                    float4 w[5][4];
-#pragma unroll
-                    for (int kx = 0; kx < 5; ++kx)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) w[kx][j] = wrow[kx * 8 + j];
+                    const float4 xl = *reinterpret_cast<const float4*>(ir);
+                    const float4 xh = *reinterpret_cast<const float4*>(ir + 4);
+                    const float x[8] = {xl.x, xl.y, xl.z, xl.w, xh.x, xh.y, xh.z, xh.w};
+                    const float4* wrow = reinterpret_cast<const float4*>(cst + kCW1 + ky * 5 * 32 + 8 * h);
+                    float4 w[5][2];
 #pragma unroll
                     for (int kx = 0; kx < 5; ++kx) {
-                        const float2 xa = make_float2(x[kx], x[kx]);
-                        const float2 xb = make_float2(x[kx + 1], x[kx + 1]);
+                        w[kx][0] = wrow[kx * 8];
+                        w[kx][1] = wrow[kx * 8 + 1];
+                    }
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const float2 wl = make_float2(w[kx][j].x, w[kx][j].y), wh = make_float2(w[kx][j].z, w[kx][j].w);
-                            a0[2 * j] = __ffma2_rn(wl, xa, a0[2 * j]);
-                            a0[2 * j + 1] = __ffma2_rn(wh, xa, a0[2 * j + 1]);
-                            a1[2 * j] = __ffma2_rn(wl, xb, a1[2 * j]);
-                            a1[2 * j + 1] = __ffma2_rn(wh, xb, a1[2 * j + 1]);
+                    for (int kx = 0; kx < 5; ++kx) {
+                        const float2 w01 = make_float2(w[kx][0].x, w[kx][0].y), w23 = make_float2(w[kx][0].z, w[kx][0].w);
+                        const float2 w45 = make_float2(w[kx][1].x, w[kx][1].y), w67 = make_float2(w[kx][1].z, w[kx][1].w);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float2 xv = make_float2(x[c + kx], x[c + kx]);
+                            acc[c][0] = __ffma2_rn(w01, xv, acc[c][0]);
+                            acc[c][1] = __ffma2_rn(w23, xv, acc[c][1]);
+                            acc[c][2] = __ffma2_rn(w45, xv, acc[c][2]);
+                            acc[c][3] = __ffma2_rn(w67, xv, acc[c][3]);
                         }
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    cur[0][2 * j] = fmaxf(a0[j].x, 0.f);
-                    cur[0][2 * j + 1] = fmaxf(a0[j].y, 0.f);
-                    cur[1][2 * j] = fmaxf(a1[j].x, 0.f);
-                    cur[1][2 * j + 1] = fmaxf(a1[j].y, 0.f);
-                }
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        cur[c][2 * j] = fmaxf(acc[c][j].x, 0.f);
+                        cur[c][2 * j + 1] = fmaxf(acc[c][j].y, 0.f);
+                    }
                 ptx::mbar_arrive(&B.in_empty[(in_seq + t + 1) % kInRing]);
                 if (t >= 0) {
                     // vertical max in place (prev is reloaded from cur below)
 #pragma unroll
-                    for (int ch = 0; ch < 16; ++ch) {
-                        prev[0][ch] = fmaxf(prev[0][ch], cur[0][ch]);
-                        prev[1][ch] = fmaxf(prev[1][ch], cur[1][ch]);
-                    }
-                    // horizontal: column c0 pairs with c0+1 (same thread); column c0+1 with c0+2 =
-                    // the next lane's first column, or for lane 31 the next warp's lane 0
-                    float* st = stage + (t & 1) * 64;
-                    if ((pw & 1) == 1 && lane == 0)
+                    for (int c = 0; c < 4; ++c)
 #pragma unroll
-                        for (int ch = 0; ch < 16; ++ch) st[h * 16 + ch] = prev[0][ch];
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    float o0[16], o1[16];
-#pragma unroll
-                    for (int ch = 0; ch < 16; ++ch) {
-                        float nb = __shfl_down_sync(0xffffffffu, prev[0][ch], 1);
-                        if (lane == 31) nb = (pw & 1) == 0 ? st[h * 16 + ch] : prev[1][ch];
-                        o0[ch] = fmaxf(prev[0][ch], prev[1][ch]);
-                        o1[ch] = fmaxf(prev[1][ch], nb);
-                    }
+                        for (int ch = 0; ch < 8; ++ch) prev[c][ch] = fmaxf(prev[c][ch], cur[c][ch]);
+                    // horizontal: column c0 + 3 pairs with the next lane's column c0 + 4; lane 31's
+                    // column 127 only feeds discarded output columns and pairs with itself
                     const uint32_t q = m1_seq + t, s = q % kRing;
                     wait_phase(&B.m1_empty[s], ((q / kRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
                     uint8_t* slot = smem + C::oR1 + s * C::kSlotBytes;
-                    store_half<FP8>(slot, c0, h, o0, cst + kCQ1 + 16 * h);
-                    store_half<FP8>(slot, c0 + 1, h, o1, cst + kCQ1 + 16 * h);
+                    float o[8];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                        for (int ch = 0; ch < 8; ++ch) {
+                            float nb;
+                            if (c < 3) {
+                                nb = prev[c + 1][ch];
+                            } else {
+                                nb = __shfl_down_sync(0xffffffffu, prev[0][ch], 1);
+                                if (lane == 31) nb = prev[3][ch];
+                            }
+                            o[ch] = fmaxf(prev[c][ch], nb);
+                        }
+                        store_eighth<FP8>(slot, c0 + c, h, o, cst + kCQ1 + 8 * h);
+                    }
                     ptx::fence_proxy_async_smem();
                     ptx::mbar_arrive(&B.m1_full[s]);
                 }
 #pragma unroll
-                for (int ch = 0; ch < 16; ++ch) {
-                    prev[0][ch] = cur[0][ch];
-                    prev[1][ch] = cur[1][ch];
-                }
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int ch = 0; ch < 8; ++ch) prev[c][ch] = cur[c][ch];
             }
             for (int u = M1 + 1; u < NR + 14; ++u) ptx::mbar_arrive(&B.in_empty[(in_seq + u) % kInRing]);
             in_seq += NR + 14;
