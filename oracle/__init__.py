@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CONV, MAXF, HEAD, SOFTMAX = 0, 1, 2, 3
+CONV, MAXF, HEAD, SOFTMAX, SOFTMAXN = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -54,6 +54,8 @@ def _load():
                 "oracle_param_count": ([p, ci], i64),
                 "oracle_pad_region": ([p, i64, i64, i64, i64, i64, i64, i64, i64, p], ci),
                 "oracle_run_layers": ([p, ci, p, p, i64, i64, p], ci),
+                "oracle_run_layers_mc": ([p, ci, p, p, i64, i64, i64, p], ci),
+                "oracle_smooth_threshold": ([p, i64, i64, d, p], ci),
                 "oracle_forward_region": ([p, ci, p, p, i64, i64, i64, i64, i64, i64, i64, p], ci),
                 "oracle_patch_pixel": ([p, ci, p, p, i64, i64, i64, i64, i64, p], ci),
                 "oracle_maxfilter_amax": ([p, ci, p, p, i64, i64, i64, i64, i64, i64, i64, p, i64], ci),
@@ -181,6 +183,54 @@ def run_layers(layers, params, xp) -> np.ndarray:
     _chk(_load().oracle_run_layers(d.ctypes.data, len(d), prm.ctypes.data, xp.ctypes.data, ph, pw,
                                    p.ctypes.data), "run_layers")
     return p
+
+
+def run_layers_mc(layers, params, xp) -> np.ndarray:
+    """Layers on a multi-channel padded input xp [c][ph][pw]; the output is [classes][h][w] for an
+    N-class softmax head, else [h][w]."""
+    d, prm, xp = _desc(layers), _f64(params), _f64(xp)
+    c, ph, pw = xp.shape
+    s = sum((int(row[1]) - 1) * int(row[5]) for row in d)
+    last = d[-1]
+    nout = int(last[3]) if int(last[0]) == SOFTMAXN else 1
+    p = np.empty((nout, ph - s, pw - s), dtype=np.float64)
+    _chk(_load().oracle_run_layers_mc(d.ctypes.data, len(d), prm.ctypes.data, xp.ctypes.data, c, ph, pw,
+                                      p.ctypes.data), "run_layers_mc")
+    return p if nout > 1 else p[0]
+
+
+def smooth_threshold(p, thr=0.5) -> np.ndarray:
+    """J of the MaskExtend transfer: 3x3 mean (reflect-101) then >= thr, as uint8 0/1."""
+    p = _f64(p)
+    h, w = p.shape
+    m = np.empty((h, w), dtype=np.uint8)
+    _chk(_load().oracle_smooth_threshold(p.ctypes.data, h, w, float(thr), m.ctypes.data), "smooth_threshold")
+    return m
+
+
+def maskextend_input(em_u8, memb, masks, z, R):
+    """The 12-map input stack of MaskExtend at section z (Sec. 3.2), mirror-padded (reflect-101)
+    by R: EM z-1..z+1 (u/255), the object masks z-4..z-1 (0/1), membrane maps z-2..z+2.
+    em_u8, memb: [Z][H][W]; masks: dict section -> [H][W] 0/1."""
+    maps = [em_u8[z + k].astype(np.float64) / 255.0 for k in (-1, 0, 1)]
+    maps += [np.asarray(masks[z + k], dtype=np.float64) for k in (-4, -3, -2, -1)]
+    maps += [np.asarray(memb[z + k], dtype=np.float64) for k in (-2, -1, 0, 1, 2)]
+    return np.stack([np.pad(m, R, mode="reflect") for m in maps])
+
+
+def mask_extend(layers, params, em_u8, memb, seed_masks, z0, n_steps, thr=0.5):
+    """The MaskExtend recursion in +z (Sec. 3.2): Mask_z = J(CNN(masks z-4..z-1, EM z-1..z+1,
+    membrane z-2..z+2)) for z = z0 .. z0+n_steps-1; seed_masks are the masks of z0-4 .. z0-1.
+    Returns (masks [n][H][W] uint8, class probabilities [n][3][H][W])."""
+    R = net_radius(layers)
+    masks = {z0 - 4 + i: np.asarray(seed_masks[i]) for i in range(4)}
+    out_m, out_p = [], []
+    for z in range(z0, z0 + n_steps):
+        p = run_layers_mc(layers, params, maskextend_input(em_u8, memb, masks, z, R))
+        masks[z] = smooth_threshold(p[0], thr)
+        out_m.append(masks[z])
+        out_p.append(p)
+    return np.stack(out_m), np.stack(out_p)
 
 
 def forward_region(layers, params, slice_u8, y0=0, x0=0, h=None, w=None) -> np.ndarray:

@@ -25,6 +25,10 @@
  *    correlation y[i][j] = b + sum W[ky][kx] x[i + d ky][j + d kx]); max-out keeps the maximum
  *    over groups of feature maps (output channel c = max_g of conv channel c*G + g); the 2-class
  *    softmax head outputs p = exp(z1) / (exp(z0) + exp(z1)).
+ * MaskExtend (Sec. 3.2): the same max-out family with a 12-map input stack, five 4x4 convs with
+ *    max-out (32, 40, 48, 56, 64 features, dilations 1..16 in dense form) and a 1x1 head to 3
+ *    classes with a softmax over all of them (OR_SOFTMAXN: every class probability is output);
+ *    J (smoothing and thresholding) is a 3x3 mean with reflect-101 borders followed by >= thr.
  *
  * Conventions: activations are [c][y][x] row-major; parameters per parameterised layer are
  * W[cout*G][cin][k][k] followed by b[cout*G] (G = max-out groups, 1 without max-out); the input
@@ -45,6 +49,7 @@
 #define OR_MAXF 1
 #define OR_HEAD 2
 #define OR_SOFTMAX 3
+#define OR_SOFTMAXN 4
 #define OR_DW 7
 
 /* reflect-101 index map for n >= 2 (one reflection suffices when |overhang| < n) */
@@ -157,7 +162,8 @@ int64_t oracle_param_count(const int32_t* desc, int n_layers) {
     for (int l = 0; l < n_layers; ++l) {
         const int32_t* d = desc + OR_DW * l;
         const int64_t co = (int64_t)d[3] * groups_of(d);
-        if (d[0] == OR_CONV || d[0] == OR_HEAD || d[0] == OR_SOFTMAX) n += co * d[2] * d[1] * d[1] + co;
+        if (d[0] == OR_CONV || d[0] == OR_HEAD || d[0] == OR_SOFTMAX || d[0] == OR_SOFTMAXN)
+            n += co * d[2] * d[1] * d[1] + co;
     }
     return n;
 }
@@ -182,23 +188,24 @@ int oracle_pad_region(const uint8_t* in, int64_t H, int64_t W, int64_t pitch, in
  * Run the layer stack on an already padded single-channel input xp (ph x pw); writes the
  * (ph - shrink) x (pw - shrink) probability map to p. Returns OR_OK or an error.
  */
-int oracle_run_layers(const int32_t* desc, int n_layers, const double* params, const double* xp,
-                      int64_t ph, int64_t pw, double* p) {
-    if (!desc || !params || !xp || !p || n_layers < 1) return OR_ERR_ARG;
-    int64_t c = 1, h = ph, w = pw;
-    double* cur = (double*)malloc(sizeof(double) * (size_t)(h * w));
+int oracle_run_layers_mc(const int32_t* desc, int n_layers, const double* params, const double* xp, int64_t cin0,
+                         int64_t ph, int64_t pw, double* p) {
+    if (!desc || !params || !xp || !p || n_layers < 1 || cin0 < 1) return OR_ERR_ARG;
+    int64_t c = cin0, h = ph, w = pw;
+    double* cur = (double*)malloc(sizeof(double) * (size_t)(c * h * w));
     if (!cur) return OR_ERR_OOM;
-    memcpy(cur, xp, sizeof(double) * (size_t)(h * w));
+    memcpy(cur, xp, sizeof(double) * (size_t)(c * h * w));
     const double* prm = params;
     int rc = OR_OK;
     for (int l = 0; l < n_layers && rc == OR_OK; ++l) {
         const int32_t* d = desc + OR_DW * l;
         const int64_t k = d[1], cin = d[2], cout = d[3], dl = dil_of(d), G = groups_of(d);
         const int last = l == n_layers - 1;
-        if (d[0] == OR_CONV || d[0] == OR_SOFTMAX) {
+        if (d[0] == OR_CONV || d[0] == OR_SOFTMAX || d[0] == OR_SOFTMAXN) {
             const int64_t span = (k - 1) * dl, cg = cout * G;
             if (cin != c || h <= span || w <= span) { rc = OR_ERR_ARG; break; }
             if (d[0] == OR_SOFTMAX && (cout != 2 || G != 1 || !last)) { rc = OR_ERR_ARG; break; }
+            if (d[0] == OR_SOFTMAXN && (cout < 2 || G != 1 || !last)) { rc = OR_ERR_ARG; break; }
             int64_t oh = h - span, ow = w - span;
             double* full = (double*)malloc(sizeof(double) * (size_t)(cg * oh * ow));
             if (!full) { rc = OR_ERR_OOM; break; }
@@ -210,6 +217,21 @@ int oracle_run_layers(const int32_t* desc, int n_layers, const double* params, c
                 free(full);
                 cur = NULL;
                 c = 1; h = oh; w = ow;
+                continue;
+            }
+            if (rc == OR_OK && d[0] == OR_SOFTMAXN) {
+                /* p[class][i] = exp(z_class - max) / sum_j exp(z_j - max) */
+                for (int64_t i = 0; i < oh * ow; ++i) {
+                    double m = full[i];
+                    for (int64_t j = 1; j < cout; ++j)
+                        if (full[j * oh * ow + i] > m) m = full[j * oh * ow + i];
+                    double den = 0.0;
+                    for (int64_t j = 0; j < cout; ++j) den += exp(full[j * oh * ow + i] - m);
+                    for (int64_t j = 0; j < cout; ++j) p[j * oh * ow + i] = exp(full[j * oh * ow + i] - m) / den;
+                }
+                free(full);
+                cur = NULL;
+                c = cout; h = oh; w = ow;
                 continue;
             }
             if (rc == OR_OK && G > 1) {
@@ -236,10 +258,32 @@ int oracle_run_layers(const int32_t* desc, int n_layers, const double* params, c
     }
     {
         const int kind = desc[OR_DW * (n_layers - 1)];
-        if (rc == OR_OK && kind != OR_HEAD && kind != OR_SOFTMAX) rc = OR_ERR_ARG;
+        if (rc == OR_OK && kind != OR_HEAD && kind != OR_SOFTMAX && kind != OR_SOFTMAXN) rc = OR_ERR_ARG;
     }
     free(cur);
     return rc;
+}
+
+/* Single-channel input (the membrane networks). */
+int oracle_run_layers(const int32_t* desc, int n_layers, const double* params, const double* xp,
+                      int64_t ph, int64_t pw, double* p) {
+    return oracle_run_layers_mc(desc, n_layers, params, xp, 1, ph, pw, p);
+}
+
+/*
+ * J of the MaskExtend transfer (Sec. 3.2): smoothing by the 3x3 mean (reflect-101 at the borders)
+ * and thresholding: mask[i][j] = 1 if mean of p over (i-1..i+1, j-1..j+1) >= thr, else 0.
+ */
+int oracle_smooth_threshold(const double* p, int64_t h, int64_t w, double thr, uint8_t* mask) {
+    if (!p || !mask || h < 2 || w < 2) return OR_ERR_ARG;
+    for (int64_t i = 0; i < h; ++i)
+        for (int64_t j = 0; j < w; ++j) {
+            double s = 0.0;
+            for (int64_t a = -1; a <= 1; ++a)
+                for (int64_t b = -1; b <= 1; ++b) s += p[oracle_reflect101(i + a, h) * w + oracle_reflect101(j + b, w)];
+            mask[i * w + j] = (s / 9.0 >= thr) ? 1 : 0;
+        }
+    return OR_OK;
 }
 
 /*

@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 # Layer kinds of the workload descriptions (same numbering as the library's mb_layer_kind).
-CONV, MAXFILTER, HEAD_SIGMOID, HEAD_SOFTMAX2 = 0, 1, 2, 3
+CONV, MAXFILTER, HEAD_SIGMOID, HEAD_SOFTMAX2, HEAD_SOFTMAX = 0, 1, 2, 3, 4
 
 # (kind, ksize, cin, cout, relu[, dilation[, maxout groups]]); dilation and groups default to 1.
 # The measured stand-in network: conv5x5 1->32 ReLU, 2x2 stride-1 max-filter, conv5x5 32->32
@@ -69,10 +69,27 @@ FASTMEMB_3NM = (
     (HEAD_SOFTMAX2, 4, 32, 2, 0, 16, 1),
 )
 
+# MaskExtend (Sec. 3.2): 12 input maps, five [conv4x4 -> max-out 2] stages with 32, 40, 48, 56, 64
+# features (the first four followed by pools: dilations 1, 2, 4, 8, 16 in dense form), then a 1x1
+# head to 3 classes (object, other neurons, membrane) with a softmax. Field of view 109x109.
+MASKEXTEND = (
+    (CONV, 4, 12, 32, 0, 1, 2),
+    (MAXFILTER, 2, 32, 32, 0, 1, 1),
+    (CONV, 4, 32, 40, 0, 2, 2),
+    (MAXFILTER, 2, 40, 40, 0, 2, 1),
+    (CONV, 4, 40, 48, 0, 4, 2),
+    (MAXFILTER, 2, 48, 48, 0, 4, 1),
+    (CONV, 4, 48, 56, 0, 8, 2),
+    (MAXFILTER, 2, 56, 56, 0, 8, 1),
+    (CONV, 4, 56, 64, 0, 16, 2),
+    (HEAD_SOFTMAX, 1, 64, 3, 0, 1, 1),
+)
+
 TEACHER_WEIGHT_SEED = 20161206
 STUDENT_WEIGHT_SEED = 20161207
 FASTMEMB_WEIGHT_SEED = 20161208
 FASTMEMB_3NM_WEIGHT_SEED = 20161209
+MASKEXTEND_WEIGHT_SEED = 20161210
 BASE_SEED = 1612021200  # + workload index
 
 
@@ -168,7 +185,7 @@ def param_count(layers) -> int:
     n = 0
     for layer in layers:
         kind, k, cin, cout = layer[:4]
-        if kind in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2):
+        if kind in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2, HEAD_SOFTMAX):
             co = cout * _groups(layer)
             n += co * cin * k * k + co
     return n
@@ -182,10 +199,10 @@ def init_params(layers, seed: int, bias_std: float = 0.01, center_head: bool = F
     a deep max-out stack's map away from saturation)."""
     parts = []
     l = 0
-    n_par = sum(1 for layer in layers if layer[0] in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2))
+    n_par = sum(1 for layer in layers if layer[0] in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2, HEAD_SOFTMAX))
     for layer in layers:
         kind, k, cin, cout = layer[:4]
-        if kind in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2):
+        if kind in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2, HEAD_SOFTMAX):
             co = cout * _groups(layer)
             w, b = he_normal(seed + l, cin * k * k, co * cin * k * k, co, bias_std)
             if center_head and l == n_par - 1:
@@ -204,3 +221,18 @@ def block_shapes(seed: int, n_blocks: int, side_lo: int = 256, side_hi: int = 15
     ws = uniform_ints(seed + 1, n_blocks, side_lo, side_hi)
     ds = uniform_ints(seed + 2, n_blocks, depth_lo, depth_hi)
     return [(int(d), int(h), int(w)) for d, h, w in zip(ds, hs, ws)]
+
+
+def disk_masks(n: int, h: int, w: int, cy: float, cx: float, r: float, dy: float = 0.0, dx: float = 0.0):
+    """n binary object masks [n][h][w] (uint8 0/1): disks of radius r centred at (cy + i dy,
+    cx + i dx) in section i: a seeded stand-in for an object followed across sections."""
+    yy, xx = np.mgrid[0:h, 0:w]
+    out = np.empty((n, h, w), dtype=np.uint8)
+    for i in range(n):
+        out[i] = ((yy - (cy + i * dy)) ** 2 + (xx - (cx + i * dx)) ** 2 <= r * r).astype(np.uint8)
+    return out
+
+
+def membrane_maps(em_u8) -> np.ndarray:
+    """Stand-in membrane probability maps for an EM stack: 1 - u/255 (membranes are dark), FP32."""
+    return (1.0 - np.asarray(em_u8, dtype=np.float32) / np.float32(255.0)).astype(np.float32)

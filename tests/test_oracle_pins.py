@@ -21,7 +21,7 @@ def split_params(layers, params):
     out, o = [], 0
     for layer in layers:
         kind, k, cin, cout = layer[:4]
-        if kind in (synth.CONV, synth.HEAD_SIGMOID, synth.HEAD_SOFTMAX2):
+        if kind in (synth.CONV, synth.HEAD_SIGMOID, synth.HEAD_SOFTMAX2, synth.HEAD_SOFTMAX):
             cout *= layer[6] if len(layer) > 6 else 1
             n = cout * cin * k * k
             out.append((params[o:o + n].reshape(cout, cin, k, k), params[o + n:o + n + cout]))
