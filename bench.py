@@ -15,6 +15,8 @@ the same through the C ABI with pinned HOST buffers (copies inside the timed reg
         student-only and cascade (teacher fallback on 256^2 tiles) on the cfg3 volume;
   cfg6  FastMemb_3nm (one more stage, 109 field of view) on 2048x2048x8 (3 nm images), FP32 and
         BF16, dense and sub-sampled by 2 (a 6 nm output map), errors on 2 seeded 256x256 crops;
+  cfg7  MaskExtend (Sec. 3.2): the +z transfer recursion on a 512x512 window for 16 sections
+        (FP32), errors of one step's 3 class maps against the oracle on a 128x128 crop;
   cfg5  FastMemb in dense form (Sec. 2.2) on the cfg1 volume, FP32 and BF16, dense and sub-sampled
         by 2 (the pruned fragment tree), with errors against the oracle on 3 seeded 384x384 crops
         (true context; even crop origins, so the sub-sampled crops are the dense crops' even pixels).
@@ -44,6 +46,7 @@ TENSOR_FLOP_PER_PX = 2 * 2 * 25 * 32 * 32                   # 102,400 (layers 2 
 STUDENT_FLOP_PER_PX = 2 * (9 * 16 + 9 * 16 * 16 + 16)       # 4,928
 FASTMEMB_FLOP_PER_PX = 2 * (16 * 64 + 2 * 16 * 32 * 64 + 16 * 32 * 2)  # 135,168
 FASTMEMB3_FLOP_PER_PX = 2 * (16 * 64 + 3 * 16 * 32 * 64 + 16 * 32 * 2)  # 200,704
+MASKEXTEND_FLOP_PER_PX = 2 * (16 * 12 * 64 + 16 * 32 * 80 + 16 * 40 * 96 + 16 * 48 * 112 + 16 * 56 * 128 + 64 * 3)
 # DRAM bytes per output voxel of tc_fused_teacher (BF16), from the ncu capture summarised in
 # profiles/tc_fused_teacher_bf16_1024x1024x4.md; None when the kernel changed since.
 TC_TRAFFIC_PER_VOX = None
@@ -196,7 +199,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--configs", default="1,2,3,4,5,6", help="extra configurations measured after the headline")
+    ap.add_argument("--configs", default="1,2,3,4,5,6,7", help="extra configurations measured after the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -519,6 +522,33 @@ def main():
             fm.close()
         paths["cfg6_fastmemb3nm_2048x2048x8"] = p
         del x6, o6, s6
+    # ---- cfg7: MaskExtend transfer recursion on a 512x512 window ----------------------------------------
+    if "7" in configs:
+        Z7, H7, W7, N7 = 20, 512, 512, 16
+        em7 = synth.em_volume(synth.BASE_SEED + 7, Z7, H7, W7)
+        mb7 = synth.membrane_maps(em7)
+        sd7 = synth.disk_masks(4, H7, W7, H7 / 2, W7 / 2, H7 / 5, 2.0, -1.0)
+        me_params = synth.init_params(synth.MASKEXTEND, synth.MASKEXTEND_WEIGHT_SEED)
+        me = m.Net(synth.MASKEXTEND, m.MB_PREC_FP32, local, me_params)
+        d_em, d_mb, d_sd = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (em7, mb7, sd7))
+        masks7 = torch.zeros((N7, H7, W7), dtype=torch.uint8, device="cuda")
+        probs7 = torch.zeros((N7, 3, H7, W7), dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            ms = time_device(lambda: m.mb_mask_extend(me.handle, d_em, d_mb, Z7, H7, W7, d_sd, 2, N7, masks7, probs7,
+                                                      stream=stream), 3, 1, stream, flush)
+        # one step's class maps against the oracle on a 128x128 crop with its true context
+        y0, x0 = 192, 160
+        xp = oracle.maskextend_input(em7, mb7, {-2 + i: sd7[i] for i in range(4)}, 2, 54)
+        ref = oracle.run_layers_mc(synth.MASKEXTEND, me_params, xp[:, y0:y0 + 128 + 108, x0:x0 + 128 + 108])
+        got = probs7[0, :, y0:y0 + 128, x0:x0 + 128].cpu().numpy()
+        vox7 = N7 * H7 * W7
+        mv = vox7 / (statistics.mean(ms) / 1e3) / 1e6
+        paths["cfg7_maskextend_512x512x16steps"] = {
+            "mvox_s": mv, "ms": statistics.mean(ms), "steps_per_s": N7 / (statistics.mean(ms) / 1e3),
+            "tflops": MASKEXTEND_FLOP_PER_PX * mv * 1e6 / 1e12, "flop_per_px": MASKEXTEND_FLOP_PER_PX,
+            "mask_fraction": float(masks7.float().mean()),
+            "error_step0_crop128": {k: v for k, v in oracle.metrics(got, ref).items()}}
+        me.close()
     if paths:
         line["paths"] = paths
     if rank == 0 and not args.no_cpu_baseline:

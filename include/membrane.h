@@ -52,7 +52,13 @@ typedef enum {
 
 typedef enum { MB_PREC_FP32 = 0, MB_PREC_BF16 = 1, MB_PREC_FP8 = 2 } mb_precision;
 typedef enum { MB_OUT_F32 = 0, MB_OUT_U8 = 1 } mb_out_type;
-typedef enum { MB_CONV = 0, MB_MAXFILTER = 1, MB_HEAD_SIGMOID = 2, MB_HEAD_SOFTMAX2 = 3 } mb_layer_kind;
+typedef enum {
+    MB_CONV = 0,
+    MB_MAXFILTER = 1,
+    MB_HEAD_SIGMOID = 2,
+    MB_HEAD_SOFTMAX2 = 3,
+    MB_HEAD_SOFTMAX = 4
+} mb_layer_kind;
 
 /*
  * One layer of a network description (Sec. 2.2 describes the networks in prose as alternating
@@ -66,6 +72,8 @@ typedef enum { MB_CONV = 0, MB_MAXFILTER = 1, MB_HEAD_SIGMOID = 2, MB_HEAD_SOFTM
  *   MB_HEAD_SIGMOID:  1x1 cin -> 1, + bias, sigmoid; must be the last layer.
  *   MB_HEAD_SOFTMAX2: ksize x ksize cross-correlation with dilation d, cin -> 2, + bias, then the
  *                     2-class softmax's class-1 probability 1 / (1 + exp(z0 - z1)); last layer.
+ *   MB_HEAD_SOFTMAX:  1x1 cin -> cout classes, + bias, softmax; every class probability is an
+ *                     output; last layer (MaskExtend).
  * dilation and maxout_groups 0 are read as 1.
  * Supported networks: the teacher (conv5x5 1->32 ReLU, maxfilter 2, conv5x5 32->32 ReLU,
  * maxfilter 2, conv5x5 32->32 ReLU, head 32->1) in FP32, BF16 and FP8; the student (conv3x3
@@ -74,7 +82,10 @@ typedef enum { MB_CONV = 0, MB_MAXFILTER = 1, MB_HEAD_SIGMOID = 2, MB_HEAD_SOFTM
  * conv4x4 32->32 G=2 d=4, maxfilter d=4, softmax head conv4x4 32->2 d=8; no ReLU; radius 26,
  * so its slices need h, w >= 27) and FastMemb_3nm (Sec. 2.2, "A subsampling CNN for 3 nm data":
  * one more stage, conv4x4 32->32 G=2 d=8 and maxfilter d=8, then the head at d=16; radius 54,
- * slices h, w >= 55), both in FP32 and BF16.
+ * slices h, w >= 55), both in FP32 and BF16; and MaskExtend (Sec. 3.2: conv4x4 12->32 G=2 d=1,
+ * maxfilter d=1, conv4x4 32->40 G=2 d=2, maxfilter d=2, conv4x4 40->48 G=2 d=4, maxfilter d=4,
+ * conv4x4 48->56 G=2 d=8, maxfilter d=8, conv4x4 56->64 G=2 d=16, head 1x1 64->3 softmax; radius
+ * 54) in FP32, run only through mb_mask_extend (the map calls return MB_ERR_UNSUPPORTED).
  */
 typedef struct {
     int32_t kind, ksize, dilation, cin, cout, relu, maxout_groups;
@@ -250,6 +261,25 @@ const char* mb_last_error(void);
 
 /* Number of kernel launches this library has issued since load (for launch accounting). */
 int64_t mb_launch_count(void);
+
+/*
+ * MaskExtend transfer (Sec. 3.2), recursed in +z: for z = z0 .. z0 + n_steps - 1,
+ *   Mask_z = J(CNN(Mask_{z-4..z-1}, EM_{z-1..z+1}, FastMemb_{z-2..z+2}))
+ * where CNN is the dense inference of a MaskExtend net over the whole h x w section (12 input maps:
+ * EM u/255, the object's binary masks, membrane probabilities; each mirror-padded reflect-101 by
+ * 54), and J is the 3x3 mean of the object-class probability (reflect-101 borders) followed by
+ * >= threshold. Each new mask feeds the next step.
+ *   em:         uint8 [z][h][w] EM stack            membrane: float [z][h][w] membrane maps
+ *   seed_masks: uint8 [4][h][w] masks of z0-4 .. z0-1 (0 or 1)
+ *   masks_out:  uint8 [n_steps][h][w] (0/1)        probs_out: float [n_steps][3][h][w] or NULL
+ *               (classes: object, other neurons, membrane)
+ * Needs 2 <= z0 and z0 + n_steps + 1 < z (else MB_ERR_SHAPE). FP32 MaskExtend nets only. Device
+ * pointers; asynchronous on `stream`. The net's workspace is shared by its calls: calls on one
+ * net must not overlap on the GPU.
+ */
+mb_status mb_mask_extend(mb_net* net, const uint8_t* em, const float* membrane, int64_t z, int64_t h, int64_t w,
+                         const uint8_t* seed_masks, int64_t z0, int64_t n_steps, float threshold, uint8_t* masks_out,
+                         float* probs_out, void* stream);
 
 #ifdef __cplusplus
 }

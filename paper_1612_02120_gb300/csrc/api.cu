@@ -127,6 +127,12 @@ static int detect_family(const mb_layer_desc* L, int n) {
         same_layer_dm(L[6], MB_CONV, 4, 32, 32, 8, 2) && same_layer_dm(L[7], MB_MAXFILTER, 2, 32, 32, 8, 1) &&
         same_layer_dm(L[8], MB_HEAD_SOFTMAX2, 4, 32, 2, 16, 1))
         return FAMILY_FASTMEMB_3NM;
+    if (n == 10 && same_layer_dm(L[0], MB_CONV, 4, 12, 32, 1, 2) && same_layer_dm(L[1], MB_MAXFILTER, 2, 32, 32, 1, 1) &&
+        same_layer_dm(L[2], MB_CONV, 4, 32, 40, 2, 2) && same_layer_dm(L[3], MB_MAXFILTER, 2, 40, 40, 2, 1) &&
+        same_layer_dm(L[4], MB_CONV, 4, 40, 48, 4, 2) && same_layer_dm(L[5], MB_MAXFILTER, 2, 48, 48, 4, 1) &&
+        same_layer_dm(L[6], MB_CONV, 4, 48, 56, 8, 2) && same_layer_dm(L[7], MB_MAXFILTER, 2, 56, 56, 8, 1) &&
+        same_layer_dm(L[8], MB_CONV, 4, 56, 64, 16, 2) && same_layer_dm(L[9], MB_HEAD_SOFTMAX, 1, 64, 3, 1, 1))
+        return FAMILY_MASKEXTEND;
     if (n == 6 && same_layer(L[0], MB_CONV, 5, 1, 32, 1) && same_layer(L[1], MB_MAXFILTER, 2, 32, 32, 0) &&
         same_layer(L[2], MB_CONV, 5, 32, 32, 1) && same_layer(L[3], MB_MAXFILTER, 2, 32, 32, 0) &&
         same_layer(L[4], MB_CONV, 5, 32, 32, 1) && same_layer(L[5], MB_HEAD_SIGMOID, 1, 32, 1, 0))
@@ -168,6 +174,7 @@ static int net_radius(const mb_net* net) {
         case FAMILY_STUDENT: return kStudentRadius;
         case FAMILY_FASTMEMB: return kFastMembRadius;
         case FAMILY_FASTMEMB_3NM: return kFastMemb3nmRadius;
+        case FAMILY_MASKEXTEND: return kFastMemb3nmRadius;
         default: return kTeacherRadius;
     }
 }
@@ -179,6 +186,15 @@ static mb_status check_net_slice(const mb_net* net, int64_t h, int64_t w) {
         set_error("slice %lldx%lld: this net's radius is %d, so h and w must be >= %d", (long long)h, (long long)w,
                   R, R + 1);
         return MB_ERR_SHAPE;
+    }
+    return MB_OK;
+}
+
+// MaskExtend reads a 12-map stack, not one uint8 slice: only mb_mask_extend runs it.
+static mb_status check_map_net(const mb_net* net, const char* call) {
+    if (net && net->family == FAMILY_MASKEXTEND) {
+        set_error("%s: MaskExtend nets run through mb_mask_extend", call);
+        return MB_ERR_UNSUPPORTED;
     }
     return MB_OK;
 }
@@ -361,7 +377,7 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
     }
     for (int i = 0; i < n_layers; ++i) {
         const mb_layer_desc& L = layers[i];
-        if (L.kind < MB_CONV || L.kind > MB_HEAD_SOFTMAX2 || L.ksize <= 0 || L.cin <= 0 || L.cout <= 0 ||
+        if (L.kind < MB_CONV || L.kind > MB_HEAD_SOFTMAX || L.ksize <= 0 || L.cin <= 0 || L.cout <= 0 ||
             L.dilation < 0 || L.maxout_groups < 0) {
             set_error("mb_net_create: layer %d is malformed", i);
             return MB_ERR_INVALID_ARG;
@@ -369,12 +385,16 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
     }
     const int fam = detect_family(layers, n_layers);
     if (!fam) {
-        set_error("mb_net_create: no kernel for this layer stack (teacher 5x5/32, student 3x3/16, FastMemb or "
-                  "FastMemb_3nm only)");
+        set_error("mb_net_create: no kernel for this layer stack (teacher 5x5/32, student 3x3/16, FastMemb, "
+                  "FastMemb_3nm or MaskExtend only)");
         return MB_ERR_UNSUPPORTED;
     }
     if (fam == FAMILY_STUDENT && prec == MB_PREC_FP8) {
         set_error("mb_net_create: the student runs in FP32 or BF16");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (fam == FAMILY_MASKEXTEND && prec != MB_PREC_FP32) {
+        set_error("mb_net_create: MaskExtend runs in FP32");
         return MB_ERR_UNSUPPORTED;
     }
     if (is_fastmemb(fam) && prec == MB_PREC_FP8) {
@@ -476,7 +496,10 @@ mb_status mb_load_weights(mb_net* net, const float* params, int64_t n_params) {
     if (net->family == FAMILY_STUDENT && net->prec == MB_PREC_BF16)
         for (auto& v : fwd) v = bf16_round(v);
     std::vector<float> packed;
-    simt_pack(net, fwd.data(), packed);
+    if (net->family == FAMILY_MASKEXTEND)
+        me_pack(net, fwd.data(), packed);
+    else
+        simt_pack(net, fwd.data(), packed);
     if (!net->d_params) MB_TRY(dev_alloc((void**)&net->d_params, sizeof(float) * n_params));
     if (!net->d_simt) MB_TRY(dev_alloc((void**)&net->d_simt, sizeof(float) * packed.size()));
     net->simt_floats = packed.size();
@@ -554,6 +577,7 @@ mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
                           mb_out_type out_type, void* stream) {
     API_BEGIN
     MB_TRY(check_ready(net));
+    MB_TRY(check_map_net(net, "mb_infer_volume"));
     if ((!in || !out) && z > 0) {
         set_error("mb_infer_volume: null buffer");
         return MB_ERR_INVALID_ARG;
@@ -579,6 +603,7 @@ mb_status mb_infer_volume_subsampled(mb_net* net, const uint8_t* in, int64_t z, 
                                      void* out, mb_out_type out_type, void* stream) {
     API_BEGIN
     MB_TRY(check_ready(net));
+    MB_TRY(check_map_net(net, "mb_infer_volume_subsampled"));
     if ((!in || !out) && z > 0) {
         set_error("mb_infer_volume_subsampled: null buffer");
         return MB_ERR_INVALID_ARG;
@@ -608,6 +633,7 @@ mb_status mb_infer_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
                           int64_t x0, int64_t rows, int64_t cols, void* out, mb_out_type out_type, void* stream) {
     API_BEGIN
     MB_TRY(check_ready(net));
+    MB_TRY(check_map_net(net, "mb_infer_region"));
     if ((!in || !out) && z > 0) {
         set_error("mb_infer_region: null buffer");
         return MB_ERR_INVALID_ARG;
@@ -633,6 +659,7 @@ mb_status mb_infer_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
 }
 
 static mb_status check_blocks(const mb_net* net, const mb_block* blocks, int32_t n, mb_out_type ot) {
+    MB_TRY(check_map_net(net, "mb_infer_batch"));
     if (!blocks && n > 0) {
         set_error("blocks is NULL");
         return MB_ERR_INVALID_ARG;
@@ -766,6 +793,37 @@ mb_status mb_infer_cascade(mb_net* student, mb_net* teacher, const uint8_t* in, 
     API_GUARD(student)
     return cascade(student, teacher, in, z, h, w, out, tile, lo, hi, max_frac, fallback_rate, tile_flags,
                    (cudaStream_t)stream);
+}
+
+mb_status mb_mask_extend(mb_net* net, const uint8_t* em, const float* membrane, int64_t z, int64_t h, int64_t w,
+                         const uint8_t* seed_masks, int64_t z0, int64_t n_steps, float threshold, uint8_t* masks_out,
+                         float* probs_out, void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(net));
+    if (net->family != FAMILY_MASKEXTEND) {
+        set_error("mb_mask_extend: not a MaskExtend net");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (!em || !membrane || !seed_masks || (!masks_out && n_steps > 0) || n_steps < 0 || !(threshold == threshold)) {
+        set_error("mb_mask_extend: null buffer or bad arguments");
+        return MB_ERR_INVALID_ARG;
+    }
+    MB_TRY(check_slice(z, h, w));
+    MB_TRY(check_net_slice(net, h, w));
+    if (n_steps > 0 && (z0 < 2 || z0 + n_steps + 2 > z)) {
+        set_error("mb_mask_extend: sections z0-2 .. z0+n_steps+1 must lie in the stack of %lld (z0 %lld, %lld steps)",
+                  (long long)z, (long long)z0, (long long)n_steps);
+        return MB_ERR_SHAPE;
+    }
+    if (n_steps == 0) return MB_OK;
+    API_GUARD(net)
+    if (!is_device_ptr(em) || !is_device_ptr(membrane) || !is_device_ptr(seed_masks) || !is_device_ptr(masks_out) ||
+        (probs_out && !is_device_ptr(probs_out))) {
+        set_error("mb_mask_extend: device pointers only");
+        return MB_ERR_INVALID_ARG;
+    }
+    return maskextend_run(net, em, membrane, z, h, w, seed_masks, z0, n_steps, threshold, masks_out, probs_out,
+                          (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -12,7 +12,7 @@
 
 namespace mb {
 
-enum Family { FAMILY_TEACHER = 1, FAMILY_STUDENT = 2, FAMILY_FASTMEMB = 3, FAMILY_FASTMEMB_3NM = 4 };
+enum Family { FAMILY_TEACHER = 1, FAMILY_STUDENT = 2, FAMILY_FASTMEMB = 3, FAMILY_FASTMEMB_3NM = 4, FAMILY_MASKEXTEND = 5 };
 
 // Teacher geometry: conv5x5 x3 with two 2x2 max-filters -> receptive radius 7.
 constexpr int kTeacherRadius = 7;
@@ -124,6 +124,11 @@ mb_status fm_tc_poll_error(mb_net* net);
 mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int64_t src_rows,
                       int64_t src_cols, int in_rows, int in_cols, int dm, int stride, void* out, int64_t out_slice,
                       int64_t out_pitch, int out_h, int out_w, int d, int nz, int out_u8, cudaStream_t st);
+// MaskExtend (maskextend.cu): SIMT weight layout, and the +z transfer recursion (device pointers).
+void me_pack(const mb_net* net, const float* params, std::vector<float>& out);
+mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int64_t zt, int64_t h, int64_t w,
+                         const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
+                         float* probs_out, cudaStream_t st);
 // FP32 teacher activations after the two max-filters: per-channel amax over n slices (device out[64]).
 mb_status simt_teacher_amax(mb_net* net, const uint8_t* in, int64_t n, int64_t h, int64_t w, float* d_amax,
                             cudaStream_t st);

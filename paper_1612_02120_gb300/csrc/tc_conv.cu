@@ -45,7 +45,7 @@ constexpr int kPitch = 136;          // pixels per ring row (128 used + dx overr
 constexpr int kStrip = 118;          // valid output columns per 128-pixel strip
 constexpr int kInCols = 132;         // input columns read per row
 constexpr int kInRing = 8;           // input row ring
-constexpr int kRing = 4;             // mf1 / mf2 ring slots
+constexpr int kRing = 6;             // mf1 / mf2 ring slots
 constexpr int kMaxBlocks = 64;       // blocks per launch (kernel-parameter table)
 constexpr int kWpackConstOff = 2 * 10 * 5120;  // constants follow the largest packed B (BF16)
 constexpr uint64_t kWaitNs = 4000000000ull;
@@ -100,6 +100,7 @@ struct Cfg {
     static constexpr int kBars = 2 * kInRing + 4 * kRing + 4 * 8 + 2;
     static constexpr int oMisc = oBar + kBars * 8;
     static constexpr int kSmem = oMisc + 16;
+    static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
 struct Bars {

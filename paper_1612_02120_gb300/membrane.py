@@ -16,13 +16,13 @@ MB_OK, MB_ERR_INVALID_ARG, MB_ERR_SHAPE, MB_ERR_OOM, MB_ERR_CUDA, MB_ERR_TIMEOUT
     MB_ERR_UNSUPPORTED = range(8)
 MB_PREC_FP32, MB_PREC_BF16, MB_PREC_FP8 = 0, 1, 2
 MB_OUT_F32, MB_OUT_U8 = 0, 1
-MB_CONV, MB_MAXFILTER, MB_HEAD_SIGMOID, MB_HEAD_SOFTMAX2 = 0, 1, 2, 3
+MB_CONV, MB_MAXFILTER, MB_HEAD_SIGMOID, MB_HEAD_SOFTMAX2, MB_HEAD_SOFTMAX = 0, 1, 2, 3, 4
 
 EXPORTED = (
     "mb_net_create", "mb_net_destroy", "mb_net_param_count", "mb_load_weights", "mb_get_weights",
     "mb_calibrate_fp8", "mb_infer_volume", "mb_infer_region", "mb_infer_batch", "mb_infer_batch_per_block",
     "mb_autotune", "mb_student_loss_grad", "mb_student_train", "mb_infer_cascade", "mb_status_string",
-    "mb_last_error", "mb_launch_count", "mb_infer_volume_noalloc", "mb_infer_volume_subsampled",
+    "mb_last_error", "mb_launch_count", "mb_infer_volume_noalloc", "mb_infer_volume_subsampled", "mb_mask_extend",
 )
 
 
@@ -82,6 +82,7 @@ def load() -> ctypes.CDLL:
         "mb_launch_count": ([], i64),
         "mb_infer_volume_noalloc": ([p, p, i64, i64, i64, p, i32, p], st),
         "mb_infer_volume_subsampled": ([p, p, i64, i64, i64, i32, p, i32, p], st),
+        "mb_mask_extend": ([p, p, p, i64, i64, i64, p, i64, i64, ctypes.c_float, p, p, p], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -183,6 +184,13 @@ def mb_infer_volume_subsampled(net, inp, z, h, w, factor, out, out_type=MB_OUT_F
     """FastMemb map at even rows and columns: out is z x ceil(h/2) x ceil(w/2)."""
     check(load().mb_infer_volume_subsampled(net, ptr(inp), z, h, w, factor, ptr(out), out_type,
                                             stream_handle(stream)), "mb_infer_volume_subsampled")
+
+
+def mb_mask_extend(net, em, membrane, z, h, w, seed_masks, z0, n_steps, masks_out, probs_out=None,
+                   threshold=0.5, stream=None) -> None:
+    """MaskExtend transfer recursion in +z (device tensors)."""
+    check(load().mb_mask_extend(net, ptr(em), ptr(membrane), z, h, w, ptr(seed_masks), z0, n_steps, float(threshold),
+                                ptr(masks_out), ptr(probs_out), stream_handle(stream)), "mb_mask_extend")
 
 
 def mb_infer_volume_noalloc(net, inp, z, h, w, out, out_type=MB_OUT_F32, stream=None) -> None:
