@@ -912,7 +912,44 @@ static int fill_blocks(mb_net* net, TcParams& prm, const mb_block* blocks, int n
                        const int64_t* y0, const int64_t* x0, const int64_t* rows, const int64_t* cols,
                        mb_out_type ot) {
     int nb = 0, items = 0;
-    const int R = std::max(8, net->rows_per_item);
+    // Rows per work item: the tuned value, unless the launch would not fill one wave of CTAs (a
+    // streamed slab, a few small blocks). Then the candidates R, R/2, .. 64 are compared by the
+    // predicted time, waves x (rows + 9) (each item restarts the layer-2 row pipeline, 9 extra
+    // rows), ties to the larger R. The choice never changes a result.
+    int R = std::max(8, net->rows_per_item);
+    {
+        if (g_num_sms == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                g_num_sms = 0;
+            }
+        }
+        const int64_t sms = std::max(g_num_sms, 1);
+        auto n_items = [&](int r) {
+            int64_t n = 0;
+            int seen = 0;
+            for (int i = first; i < n_blocks && seen < kMaxBlocks; ++i) {
+                if (blocks[i].z == 0 || rows[i] == 0 || cols[i] == 0) continue;
+                n += blocks[i].z * ((cols[i] + kStrip - 1) / kStrip) * ((rows[i] + r - 1) / r);
+                ++seen;
+            }
+            return n;
+        };
+        if (n_items(R) < sms) {
+            int64_t best = INT64_MAX;
+            int best_r = R;
+            for (int r = R; r >= 64; r /= 2) {
+                const int64_t cost = (n_items(r) + sms - 1) / sms * (r + 9);
+                if (cost < best) {
+                    best = cost;
+                    best_r = r;
+                }
+            }
+            R = best_r;
+        }
+    }
     for (int i = first; i < n_blocks && nb < kMaxBlocks; ++i) {
         const mb_block& b = blocks[i];
         if (b.z == 0 || rows[i] == 0 || cols[i] == 0) continue;
@@ -1153,8 +1190,8 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
                 const int S = kRing;  // A-ring depth: fixed at compile time, reported
                 net->rows_per_item = R;
                 net->stages = S;
-                float ms_sum = 0.f;
-                for (int rep = 0; rep < 3 && rc == MB_OK; ++rep) {
+                float ms_rep[5] = {};
+                for (int rep = 0; rep < 5 && rc == MB_OK; ++rep) {
                     cudaError_t e = cudaEventRecord(e0, st);
                     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__); break; }
                     rc = tc_infer_blocks(net, &b, 1, &y0, &x0, &h, &w, MB_OUT_F32, st, false);
@@ -1164,11 +1201,14 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
                     float ms = 0.f;
                     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                     if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing", __FILE__, __LINE__); break; }
-                    if (rep > 0) ms_sum += ms;  // first repetition warms up
+                    ms_rep[rep] = ms;
                 }
                 if (rc != MB_OK) break;
-                if (ms_sum / 2 < best) {
-                    best = ms_sum / 2;
+                // median of the 4 timed repetitions (the first one warms up)
+                std::sort(ms_rep + 1, ms_rep + 5);
+                const float med = 0.5f * (ms_rep[2] + ms_rep[3]);
+                if (med < best) {
+                    best = med;
                     best_r = R;
                     best_s = S;
                 }
