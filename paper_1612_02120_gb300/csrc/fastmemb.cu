@@ -6,17 +6,11 @@
 // pool into a stride-1 max-filter plus 2-factor sub-sampling; here that becomes a max-filter
 // with dilation d and a conv with dilation 2d behind it (d = 1, 2, 4; the head has dilation 8).
 //
-// The paper's max-pooling fragments are also how the kernel tiles the work: a conv with
-// dilation d restricted to one residue class (y mod d, x mod d) of the output is a plain 4x4
-// conv on the d-strided sub-grid (one fragment), so every CTA works on one fragment tile and
-// keeps the register reuse of an undilated conv (each thread's 4 pixels and 7 input columns are
-// consecutive in fragment coordinates).
-//
-// Per CTA of 256 threads: a TH x 32 fragment tile with all CO conv channels; each thread holds 4
-// consecutive fragment pixels x CPT channels. The input is staged CC channels at a time; the
-// previous stage's dilated 2x2 max-filter is applied while staging. Epilogues: max-out over
-// adjacent channel pairs (conv channel 2c+g -> channel c) to FP32 [slice][y][x][32], or the
-// 2-class softmax p = 1 / (1 + exp(z0 - z1)).
+// The convolution kernel (fm_conv.cuh) tiles each dilated conv by the paper's max-pooling
+// fragments: a conv with dilation d restricted to one residue class (y mod d, x mod d) is a plain
+// 4x4 conv on the d-strided sub-grid, so every CTA keeps the register reuse of an undilated conv.
+// The previous stage's dilated max-filter is applied while staging; epilogues are max-out of
+// adjacent channel pairs or the 2-class softmax p = 1 / (1 + exp(z0 - z1)).
 //
 // Domains for an output region rows x cols (radius 26):
 //   conv1 out (rows+49)^2 .. conv2 out (rows+42) .. conv3 out (rows+28) .. head out rows
