@@ -166,6 +166,22 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "Mvox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """This rank's time -> the maximum over all ranks (the whole job finishes with its slowest
+    rank); unchanged on a single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mvox_s(world, vox_per_rank, seconds):
+    """Whole-job throughput: every rank processed vox_per_rank voxels (weak scaling, replicas)."""
+    return world * vox_per_rank / seconds / 1e6
+
+
 def time_device(fn, steps, warmup, stream, flush):
     """Per-step CUDA-event times (ms) of fn() on `stream`, L2 flushed between steps."""
     import torch
@@ -255,14 +271,10 @@ def main():
         with ClockSampler(local) as clk:
             step_ms = time_device(step, args.steps, 0, stream, flush)
         launches = m.launch_count() - launches0
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        barrier()
+    total_ms = max_over_ranks(sum(step_ms), dist)
+    barrier()
     ms_per_step = total_ms / args.steps
-    value = world * vox / (ms_per_step / 1e3) / 1e6
+    value = whole_job_mvox_s(world, vox, ms_per_step / 1e3)
     bf16_map = out.cpu().numpy()
 
     # end to end through the C ABI with pinned host buffers
@@ -273,8 +285,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         m.mb_infer_volume(net.handle, pin_in, Z, H, W, pin_out)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_value = world * vox / e2e_s / 1e6
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist)
+    e2e_value = whole_job_mvox_s(world, vox, e2e_s)
 
     pk, pk_kind = peaks()
     kernel_ms = statistics.mean(step_ms)

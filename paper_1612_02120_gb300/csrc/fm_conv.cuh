@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
     constexpr int IH = TH + K - 1;
     constexpr int IW = TW + K - 1;
     constexpr int IWP = 36;
-    static_assert(CO % CPT == 0 && (CPT == 8 || CPT == 2), "channel split");
+    static_assert(CO % CPT == 0 && (CPT == 16 || CPT == 8 || CPT == 2), "channel split");
     static_assert(CIN % CC == 0 && (CC == 1 || CC == 4 || CC == 8), "channel chunking");
     static_assert(NT <= 256 && TH >= 1, "block size");
     __shared__ __align__(16) float s_in[CC * IH * IWP];
@@ -138,11 +138,12 @@ __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
 #pragma unroll
                 for (int kx = 0; kx < K; ++kx) {
                     float wv[CPT];
-                    if constexpr (CPT == 8) {
-                        const float4 w0 = *reinterpret_cast<const float4*>(wr + kx * CO);
-                        const float4 w1 = *reinterpret_cast<const float4*>(wr + kx * CO + 4);
-                        wv[0] = w0.x; wv[1] = w0.y; wv[2] = w0.z; wv[3] = w0.w;
-                        wv[4] = w1.x; wv[5] = w1.y; wv[6] = w1.z; wv[7] = w1.w;
+                    if constexpr (CPT >= 8) {
+#pragma unroll
+                        for (int q = 0; q < CPT / 4; ++q) {
+                            const float4 w4 = *reinterpret_cast<const float4*>(wr + kx * CO + 4 * q);
+                            wv[4 * q] = w4.x; wv[4 * q + 1] = w4.y; wv[4 * q + 2] = w4.z; wv[4 * q + 3] = w4.w;
+                        }
                     } else {
                         const float2 w0 = *reinterpret_cast<const float2*>(wr + kx * CO);
                         wv[0] = w0.x; wv[1] = w0.y;
@@ -159,29 +160,38 @@ __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
     const int oy = ry + d * (fy0 + ty);
     if (oy >= a.out_h) return;
     if constexpr (OUT == FM_OUT_MAXOUT_BF16) {
+        static_assert(CPT >= 8, "max-out epilogue writes 4 channels per 8 conv channels");
         __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + (int64_t)zi * a.out_slice;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int ox = rx + d * (fx0 + 4 * tx + j);
             if (ox < a.out_w) {
-                __nv_bfloat162 lo = __floats2bfloat162_rn(fmaxf(acc[j][0], acc[j][1]), fmaxf(acc[j][2], acc[j][3]));
-                __nv_bfloat162 hi = __floats2bfloat162_rn(fmaxf(acc[j][4], acc[j][5]), fmaxf(acc[j][6], acc[j][7]));
-                uint2 u;
-                u.x = *reinterpret_cast<uint32_t*>(&lo);
-                u.y = *reinterpret_cast<uint32_t*>(&hi);
-                *reinterpret_cast<uint2*>(o + ((int64_t)oy * a.out_pitch + ox) * (CO / 2) + 4 * cg) = u;
+#pragma unroll
+                for (int q = 0; q < CPT / 8; ++q) {
+                    const float* v = acc[j] + 8 * q;
+                    __nv_bfloat162 lo = __floats2bfloat162_rn(fmaxf(v[0], v[1]), fmaxf(v[2], v[3]));
+                    __nv_bfloat162 hi = __floats2bfloat162_rn(fmaxf(v[4], v[5]), fmaxf(v[6], v[7]));
+                    uint2 u;
+                    u.x = *reinterpret_cast<uint32_t*>(&lo);
+                    u.y = *reinterpret_cast<uint32_t*>(&hi);
+                    *reinterpret_cast<uint2*>(o + ((int64_t)oy * a.out_pitch + ox) * (CO / 2) + (CPT / 2) * cg + 4 * q) =
+                        u;
+                }
             }
         }
     } else if constexpr (OUT == FM_OUT_MAXOUT) {
-        static_assert(CPT == 8, "max-out epilogue writes 4 channels per thread");
+        static_assert(CPT >= 8, "max-out epilogue writes 4 channels per 8 conv channels");
         float* o = static_cast<float*>(a.out) + (int64_t)zi * a.out_slice;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int ox = rx + d * (fx0 + 4 * tx + j);
             if (ox < a.out_w) {
-                const float4 m = make_float4(fmaxf(acc[j][0], acc[j][1]), fmaxf(acc[j][2], acc[j][3]),
-                                             fmaxf(acc[j][4], acc[j][5]), fmaxf(acc[j][6], acc[j][7]));
-                *reinterpret_cast<float4*>(o + ((int64_t)oy * a.out_pitch + ox) * (CO / 2) + 4 * cg) = m;
+#pragma unroll
+                for (int q = 0; q < CPT / 8; ++q) {
+                    const float* v = acc[j] + 8 * q;
+                    const float4 m = make_float4(fmaxf(v[0], v[1]), fmaxf(v[2], v[3]), fmaxf(v[4], v[5]), fmaxf(v[6], v[7]));
+                    *reinterpret_cast<float4*>(o + ((int64_t)oy * a.out_pitch + ox) * (CO / 2) + (CPT / 2) * cg + 4 * q) = m;
+                }
             }
         }
     } else {
