@@ -132,3 +132,21 @@ def test_fp8_uncalibrated_is_not_ready():
     out = torch.empty((1, 16, 16), dtype=torch.float32, device="cuda")
     assert m.load().mb_infer_volume(n.handle, x.data_ptr(), 1, 16, 16, out.data_ptr(), 0, None) == m.MB_ERR_NOT_READY
     n.close()
+
+
+def test_host_streaming_over_several_slabs_equals_device_path():
+    """1024x1024x20 from pinned host buffers streams as slabs of 8, 8 and 4 slices (the third
+    reuses the first slab's buffers); the maps equal the device-resident call bitwise."""
+    import torch
+    from paper_1612_02120_gb300 import build, membrane as m
+    build.build()
+    net = make_net(T, m.MB_PREC_BF16, teacher_params())
+    v = synth.em_volume(5100, 20, 1024, 1024)
+    dev = infer(net, v)
+    pin_in = torch.from_numpy(v).pin_memory()
+    pin_out = torch.empty((20, 1024, 1024), dtype=torch.float32).pin_memory()
+    for _ in range(2):  # the second call reuses the net's slab buffers, streams and events
+        pin_out.fill_(-1.0)
+        m.mb_infer_volume(net.handle, pin_in, 20, 1024, 1024, pin_out)
+        np.testing.assert_array_equal(pin_out.numpy(), dev)
+    net.close()
