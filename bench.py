@@ -544,26 +544,33 @@ def main():
         mb7 = synth.membrane_maps(em7)
         sd7 = synth.disk_masks(4, H7, W7, H7 / 2, W7 / 2, H7 / 5, 2.0, -1.0)
         me_params = synth.init_params(synth.MASKEXTEND, synth.MASKEXTEND_WEIGHT_SEED)
-        me = m.Net(synth.MASKEXTEND, m.MB_PREC_FP32, local, me_params)
         d_em, d_mb, d_sd = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (em7, mb7, sd7))
-        masks7 = torch.zeros((N7, H7, W7), dtype=torch.uint8, device="cuda")
-        probs7 = torch.zeros((N7, 3, H7, W7), dtype=torch.float32, device="cuda")
-        with torch.cuda.stream(stream):
-            ms = time_device(lambda: m.mb_mask_extend(me.handle, d_em, d_mb, Z7, H7, W7, d_sd, 2, N7, masks7, probs7,
-                                                      stream=stream), 3, 1, stream, flush)
         # one step's class maps against the oracle on a 128x128 crop with its true context
         y0, x0 = 192, 160
         xp = oracle.maskextend_input(em7, mb7, {-2 + i: sd7[i] for i in range(4)}, 2, 54)
         ref = oracle.run_layers_mc(synth.MASKEXTEND, me_params, xp[:, y0:y0 + 128 + 108, x0:x0 + 128 + 108])
-        got = probs7[0, :, y0:y0 + 128, x0:x0 + 128].cpu().numpy()
         vox7 = N7 * H7 * W7
-        mv = vox7 / (statistics.mean(ms) / 1e3) / 1e6
-        paths["cfg7_maskextend_512x512x16steps"] = {
-            "mvox_s": mv, "ms": statistics.mean(ms), "steps_per_s": N7 / (statistics.mean(ms) / 1e3),
-            "tflops": MASKEXTEND_FLOP_PER_PX * mv * 1e6 / 1e12, "flop_per_px": MASKEXTEND_FLOP_PER_PX,
-            "mask_fraction": float(masks7.float().mean()),
-            "error_step0_crop128": {k: v for k, v in oracle.metrics(got, ref).items()}}
-        me.close()
+        p7, masks_by = {}, {}
+        for name, prec in (("fp32", m.MB_PREC_FP32), ("fp16_tcgen05", m.MB_PREC_FP16)):
+            me = m.Net(synth.MASKEXTEND, prec, local, me_params)
+            masks7 = torch.zeros((N7, H7, W7), dtype=torch.uint8, device="cuda")
+            probs7 = torch.zeros((N7, 3, H7, W7), dtype=torch.float32, device="cuda")
+            with torch.cuda.stream(stream):
+                ms = time_device(lambda: m.mb_mask_extend(me.handle, d_em, d_mb, Z7, H7, W7, d_sd, 2, N7, masks7,
+                                                          probs7, stream=stream), 3 if prec == m.MB_PREC_FP32 else 10,
+                                 1 if prec == m.MB_PREC_FP32 else 3, stream, flush)
+            got = probs7[0, :, y0:y0 + 128, x0:x0 + 128].cpu().numpy()
+            mv = vox7 / (statistics.mean(ms) / 1e3) / 1e6
+            masks_by[name] = masks7.cpu().numpy()
+            p7[name] = {
+                "mvox_s": mv, "ms": statistics.mean(ms), "steps_per_s": N7 / (statistics.mean(ms) / 1e3),
+                "tflops": MASKEXTEND_FLOP_PER_PX * mv * 1e6 / 1e12,
+                "mask_fraction": float(masks7.float().mean()),
+                "error_step0_crop128": {k: v for k, v in oracle.metrics(got, ref).items()}}
+            me.close()
+        p7["flop_per_px"] = MASKEXTEND_FLOP_PER_PX
+        p7["fp16_vs_fp32_mask_agreement_16_free_steps"] = float((masks_by["fp16_tcgen05"] == masks_by["fp32"]).mean())
+        paths["cfg7_maskextend_512x512x16steps"] = p7
     if paths:
         line["paths"] = paths
     if rank == 0 and not args.no_cpu_baseline:

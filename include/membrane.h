@@ -50,7 +50,7 @@ typedef enum {
     MB_ERR_UNSUPPORTED = 7  /* no kernel for this net / precision / option */
 } mb_status;
 
-typedef enum { MB_PREC_FP32 = 0, MB_PREC_BF16 = 1, MB_PREC_FP8 = 2 } mb_precision;
+typedef enum { MB_PREC_FP32 = 0, MB_PREC_BF16 = 1, MB_PREC_FP8 = 2, MB_PREC_FP16 = 3 } mb_precision;
 typedef enum { MB_OUT_F32 = 0, MB_OUT_U8 = 1 } mb_out_type;
 typedef enum {
     MB_CONV = 0,
@@ -85,7 +85,9 @@ typedef enum {
  * slices h, w >= 55), both in FP32 and BF16; and MaskExtend (Sec. 3.2: conv4x4 12->32 G=2 d=1,
  * maxfilter d=1, conv4x4 32->40 G=2 d=2, maxfilter d=2, conv4x4 40->48 G=2 d=4, maxfilter d=4,
  * conv4x4 48->56 G=2 d=8, maxfilter d=8, conv4x4 56->64 G=2 d=16, head 1x1 64->3 softmax; radius
- * 54) in FP32, run only through mb_mask_extend (the map calls return MB_ERR_UNSUPPORTED).
+ * 54) in FP32 (CUDA cores) and FP16 (tensor cores: FP16 operands, FP32 accumulation; MB_PREC_FP16
+ * is accepted for MaskExtend nets only), run only through mb_mask_extend (the map calls return
+ * MB_ERR_UNSUPPORTED).
  */
 typedef struct {
     int32_t kind, ksize, dilation, cin, cout, relu, maxout_groups;
@@ -273,8 +275,10 @@ int64_t mb_launch_count(void);
  *   seed_masks: uint8 [4][h][w] masks of z0-4 .. z0-1 (0 or 1)
  *   masks_out:  uint8 [n_steps][h][w] (0/1)        probs_out: float [n_steps][3][h][w] or NULL
  *               (classes: object, other neurons, membrane)
- * Needs 2 <= z0 and z0 + n_steps + 1 < z (else MB_ERR_SHAPE). FP32 MaskExtend nets only. Device
- * pointers; asynchronous on `stream`. The net's workspace is shared by its calls: calls on one
+ * Needs 2 <= z0 and z0 + n_steps + 1 < z (else MB_ERR_SHAPE). MaskExtend nets in FP32 or FP16 (an
+ * FP16 net rounds the 12 maps, its weights and every layer's features to FP16 and accumulates in
+ * FP32; a timed-out device-side wait returns MB_ERR_TIMEOUT). Device pointers; asynchronous on
+ * `stream`. The net's workspace is shared by its calls: calls on one
  * net must not overlap on the GPU.
  */
 mb_status mb_mask_extend(mb_net* net, const uint8_t* em, const float* membrane, int64_t z, int64_t h, int64_t w,

@@ -371,7 +371,7 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
         return MB_ERR_INVALID_ARG;
     }
     *out_net = nullptr;
-    if (prec != MB_PREC_FP32 && prec != MB_PREC_BF16 && prec != MB_PREC_FP8) {
+    if (prec != MB_PREC_FP32 && prec != MB_PREC_BF16 && prec != MB_PREC_FP8 && prec != MB_PREC_FP16) {
         set_error("mb_net_create: unknown precision %d", (int)prec);
         return MB_ERR_INVALID_ARG;
     }
@@ -393,8 +393,12 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
         set_error("mb_net_create: the student runs in FP32 or BF16");
         return MB_ERR_UNSUPPORTED;
     }
-    if (fam == FAMILY_MASKEXTEND && prec != MB_PREC_FP32) {
-        set_error("mb_net_create: MaskExtend runs in FP32");
+    if (fam == FAMILY_MASKEXTEND && prec != MB_PREC_FP32 && prec != MB_PREC_FP16) {
+        set_error("mb_net_create: MaskExtend runs in FP32 or FP16");
+        return MB_ERR_UNSUPPORTED;
+    }
+    if (fam != FAMILY_MASKEXTEND && prec == MB_PREC_FP16) {
+        set_error("mb_net_create: FP16 is MaskExtend's tensor-core precision only");
         return MB_ERR_UNSUPPORTED;
     }
     if (is_fastmemb(fam) && prec == MB_PREC_FP8) {
@@ -449,6 +453,7 @@ mb_status mb_net_destroy(mb_net* net) {
         cudaDeviceSynchronize();
         tc_release(net);
         fm_tc_release(net);
+        me_tc_release(net);
         dev_free(net->d_params);
         dev_free(net->d_simt);
         dev_free(net->d_queue);
@@ -509,6 +514,7 @@ mb_status mb_load_weights(mb_net* net, const float* params, int64_t n_params) {
     net->loaded = true;
     if (net->family == FAMILY_TEACHER && net->prec == MB_PREC_BF16) MB_TRY(tc_prepare(net));
     if (is_fastmemb(net->family) && net->prec == MB_PREC_BF16) MB_TRY(fm_tc_prepare(net));
+    if (net->family == FAMILY_MASKEXTEND && net->prec == MB_PREC_FP16) MB_TRY(me_tc_prepare(net));
     return MB_OK;
 }
 

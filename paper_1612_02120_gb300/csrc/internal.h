@@ -76,6 +76,7 @@ struct mb_net {
     size_t simt_floats = 0;
     void* tc_state = nullptr;    // tensor-core path state (packed operands, constants), tc_conv.cu
     void* fm_state = nullptr;    // FastMemb tensor-core state (packed operands, error word), fastmemb_tc.cu
+    void* me_state = nullptr;    // MaskExtend tensor-core state (packed operands, error word), maskextend_tc.cu
     float fp8_amax[2][32] = {};
     mb::Workspace ws;            // layered FP32 path activations
     mb::Workspace ws2;           // student training / cascade scratch
@@ -126,6 +127,16 @@ mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, 
                       int64_t out_pitch, int out_h, int out_w, int d, int nz, int out_u8, cudaStream_t st);
 // MaskExtend (maskextend.cu): SIMT weight layout, and the +z transfer recursion (device pointers).
 void me_pack(const mb_net* net, const float* params, std::vector<float>& out);
+// MaskExtend FP16 tensor-core convs (maskextend_tc.cu). layer 0..4; in: [src rows][in_pitch][cs] FP16;
+// the conv reads input (r, c) = 2x2 max (dilation dm) at source (r, c), r < in_rows, c < in_cols;
+// layers 0-3 write FP16 features [out_h][out_pitch][N/2]; layer 4 writes the 3 class probabilities
+// [3][out_h][out_pitch] (planes probs_plane apart).
+mb_status me_tc_prepare(mb_net* net);
+void me_tc_release(mb_net* net);
+mb_status me_tc_poll_error(mb_net* net);
+mb_status me_tc_layer(mb_net* net, int layer, const void* in, int64_t in_pitch, int cs, int in_rows, int in_cols,
+                      int dm, void* out, int64_t out_pitch, int out_h, int out_w, float* probs, int64_t probs_plane,
+                      cudaStream_t st);
 mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int64_t zt, int64_t h, int64_t w,
                          const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
                          float* probs_out, cudaStream_t st);

@@ -14,6 +14,7 @@
 // Domains for a section of h x w (walking back from the head: conv k's input needs 3 d_k + dm_k
 // more rows than its output): conv5 out h, conv4 out h+56, conv3 out h+84, conv2 out h+98,
 // conv1 out h+105, input h+108.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,9 +35,11 @@ struct MeMasks {
     const uint8_t* m[4];  // masks of sections z-4 .. z-1, [h][w]
 };
 
-// Mirror-padded input stack of section z: out[(r, c)][ch] for r < h + 108, c < w + 108.
+// Mirror-padded input stack of section z: out[(r, c)][ch] for r < h + 108, c < w + 108, FP32 or
+// (for the tensor-core path) FP16.
+template <typename T>
 __global__ void me_assemble(const uint8_t* __restrict__ em, const float* __restrict__ memb, MeMasks mk, int64_t z,
-                            int h, int w, float* __restrict__ out) {
+                            int h, int w, T* __restrict__ out) {
     const int pw = w + 2 * kMeR, ph = h + 2 * kMeR;
     const int64_t n = (int64_t)ph * pw;
     const int64_t hw = (int64_t)h * w;
@@ -53,9 +56,21 @@ __global__ void me_assemble(const uint8_t* __restrict__ em, const float* __restr
         for (int k = 0; k < 5; ++k) v[7 + k] = memb[(z - 2 + k) * hw + o];
 #pragma unroll
         for (int k = 12; k < 16; ++k) v[k] = 0.f;
-        float4* d = reinterpret_cast<float4*>(out + i * kMeCin);
+        if constexpr (sizeof(T) == 4) {
+            float4* d = reinterpret_cast<float4*>(out + i * kMeCin);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else {
+            uint32_t hw[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                __half2 h2 = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+                hw[k] = *reinterpret_cast<uint32_t*>(&h2);
+            }
+            uint4* d = reinterpret_cast<uint4*>(out + i * kMeCin);
+            d[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            d[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+        }
     }
 }
 
@@ -131,11 +146,64 @@ static int me_grid(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
 }
 
+// FP16 tensor-core form of the recursion: the same stack in FP16, the five convs on the tensor cores
+// (maskextend_tc.cu; the last one with the head and the softmax), then J.
+static mb_status maskextend_run_tc(mb_net* net, const uint8_t* em, const float* memb, int64_t h, int64_t w,
+                                   const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
+                                   float* probs_out, cudaStream_t st) {
+    MB_TRY(me_tc_poll_error(net));  // a wait that timed out in an earlier call on this net
+    const int64_t r[5] = {h + 105, h + 98, h + 84, h + 56, h}, c[5] = {w + 105, w + 98, w + 84, w + 56, w};
+    const int d[5] = {1, 2, 4, 8, 16}, dm[5] = {0, 1, 2, 4, 8};
+    const int64_t feat[5] = {32, 40, 48, 56, 64};
+    auto up = [](int64_t n) { return (n + 127) & ~(int64_t)127; };  // 256-byte aligned sub-buffers (FP16)
+    const int64_t n_in = up((h + 108) * (w + 108) * kMeCin);
+    int64_t n_act[4], total = n_in;
+    for (int k = 0; k < 4; ++k) {
+        n_act[k] = up(r[k] * c[k] * feat[k]);
+        total += n_act[k];
+    }
+    const int64_t n_prob = up(2 * 3 * h * w);  // FP32 probabilities, counted in FP16 units
+    total += n_prob;
+    MB_TRY(net->ws.ensure((size_t)total * sizeof(__half)));
+    __half* xin = static_cast<__half*>(net->ws.ptr);
+    __half* act[4];
+    act[0] = xin + n_in;
+    for (int k = 1; k < 4; ++k) act[k] = act[k - 1] + n_act[k - 1];
+    float* prob_tmp = reinterpret_cast<float*>(act[3] + n_act[3]);
+    const int64_t hw = h * w;
+    for (int64_t s = 0; s < n_steps; ++s) {
+        const int64_t z = z0 + s;
+        MeMasks mk;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t zz = z - 4 + k;
+            mk.m[k] = zz < z0 ? seeds + (zz - (z0 - 4)) * hw : masks_out + (zz - z0) * hw;
+        }
+        me_assemble<__half><<<me_grid((h + 108) * (w + 108)), 256, 0, st>>>(em, memb, mk, z, (int)h, (int)w, xin);
+        count_launch();
+        MB_CUDA(cudaGetLastError());
+        float* probs = probs_out ? probs_out + s * 3 * hw : prob_tmp;
+        for (int k = 0; k < 5; ++k) {
+            const void* in = k == 0 ? (const void*)xin : (const void*)act[k - 1];
+            const int64_t in_pitch = k == 0 ? w + 108 : c[k - 1];
+            const int cs = k == 0 ? kMeCin : (int)feat[k - 1];
+            MB_TRY(me_tc_layer(net, k, in, in_pitch, cs, (int)(r[k] + 3 * d[k]), (int)(c[k] + 3 * d[k]), dm[k],
+                               k < 4 ? (void*)act[k] : nullptr, k < 4 ? c[k] : w, (int)r[k], (int)c[k],
+                               k == 4 ? probs : nullptr, hw, st));
+        }
+        me_smooth_threshold<<<me_grid(hw), 256, 0, st>>>(probs, (int)h, (int)w, thr, masks_out + s * hw);
+        count_launch();
+        MB_CUDA(cudaGetLastError());
+    }
+    return me_tc_poll_error(net);
+}
+
 mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int64_t zt, int64_t h, int64_t w,
                          const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
                          float* probs_out, cudaStream_t st) {
     (void)zt;
     if (n_steps == 0) return MB_OK;
+    if (net->prec == MB_PREC_FP16)
+        return maskextend_run_tc(net, em, memb, h, w, seeds, z0, n_steps, thr, masks_out, probs_out, st);
     // geometry (dense): conv outputs and their input domains
     const int64_t r[5] = {h + 105, h + 98, h + 84, h + 56, h}, c[5] = {w + 105, w + 98, w + 84, w + 56, w};
     const int d[5] = {1, 2, 4, 8, 16}, dm[5] = {0, 1, 2, 4, 8};
@@ -177,7 +245,7 @@ mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int6
             const int64_t zz = z - 4 + k;
             mk.m[k] = zz < z0 ? seeds + (zz - (z0 - 4)) * hw : masks_out + (zz - z0) * hw;
         }
-        me_assemble<<<me_grid((h + 108) * (w + 108)), 256, 0, st>>>(em, memb, mk, z, (int)h, (int)w, xin);
+        me_assemble<float><<<me_grid((h + 108) * (w + 108)), 256, 0, st>>>(em, memb, mk, z, (int)h, (int)w, xin);
         count_launch();
         MB_CUDA(cudaGetLastError());
         for (int k = 0; k < 5; ++k) {

@@ -1,0 +1,629 @@
+// maskextend_tc.cu - MaskExtend's five max-out convolutions (Sec. 3.2) on the 5th-generation tensor
+// cores, FP16 operands and FP32 accumulation; the last one ends with the 1x1 64->3 head and the
+// 3-class softmax in its epilogue.
+//
+// Implicit GEMM per output row y and 128-pixel column strip x0 of a conv with dilation D:
+//   D[128 px][N] = sum over taps (ky, kx) and K chunks kc of  A[128 px][16 ch] x B[N][16 ch]^T
+// N = 2 x features (the max-out pairs, channels 2c and 2c+1 -> feature c), K = input channels
+// padded to a multiple of 16 (12 -> 16, 40 -> 48, 56 -> 64). A for tap (ky, kx) is staged input row
+// y + D ky at pixels x0 + D kx .. + 127: one staged row in the no-swizzle K-major layout
+// [8-channel chunk][pixel][16 B], the column tap a (D kx x 16)-byte shift of the descriptor.
+//
+// The weights of the deeper layers (up to 16 taps x 64 x 128 FP16 = 256 KB) do not fit in shared
+// memory beside the staged rows, so B is streamed per tap and reused over a group of 4 output rows
+// of one residue class y mod D (4 TMEM accumulators, 128 columns apart). A group's taps run
+// ky-major: step ky reads staged rows m + ky .. m + ky + 3, so the window of staged rows slides by
+// one row per step and one new row is staged per step. In step 0 the four rows are issued one after
+// the other (all four taps of ky = 0 resident), so an accumulator is only waited for when its row
+// starts while the epilogue drains the previous group's rows in the same order.
+//
+// Warp roles (512 threads, 1 CTA per SM, persistent over work items):
+//   warp 0       TMEM owner; lane 0 issues the MMAs
+//   warps 4-7    epilogue: TMEM -> registers, + bias, max-out, FP16 store (head: the 1x1 conv to 3
+//                classes and the softmax, FP32 probabilities)
+//   warps 8-11   A producers: the 2x2 max-filter (dilation dm) of the previous layer's output, or
+//                the assembled input stack, into the staged-row ring
+//   warps 12-15  B producers: tap tiles of the packed weights into the tap ring
+// Every mbarrier wait is bounded (a global-timer limit), after which the CTA records
+// MB_ERR_TIMEOUT in a mapped host word, stops issuing work and frees its TMEM.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace mb {
+
+namespace {
+
+constexpr int kMThreads = 512;
+constexpr int kMARing = 5;   // staged rows: 4 in use by a step + 1 being filled
+constexpr int kMBRing = 6;   // tap tiles: the 4 taps of a group's first step + 2 ahead
+constexpr int kMAcc = 4;     // accumulators = output rows per group
+constexpr uint64_t kMWaitNs = 4000000000ull;
+
+// Staged pixels per row: >= 128 + 3 D, and chosen so that the 8 threads of a quarter-warp, which
+// store consecutive (chunk, pixel) tasks, hit distinct 16-byte bank groups (pixel pitch of a chunk
+// plane = MP x 16 bytes).
+__host__ __device__ constexpr int me_mp(int chunks, int D) {
+    return chunks == 2 ? 132 : chunks == 4 ? 138 : D <= 4 ? 141 : D <= 8 ? 153 : 177;
+}
+
+template <int KC, int N, int D, bool HEAD>
+struct MCfg {
+    static constexpr int kChunks = 2 * KC;              // 8-channel chunks per staged pixel
+    static constexpr int kMP = me_mp(kChunks, D);
+    static constexpr int kNpix = 128 + 3 * D;            // staged pixels a row needs
+    static constexpr int kARow = kChunks * kMP * 16;     // bytes per staged row
+    static constexpr int kBTap = kChunks * N * 16;       // bytes per tap tile [chunk][N][16 B]
+    static constexpr int kConsts = N + (HEAD ? 3 * 64 + 3 : 0);  // biases (+ head W[3][64], b[3])
+    static constexpr int oA = 0;
+    static constexpr int oB = oA + kMARing * kARow;
+    static constexpr int oConst = oB + kMBRing * kBTap;
+    static constexpr int oBar = oConst + ((kConsts * 4 + 15) & ~15);
+    static constexpr int kBars = 2 * kMARing + 2 * kMBRing + 2 * kMAcc + 1;
+    static constexpr int oMisc = oBar + kBars * 8;
+    static constexpr int kSmem = oMisc + 16;
+    static constexpr int kATasks = (kNpix * kChunks + 127) / 128;
+    static constexpr int kBTasks = (kBTap / 16 + 127) / 128;
+    static_assert(kNpix <= kMP, "staged row too short");
+    static_assert(N % 16 == 0 && N <= 128, "MMA N");
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+struct MeTcParams {
+    const __half* in;       // source [src rows][in_pitch][cs] FP16
+    __half* out;            // layers: [out_h][out_pitch][N/2] FP16
+    float* probs;           // head: [3][out_h][out_pitch] FP32, planes probs_plane apart
+    const uint8_t* wpack;   // 16 tap tiles, then the FP32 constants
+    int* err;
+    int64_t in_pitch, out_pitch, probs_plane;  // pixels
+    int cs;                 // source channels (a multiple of 8, <= 16 KC)
+    int in_rows, in_cols;   // conv input domain: input (r, c) = 2x2 max (dilation dm) at source (r, c)
+    int out_h, out_w, dm;
+    int n_strips, n_chunks, rows_per_item, n_items;
+    int fault_stall;        // test injection: producers withhold their arrivals
+    uint64_t wait_ns;
+};
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                         uint64_t limit_ns) {
+    if (*abort_flag) return false;
+    if (ptx::mbar_test(bar, parity)) return true;
+    const uint64_t t0 = gtime();
+    uint32_t n = 0;
+    while (!ptx::mbar_test(bar, parity)) {
+        __nanosleep(32);
+        if ((++n & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (gtime() - t0 > limit_ns) {
+                *abort_flag = 1;
+                *(volatile int*)err = MB_ERR_TIMEOUT;
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+struct MeItem {
+    int ry, x0, m0, rows;  // output rows y = ry + D (m0 + j), j < rows; rows may be 0
+};
+
+template <int D>
+__device__ __forceinline__ MeItem me_item(const MeTcParams& p, int k) {
+    MeItem it;
+    const int chunk = k % p.n_chunks;
+    k /= p.n_chunks;
+    it.x0 = (k % p.n_strips) * 128;
+    it.ry = k / p.n_strips;
+    it.m0 = chunk * p.rows_per_item;
+    const int hr = (p.out_h - it.ry + D - 1) / D;  // rows of this residue class
+    it.rows = max(0, min(p.rows_per_item, hr - it.m0));
+    return it;
+}
+
+__device__ __forceinline__ uint4 hmax4(uint4 a, uint4 b) {
+    uint4 r;
+    const __half2* x = reinterpret_cast<const __half2*>(&a);
+    const __half2* y = reinterpret_cast<const __half2*>(&b);
+    __half2* o = reinterpret_cast<__half2*>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = __hmax2(x[i], y[i]);
+    return r;
+}
+
+template <int KC, int N, int D, bool HEAD>
+__global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant__ MeTcParams p) {
+    using C = MCfg<KC, N, D, HEAD>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* a_full = reinterpret_cast<uint64_t*>(smem + C::oBar);
+    uint64_t* a_empty = a_full + kMARing;
+    uint64_t* b_full = a_empty + kMARing;
+    uint64_t* b_empty = b_full + kMBRing;
+    uint64_t* acc_full = b_empty + kMBRing;
+    uint64_t* acc_free = acc_full + kMAcc;
+    uint64_t* fin = acc_free + kMAcc;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::oMisc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::oMisc + 4);
+    const float* cst = reinterpret_cast<const float*>(smem + C::oConst);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < kMARing; ++i) {
+            ptx::mbar_init(&a_full[i], 128);
+            ptx::mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < kMBRing; ++i) {
+            ptx::mbar_init(&b_full[i], 128);
+            ptx::mbar_init(&b_empty[i], 1);
+        }
+        for (int i = 0; i < kMAcc; ++i) {
+            ptx::mbar_init(&acc_full[i], 1);
+            ptx::mbar_init(&acc_free[i], 128);
+        }
+        ptx::mbar_init(fin, 1);
+        *abort_flag = 0;
+        ptx::mbar_fence_init();
+    }
+    {
+        const float* src = reinterpret_cast<const float*>(p.wpack + 16 * C::kBTap);
+        float* dst = reinterpret_cast<float*>(smem + C::oConst);
+        for (int i = tid; i < C::kConsts; i += kMThreads) dst[i] = __ldg(src + i);
+    }
+    if (warp == 0) {
+        ptx::tmem_alloc(tmem_slot, 512);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const uint32_t sbase = ptx::smem_u32(smem);
+
+    if (warp == 0) {
+        // ================= MMA issuer ================================================================
+        if (lane == 0) {
+            const uint64_t adesc0 = ptx::smem_desc(sbase + C::oA, C::kMP * 16, 128);
+            const uint64_t bdesc0 = ptx::smem_desc(sbase + C::oB, N * 16, 128);
+            constexpr uint32_t idesc = ptx::idesc_f32acc(ptx::kFmtF16, 128, N);
+            uint32_t a_seq = 0, b_seq = 0, acc_seq = 0;
+            bool ok = true;
+            // output row j of the group, staged row s + j, tap kx, tap tile of sequence number bq
+            auto issue = [&](int j, int s, int kx, uint32_t bq, bool first) {
+                const uint32_t dcol = tbase + 128u * ((acc_seq + j) % kMAcc);
+                const uint32_t aslot = (a_seq + s + j) % kMARing;
+                const uint64_t ad = adesc0 + (uint64_t)((aslot * C::kARow + D * kx * 16) >> 4);
+                const uint64_t bd = bdesc0 + (uint64_t)(((bq % kMBRing) * C::kBTap) >> 4);
+#pragma unroll
+                for (int kc = 0; kc < KC; ++kc)
+                    ptx::mma_bf16(dcol, ad + (uint64_t)((kc * 2 * C::kMP * 16) >> 4),
+                                  bd + (uint64_t)((kc * 2 * N * 16) >> 4), idesc, (first && kc == 0) ? 0u : 1u);
+            };
+            for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+                const MeItem it = me_item<D>(p, k);
+                if (it.rows == 0) continue;
+                const int groups = (it.rows + kMAcc - 1) / kMAcc;
+                int a_known = 0;  // staged rows [0, a_known) of the item are known full
+                for (int g = 0; g < groups; ++g) {
+                    const int rg = min(kMAcc, it.rows - kMAcc * g);
+                    for (int ky = 0; ky < 4; ++ky) {
+                        const int s = kMAcc * g + ky;  // staged rows s .. s + rg - 1
+                        for (; a_known < s + rg; ++a_known) {
+                            const uint32_t q = a_seq + a_known;
+                            ok = ok && wait_bar(&a_full[q % kMARing], (q / kMARing) & 1, abort_flag, p.err, p.wait_ns);
+                        }
+                        if (ky == 0) {
+                            for (int j = 0; j < rg; ++j) {
+                                const uint32_t qa = acc_seq + j;
+                                ok = ok && wait_bar(&acc_free[qa % kMAcc], ((qa / kMAcc) & 1) ^ 1, abort_flag, p.err,
+                                                    p.wait_ns);
+                                for (int kx = 0; kx < 4; ++kx) {
+                                    if (j == 0) {
+                                        const uint32_t bq = b_seq + kx;
+                                        ok = ok && wait_bar(&b_full[bq % kMBRing], (bq / kMBRing) & 1, abort_flag,
+                                                            p.err, p.wait_ns);
+                                    }
+                                    ptx::tc_fence_after();
+                                    if (ok) issue(j, s, kx, b_seq + kx, kx == 0);
+                                }
+                            }
+                            for (int kx = 0; kx < 4; ++kx) ptx::mma_commit(&b_empty[(b_seq + kx) % kMBRing]);
+                            b_seq += 4;
+                        } else {
+                            for (int kx = 0; kx < 4; ++kx) {
+                                ok = ok && wait_bar(&b_full[b_seq % kMBRing], (b_seq / kMBRing) & 1, abort_flag, p.err,
+                                                    p.wait_ns);
+                                ptx::tc_fence_after();
+                                if (ok)
+                                    for (int j = 0; j < rg; ++j) issue(j, s, kx, b_seq, false);
+                                ptx::mma_commit(&b_empty[b_seq % kMBRing]);
+                                ++b_seq;
+                            }
+                        }
+                        // staged row s is not read by any later step
+                        ptx::mma_commit(&a_empty[(a_seq + s) % kMARing]);
+                    }
+                    for (int j = 0; j < rg; ++j) ptx::mma_commit(&acc_full[(acc_seq + j) % kMAcc]);
+                    acc_seq += rg;
+                }
+                // staged rows after the last step's first row (the item stages rows + 3)
+                for (int u = kMAcc * groups; u < it.rows + 3; ++u) ptx::mma_commit(&a_empty[(a_seq + u) % kMARing]);
+                a_seq += it.rows + 3;
+            }
+            ptx::mma_commit(fin);
+            const uint64_t t0 = gtime();
+            while (!ptx::mbar_test(fin, 0)) {
+                if (gtime() - t0 > p.wait_ns) {
+                    *(volatile int*)p.err = MB_ERR_TIMEOUT;
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4 && warp < 8) {
+        // ================= epilogue ===================================================================
+        const int px = tid - 128;  // TMEM lane = pixel of the strip
+        const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
+        uint32_t acc_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const MeItem it = me_item<D>(p, k);
+            const int x = it.x0 + px;
+            for (int j = 0; j < it.rows; ++j) {
+                const uint32_t qa = acc_seq + j, s = qa % kMAcc;
+                wait_bar(&acc_full[s], (qa / kMAcc) & 1, abort_flag, p.err, p.wait_ns);
+                ptx::tc_fence_after();
+                const uint32_t ta = tbase + lanes + 128u * s;
+                const int y = it.ry + D * (it.m0 + j);
+                const bool store = x < p.out_w && y < p.out_h && !*abort_flag;
+                if constexpr (HEAD) {
+                    // features c = 0..63 -> logits z_k = b_k + sum_c W[k][c] f_c, in order of c
+                    const float* hw = cst + N;
+                    float z0 = hw[192], z1 = hw[193], z2 = hw[194];
+#pragma unroll
+                    for (int q = 0; q < N / 32; ++q) {
+                        float v[32];
+                        ptx::tmem_ld32(ta + 32u * q, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int c = 16 * q + i;
+                            const float f = fmaxf(v[2 * i] + cst[2 * c], v[2 * i + 1] + cst[2 * c + 1]);
+                            z0 = fmaf(hw[c], f, z0);
+                            z1 = fmaf(hw[64 + c], f, z1);
+                            z2 = fmaf(hw[128 + c], f, z2);
+                        }
+                    }
+                    ptx::tc_fence_before();
+                    ptx::mbar_arrive(&acc_free[s]);
+                    const float m = fmaxf(z0, fmaxf(z1, z2));
+                    const float e0 = expf(z0 - m), e1 = expf(z1 - m), e2 = expf(z2 - m);
+                    const float den = e0 + e1 + e2;
+                    if (store) {
+                        float* o = p.probs + (int64_t)y * p.out_pitch + x;
+                        o[0] = e0 / den;
+                        o[p.probs_plane] = e1 / den;
+                        o[2 * p.probs_plane] = e2 / den;
+                    }
+                } else {
+                    // conv channels 2c, 2c+1 -> feature c; N/2 FP16 features = N/16 16-byte words
+                    uint32_t w[N / 4];
+#pragma unroll
+                    for (int q = 0; q < N / 32; ++q) {
+                        float v[32];
+                        ptx::tmem_ld32(ta + 32u * q, v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int n = 32 * q + 4 * i;
+                            const float f0 = fmaxf(v[4 * i] + cst[n], v[4 * i + 1] + cst[n + 1]);
+                            const float f1 = fmaxf(v[4 * i + 2] + cst[n + 2], v[4 * i + 3] + cst[n + 3]);
+                            __half2 h2 = __floats2half2_rn(f0, f1);
+                            w[8 * q + i] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                    }
+                    if constexpr (N % 32 != 0) {
+                        constexpr int q = N / 32;
+                        float v[16];
+                        ptx::tmem_ld16(ta + 32u * q, v);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int n = 32 * q + 4 * i;
+                            const float f0 = fmaxf(v[4 * i] + cst[n], v[4 * i + 1] + cst[n + 1]);
+                            const float f1 = fmaxf(v[4 * i + 2] + cst[n + 2], v[4 * i + 3] + cst[n + 3]);
+                            __half2 h2 = __floats2half2_rn(f0, f1);
+                            w[8 * q + i] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                    }
+                    ptx::tc_fence_before();
+                    ptx::mbar_arrive(&acc_free[s]);
+                    if (store) {
+                        uint4* o = reinterpret_cast<uint4*>(p.out + ((int64_t)y * p.out_pitch + x) * (N / 2));
+#pragma unroll
+                        for (int i = 0; i < N / 16; ++i) o[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+                    }
+                }
+            }
+            acc_seq += it.rows;
+        }
+    } else if (warp >= 8 && warp < 12) {
+        // ================= A producers: staged input rows ===========================================
+        // Task e = pt + 128 i: chunk e % kChunks of staged pixel e / kChunks (consecutive threads
+        // read consecutive 16-byte chunks of one source pixel). All loads of a row are issued
+        // before the slot wait so their latency overlaps it.
+        const int pt = tid - 256;
+        const int64_t dxo = (int64_t)p.dm * p.cs, dyo = (int64_t)p.dm * p.in_pitch * p.cs;
+        const int src_chunks = p.cs / 8;
+        uint32_t a_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const MeItem it = me_item<D>(p, k);
+            if (it.rows == 0) continue;
+            for (int u = 0; u < it.rows + 3; ++u) {
+                const uint32_t q = a_seq + u, slot = q % kMARing;
+                const int yin = it.ry + D * (it.m0 + u);
+                uint4 v[C::kATasks];
+#pragma unroll
+                for (int i = 0; i < C::kATasks; ++i) {
+                    const int e = pt + 128 * i;
+                    const int c = e % C::kChunks, xin = it.x0 + e / C::kChunks;
+                    v[i] = make_uint4(0, 0, 0, 0);
+                    if (e < C::kNpix * C::kChunks && c < src_chunks && yin < p.in_rows && xin < p.in_cols) {
+                        const __half* a = p.in + ((int64_t)yin * p.in_pitch + xin) * p.cs + c * 8;
+                        const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a));
+                        if (p.dm > 0) {
+                            const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a + dxo));
+                            const uint4 r2 = __ldg(reinterpret_cast<const uint4*>(a + dyo));
+                            const uint4 r3 = __ldg(reinterpret_cast<const uint4*>(a + dyo + dxo));
+                            v[i] = hmax4(hmax4(r0, r1), hmax4(r2, r3));
+                        } else {
+                            v[i] = r0;
+                        }
+                    }
+                }
+                wait_bar(&a_empty[slot], ((q / kMARing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                uint8_t* dst = smem + C::oA + slot * C::kARow;
+#pragma unroll
+                for (int i = 0; i < C::kATasks; ++i) {
+                    const int e = pt + 128 * i;
+                    if (e < C::kNpix * C::kChunks)
+                        *reinterpret_cast<uint4*>(dst + ((e % C::kChunks) * C::kMP + e / C::kChunks) * 16) = v[i];
+                }
+                ptx::fence_proxy_async_smem();
+                if (!p.fault_stall) ptx::mbar_arrive(&a_full[slot]);
+            }
+            a_seq += it.rows + 3;
+        }
+    } else if (warp >= 12) {
+        // ================= B producers: tap tiles, in the issuer's order ============================
+        const int pb = tid - 384;
+        uint32_t b_seq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const MeItem it = me_item<D>(p, k);
+            if (it.rows == 0) continue;
+            const int groups = (it.rows + kMAcc - 1) / kMAcc;
+            for (int g = 0; g < groups; ++g)
+                for (int t = 0; t < 16; ++t, ++b_seq) {
+                    const uint32_t slot = b_seq % kMBRing;
+                    const uint4* src = reinterpret_cast<const uint4*>(p.wpack + (size_t)t * C::kBTap);
+                    uint4 v[C::kBTasks];
+#pragma unroll
+                    for (int i = 0; i < C::kBTasks; ++i) {
+                        const int e = pb + 128 * i;
+                        v[i] = e < C::kBTap / 16 ? __ldg(src + e) : make_uint4(0, 0, 0, 0);
+                    }
+                    wait_bar(&b_empty[slot], ((b_seq / kMBRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                    uint4* dst = reinterpret_cast<uint4*>(smem + C::oB + slot * C::kBTap);
+#pragma unroll
+                    for (int i = 0; i < C::kBTasks; ++i) {
+                        const int e = pb + 128 * i;
+                        if (e < C::kBTap / 16) dst[e] = v[i];
+                    }
+                    ptx::fence_proxy_async_smem();
+                    if (!p.fault_stall) ptx::mbar_arrive(&b_full[slot]);
+                }
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 0) ptx::tmem_dealloc(tbase, 512);
+}
+
+uint16_t f16_bits(float f) {
+    const __half h = __float2half_rn(f);
+    uint16_t b;
+    memcpy(&b, &h, 2);
+    return b;
+}
+
+// Pack conv layer W[n][cin][4][4], b[n] (n < N conv channels) as 16 tap tiles: tile t = 4 ky + kx is
+// [chunk kc][row n][8 FP16], input channel 8 kc + e (zero beyond cin); then the N FP32 biases and,
+// for the last layer, the head W[3][64] and b[3].
+void me_tc_pack(const float* W, const float* b, int cin, int n, int kc, const float* head, std::vector<uint8_t>& out) {
+    const int chunks = 2 * kc, tap = chunks * n * 16;
+    const size_t consts = (size_t)n + (head ? 3 * 64 + 3 : 0);
+    out.assign((size_t)16 * tap + consts * 4, 0);
+    for (int o = 0; o < n; ++o)
+        for (int ci = 0; ci < cin; ++ci)
+            for (int t = 0; t < 16; ++t) {
+                const uint16_t h = f16_bits(W[((size_t)o * cin + ci) * 16 + t]);
+                memcpy(out.data() + (size_t)t * tap + ((size_t)(ci / 8) * n + o) * 16 + (ci % 8) * 2, &h, 2);
+            }
+    float* c = reinterpret_cast<float*>(out.data() + (size_t)16 * tap);
+    for (int o = 0; o < n; ++o) c[o] = b[o];
+    if (head)
+        for (int i = 0; i < 3 * 64 + 3; ++i) c[n + i] = head[i];
+}
+
+template <int KC, int N, int D, bool HEAD>
+mb_status launch_me_tc(const MeTcParams& p, cudaStream_t st) {
+    using C = MCfg<KC, N, D, HEAD>;
+    static int n_sms = 0;
+    if (n_sms == 0) {
+        int dev = 0;
+        MB_CUDA(cudaGetDevice(&dev));
+        MB_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    static bool attr = false;
+    if (!attr) {
+        MB_CUDA(cudaFuncSetAttribute(me_tc_conv<KC, N, D, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     C::kSmem));
+        attr = true;
+    }
+    const int grid = std::max(1, std::min(p.n_items, n_sms));
+    me_tc_conv<KC, N, D, HEAD><<<grid, kMThreads, C::kSmem, st>>>(p);
+    count_launch();
+    MB_CUDA(cudaGetLastError());
+    return MB_OK;
+}
+
+// Layer table: input channels, K chunks of 16, N (= 2 x features), dilation.
+constexpr int kMeCin[5] = {12, 32, 40, 48, 56};
+constexpr int kMeKc[5] = {1, 2, 3, 3, 4};
+constexpr int kMeN[5] = {64, 80, 96, 112, 128};
+
+struct MeTcState {
+    uint8_t* d_wpack[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int* h_err = nullptr;
+    int* d_err = nullptr;
+    int n_sms = 0;
+};
+
+}  // namespace
+
+mb_status me_tc_prepare(mb_net* net) {
+    MeTcState* S = reinterpret_cast<MeTcState*>(net->me_state);
+    if (!S) {
+        S = new (std::nothrow) MeTcState();
+        if (!S) {
+            set_error("host allocation failed");
+            return MB_ERR_OOM;
+        }
+        net->me_state = S;
+    }
+    // API layout: per conv W [N][cin][4][4], b [N]; then the head W [3][64], b [3]
+    const float* P = net->host_params.data();
+    const float* head = P;
+    for (int l = 0; l < 5; ++l) head += (size_t)kMeN[l] * kMeCin[l] * 16 + kMeN[l];
+    std::vector<uint8_t> pk;
+    for (int l = 0; l < 5; ++l) {
+        const size_t nw = (size_t)kMeN[l] * kMeCin[l] * 16;
+        me_tc_pack(P, P + nw, kMeCin[l], kMeN[l], kMeKc[l], l == 4 ? head : nullptr, pk);
+        P += nw + kMeN[l];
+        if (!S->d_wpack[l]) MB_TRY(dev_alloc((void**)&S->d_wpack[l], pk.size()));
+        MB_CUDA(cudaMemcpy(S->d_wpack[l], pk.data(), pk.size(), cudaMemcpyHostToDevice));
+    }
+    if (!S->h_err) {
+        if (fault_oom()) {
+            set_error("pinned allocation failed (MB_FAULT_OOM injected)");
+            return MB_ERR_OOM;
+        }
+        MB_CUDA(cudaHostAlloc((void**)&S->h_err, sizeof(int), cudaHostAllocMapped));
+        *S->h_err = 0;
+        MB_CUDA(cudaHostGetDevicePointer((void**)&S->d_err, S->h_err, 0));
+    }
+    if (!S->n_sms) {
+        int dev = 0;
+        MB_CUDA(cudaGetDevice(&dev));
+        MB_CUDA(cudaDeviceGetAttribute(&S->n_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return MB_OK;
+}
+
+void me_tc_release(mb_net* net) {
+    MeTcState* S = reinterpret_cast<MeTcState*>(net->me_state);
+    if (!S) return;
+    for (uint8_t* w : S->d_wpack) dev_free(w);
+    if (S->h_err) cudaFreeHost(S->h_err);
+    delete S;
+    net->me_state = nullptr;
+}
+
+mb_status me_tc_poll_error(mb_net* net) {
+    MeTcState* S = reinterpret_cast<MeTcState*>(net->me_state);
+    if (S && S->h_err && *(volatile int*)S->h_err) {
+        *(volatile int*)S->h_err = 0;
+        set_error("a MaskExtend tensor-core launch gave up waiting (device-side wait limit)");
+        return MB_ERR_TIMEOUT;
+    }
+    return MB_OK;
+}
+
+// Rows per work item: the cost of a launch is taken as waves x (rows + 5) staged-row steps (3 rows
+// of context and ~2 of pipeline fill per item); the smallest cost wins, ties to more rows.
+static int me_rows_per_item(int d, int strips, int out_h, int n_sms) {
+    const int hr = (out_h + d - 1) / d;
+    int best = 4, best_cost = 0x7fffffff;
+    for (int r = 4; r < hr + 4; r += 4) {
+        const int64_t items = (int64_t)d * strips * ((hr + r - 1) / r);
+        const int64_t cost = ((items + n_sms - 1) / n_sms) * (r + 5);
+        if (cost <= best_cost) {
+            best_cost = (int)std::min<int64_t>(cost, 0x7fffffff);
+            best = r;
+        }
+    }
+    return best;
+}
+
+mb_status me_tc_layer(mb_net* net, int layer, const void* in, int64_t in_pitch, int cs, int in_rows, int in_cols,
+                      int dm, void* out, int64_t out_pitch, int out_h, int out_w, float* probs, int64_t probs_plane,
+                      cudaStream_t st) {
+    MeTcState* S = reinterpret_cast<MeTcState*>(net->me_state);
+    if (!S || !S->d_wpack[layer]) {
+        set_error("MaskExtend tensor-core weights not prepared");
+        return MB_ERR_NOT_READY;
+    }
+    static const int kD[5] = {1, 2, 4, 8, 16};
+    const int d = kD[layer];
+    if (cs % 8 != 0 || cs > 16 * kMeKc[layer] || in_rows < out_h + 3 * d || in_cols < out_w + 3 * d) {
+        set_error("MaskExtend: inconsistent layer geometry");
+        return MB_ERR_INVALID_ARG;
+    }
+    MeTcParams p{};
+    p.in = static_cast<const __half*>(in);
+    p.out = static_cast<__half*>(out);
+    p.probs = probs;
+    p.wpack = S->d_wpack[layer];
+    p.err = S->d_err;
+    p.in_pitch = in_pitch;
+    p.out_pitch = out_pitch;
+    p.probs_plane = probs_plane;
+    p.cs = cs;
+    p.in_rows = in_rows;
+    p.in_cols = in_cols;
+    p.out_h = out_h;
+    p.out_w = out_w;
+    p.dm = dm;
+    p.n_strips = (out_w + 127) / 128;
+    p.rows_per_item = me_rows_per_item(d, p.n_strips, out_h, S->n_sms);
+    const int hr = (out_h + d - 1) / d;
+    p.n_chunks = (hr + p.rows_per_item - 1) / p.rows_per_item;
+    const int64_t items = (int64_t)d * p.n_strips * p.n_chunks;
+    if (items > 0x7fffffffLL) {
+        set_error("MaskExtend: too many work items for one launch");
+        return MB_ERR_SHAPE;
+    }
+    p.n_items = (int)items;
+    const char* stall = getenv("MB_FAULT_STALL");
+    p.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
+    p.wait_ns = p.fault_stall ? 200000000ull : kMWaitNs;
+    switch (layer) {
+        case 0: return launch_me_tc<1, 64, 1, false>(p, st);
+        case 1: return launch_me_tc<2, 80, 2, false>(p, st);
+        case 2: return launch_me_tc<3, 96, 4, false>(p, st);
+        case 3: return launch_me_tc<3, 112, 8, false>(p, st);
+        default: return launch_me_tc<4, 128, 16, true>(p, st);
+    }
+}
+
+}  // namespace mb

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libmembrane.so")
 
 MB_OK, MB_ERR_INVALID_ARG, MB_ERR_SHAPE, MB_ERR_OOM, MB_ERR_CUDA, MB_ERR_TIMEOUT, MB_ERR_NOT_READY, \
     MB_ERR_UNSUPPORTED = range(8)
-MB_PREC_FP32, MB_PREC_BF16, MB_PREC_FP8 = 0, 1, 2
+MB_PREC_FP32, MB_PREC_BF16, MB_PREC_FP8, MB_PREC_FP16 = 0, 1, 2, 3
 MB_OUT_F32, MB_OUT_U8 = 0, 1
 MB_CONV, MB_MAXFILTER, MB_HEAD_SIGMOID, MB_HEAD_SOFTMAX2, MB_HEAD_SOFTMAX = 0, 1, 2, 3, 4
 

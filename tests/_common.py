@@ -9,6 +9,8 @@ TOL = {
     "fp32": {"max_abs": 1e-5, "agreement": 0.995},
     "bf16": {"max_abs": 3e-2, "mean_abs": 2e-3, "agreement": 0.995},
     "fp8": {"max_abs": 1e-1, "mean_abs": 1e-2, "agreement": 0.995},
+    # MaskExtend on the tensor cores (FP16 operands): held to the 16-bit (BF16) bar
+    "fp16": {"max_abs": 3e-2, "mean_abs": 2e-3},
     "student": {"mean_abs": 3e-2, "agreement": 0.995},
 }
 
