@@ -19,13 +19,16 @@
 //
 // Warp roles (512 threads, 1 CTA per SM, persistent over work items):
 //   warp 0       TMEM owner; lane 0 issues the MMAs
+//   warp 1       lane 0 streams the tap tiles of the packed weights into the tap ring with bulk
+//                asynchronous copies (completion counted on the slot's mbarrier)
 //   warps 4-7    epilogue: TMEM -> registers, + bias, max-out, FP16 store (head: the 1x1 conv to 3
 //                classes and the softmax, FP32 probabilities)
-//   warps 8-11   A producers: the 2x2 max-filter (dilation dm) of the previous layer's output, or
-//                the assembled input stack, into the staged-row ring
-//   warps 12-15  B producers: tap tiles of the packed weights into the tap ring
+//   warps 8-15   A producers, two groups of 4 warps taking alternate staged rows: the 2x2
+//                max-filter (dilation dm) of the previous layer's output, or the assembled input
+//                stack, into the staged-row ring
 // Every mbarrier wait is bounded (a global-timer limit), after which the CTA records
-// MB_ERR_TIMEOUT in a mapped host word, stops issuing work and frees its TMEM.
+// MB_ERR_TIMEOUT in a mapped host word, stops issuing work, waits (bounded) for its bulk copies in
+// flight and frees its TMEM.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -70,7 +73,6 @@ struct MCfg {
     static constexpr int oMisc = oBar + kBars * 8;
     static constexpr int kSmem = oMisc + 16;
     static constexpr int kATasks = (kNpix * kChunks + 127) / 128;
-    static constexpr int kBTasks = (kBTap / 16 + 127) / 128;
     static_assert(kNpix <= kMP, "staged row too short");
     static_assert(N % 16 == 0 && N <= 128, "MMA N");
     static_assert(kSmem <= 227 * 1024, "shared memory");
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
             ptx::mbar_init(&a_empty[i], 1);
         }
         for (int i = 0; i < kMBRing; ++i) {
-            ptx::mbar_init(&b_full[i], 128);
+            ptx::mbar_init(&b_full[i], 1);
             ptx::mbar_init(&b_empty[i], 1);
         }
         for (int i = 0; i < kMAcc; ++i) {
@@ -355,19 +357,53 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
             }
             acc_seq += it.rows;
         }
-    } else if (warp >= 8 && warp < 12) {
+    } else if (warp == 1) {
+        // ================= B producer: tap tiles, in the issuer's order =============================
+        if (lane == 0) {
+            uint32_t issued = 0;
+            bool go = true;
+            for (int k = blockIdx.x; go && k < p.n_items; k += gridDim.x) {
+                const MeItem it = me_item<D>(p, k);
+                if (it.rows == 0) continue;
+                const int groups = (it.rows + kMAcc - 1) / kMAcc;
+                for (int g = 0; go && g < groups; ++g)
+                    for (int t = 0; go && t < 16; ++t) {
+                        const uint32_t slot = issued % kMBRing;
+                        go = wait_bar(&b_empty[slot], ((issued / kMBRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                        if (go && !p.fault_stall) {
+                            ptx::mbar_arrive_expect_tx(&b_full[slot], C::kBTap);
+                            ptx::bulk_copy_g2s(smem + C::oB + slot * C::kBTap, p.wpack + (size_t)t * C::kBTap,
+                                               C::kBTap, &b_full[slot]);
+                            ++issued;
+                        }
+                    }
+            }
+            // the copies still in flight land before the CTA exits (bounded, abort or not)
+            for (uint32_t q = issued > (uint32_t)kMBRing ? issued - kMBRing : 0; q < issued; ++q) {
+                const uint64_t t0 = gtime();
+                while (!ptx::mbar_test(&b_full[q % kMBRing], (q / kMBRing) & 1))
+                    if (gtime() - t0 > p.wait_ns) {
+                        *(volatile int*)p.err = MB_ERR_TIMEOUT;
+                        break;
+                    }
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 8) {
         // ================= A producers: staged input rows ===========================================
-        // Task e = pt + 128 i: chunk e % kChunks of staged pixel e / kChunks (consecutive threads
-        // read consecutive 16-byte chunks of one source pixel). All loads of a row are issued
-        // before the slot wait so their latency overlaps it.
-        const int pt = tid - 256;
+        // Group grp = warps 8-11 / 12-15 stages the rows u = grp mod 2 of every item. Task
+        // e = pt + 128 i: chunk e % kChunks of staged pixel e / kChunks (consecutive threads read
+        // consecutive 16-byte chunks of one source pixel). All loads of a row are issued before the
+        // slot wait so their latency overlaps it.
+        const int grp = (warp - 8) >> 2;
+        const int pt = tid - 256 - 128 * grp;
         const int64_t dxo = (int64_t)p.dm * p.cs, dyo = (int64_t)p.dm * p.in_pitch * p.cs;
         const int src_chunks = p.cs / 8;
         uint32_t a_seq = 0;
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const MeItem it = me_item<D>(p, k);
             if (it.rows == 0) continue;
-            for (int u = 0; u < it.rows + 3; ++u) {
+            for (int u = grp; u < it.rows + 3; u += 2) {
                 const uint32_t q = a_seq + u, slot = q % kMARing;
                 const int yin = it.ry + D * (it.m0 + u);
                 uint4 v[C::kATasks];
@@ -401,35 +437,6 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
                 if (!p.fault_stall) ptx::mbar_arrive(&a_full[slot]);
             }
             a_seq += it.rows + 3;
-        }
-    } else if (warp >= 12) {
-        // ================= B producers: tap tiles, in the issuer's order ============================
-        const int pb = tid - 384;
-        uint32_t b_seq = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const MeItem it = me_item<D>(p, k);
-            if (it.rows == 0) continue;
-            const int groups = (it.rows + kMAcc - 1) / kMAcc;
-            for (int g = 0; g < groups; ++g)
-                for (int t = 0; t < 16; ++t, ++b_seq) {
-                    const uint32_t slot = b_seq % kMBRing;
-                    const uint4* src = reinterpret_cast<const uint4*>(p.wpack + (size_t)t * C::kBTap);
-                    uint4 v[C::kBTasks];
-#pragma unroll
-                    for (int i = 0; i < C::kBTasks; ++i) {
-                        const int e = pb + 128 * i;
-                        v[i] = e < C::kBTap / 16 ? __ldg(src + e) : make_uint4(0, 0, 0, 0);
-                    }
-                    wait_bar(&b_empty[slot], ((b_seq / kMBRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                    uint4* dst = reinterpret_cast<uint4*>(smem + C::oB + slot * C::kBTap);
-#pragma unroll
-                    for (int i = 0; i < C::kBTasks; ++i) {
-                        const int e = pb + 128 * i;
-                        if (e < C::kBTap / 16) dst[e] = v[i];
-                    }
-                    ptx::fence_proxy_async_smem();
-                    if (!p.fault_stall) ptx::mbar_arrive(&b_full[slot]);
-                }
         }
     }
 

@@ -3,6 +3,8 @@ volume (the generator of `synth`), so a capture of one kernel stays a few hundre
 
     python -m paper_1612_02120_gb300.profile_case --prec bf16 --z 4 --h 1024 --w 1024 --reps 3
     python -m paper_1612_02120_gb300.profile_case --net fastmemb --prec bf16 --z 4 --reps 3
+    python -m paper_1612_02120_gb300.profile_case --net maskextend --prec fp16 --z 4 --h 512 --w 512
+      (MaskExtend: `z` transfer steps on an h x w window per rep)
 """
 import argparse
 import os
@@ -15,8 +17,8 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--net", default="teacher", choices=["teacher", "fastmemb"])
-    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp8", "student"])
+    ap.add_argument("--net", default="teacher", choices=["teacher", "fastmemb", "maskextend"])
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp8", "fp16", "student"])
     ap.add_argument("--z", type=int, default=4)
     ap.add_argument("--h", type=int, default=1024)
     ap.add_argument("--w", type=int, default=1024)
@@ -27,6 +29,19 @@ def main():
     import synth
     from paper_1612_02120_gb300 import build, membrane as m
     build.build()
+    if a.net == "maskextend":
+        em = synth.em_volume(synth.BASE_SEED + 7, a.z + 4, a.h, a.w)
+        d = [torch.from_numpy(arr).cuda() for arr in
+             (em, synth.membrane_maps(em), synth.disk_masks(4, a.h, a.w, a.h / 2, a.w / 2, a.h / 5, 2.0, -1.0))]
+        prec = {"fp32": m.MB_PREC_FP32, "fp16": m.MB_PREC_FP16}[a.prec]
+        net = m.Net(synth.MASKEXTEND, prec, 0, synth.init_params(synth.MASKEXTEND, synth.MASKEXTEND_WEIGHT_SEED))
+        masks = torch.zeros((a.z, a.h, a.w), dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            m.mb_mask_extend(net.handle, d[0], d[1], a.z + 4, a.h, a.w, d[2], 2, a.z, masks, None)
+        torch.cuda.synchronize()
+        print(f"ok maskextend {a.prec} {a.z} steps of {a.h}x{a.w} mask fraction {float(masks.float().mean()):.6f}")
+        net.close()
+        return
     v = synth.em_volume(synth.BASE_SEED + 1, a.z, a.h, a.w)
     x = torch.from_numpy(v).cuda()
     out = torch.empty((a.z, a.h, a.w), dtype=torch.float32, device="cuda")
