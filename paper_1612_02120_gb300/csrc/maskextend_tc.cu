@@ -10,22 +10,26 @@
 // [8-channel chunk][pixel][16 B], the column tap a (D kx x 16)-byte shift of the descriptor.
 //
 // The weights of the deeper layers (up to 16 taps x 64 x 128 FP16 = 256 KB) do not fit in shared
-// memory beside the staged rows, so B is streamed per tap and reused over a group of 4 output rows
-// of one residue class y mod D (4 TMEM accumulators, 128 columns apart). A group's taps run
-// ky-major: step ky reads staged rows m + ky .. m + ky + 3, so the window of staged rows slides by
-// one row per step and one new row is staged per step. In step 0 the four rows are issued one after
+// memory beside the staged rows, so B is streamed in units of 4 taps (2 for the widest layer) and
+// reused over a group of R output rows of one residue class y mod D (R TMEM accumulators: 8 at
+// N = 64, else 4). A group's taps run ky-major: step ky reads staged rows m + ky .. m + ky + R - 1,
+// so the window of staged rows slides by one row per step. In step 0 the rows are issued one after
 // the other (all four taps of ky = 0 resident), so an accumulator is only waited for when its row
-// starts while the epilogue drains the previous group's rows in the same order.
+// starts while the epilogue drains the previous group's rows in the same order. The issuing thread
+// polls one mbarrier per weight unit and per staged row and commits once per unit, per staged row
+// and per group: with the tensor pipe reading shared memory at its full rate, each poll or commit
+// costs tens of cycles of MMA issue.
 //
 // Warp roles (512 threads, 1 CTA per SM, persistent over work items):
 //   warp 0       TMEM owner; lane 0 issues the MMAs
-//   warp 1       lane 0 streams the tap tiles of the packed weights into the tap ring with bulk
-//                asynchronous copies (completion counted on the slot's mbarrier)
+//   warp 1       lane 0 streams the weight units into their ring with bulk asynchronous copies
+//                (completion counted on the unit's mbarrier)
 //   warps 4-7    epilogue: TMEM -> registers, + bias, max-out, FP16 store (head: the 1x1 conv to 3
 //                classes and the softmax, FP32 probabilities)
-//   warps 8-15   A producers, two groups of 4 warps taking alternate staged rows: the 2x2
-//                max-filter (dilation dm) of the previous layer's output, or the assembled input
-//                stack, into the staged-row ring
+//   warps 8-15   A producers, groups taking staged rows in turn (4 groups of 2 warps for the first
+//                layer, 2 of 4 after): the 2x2 max-filter (dilation dm) of the previous layer's
+//                output, or the assembled input stack, into the staged-row ring (as deep as shared
+//                memory allows, up to 12 rows)
 // Every mbarrier wait is bounded (a global-timer limit), after which the CTA records
 // MB_ERR_TIMEOUT in a mapped host word, stops issuing work, waits (bounded) for its bulk copies in
 // flight and frees its TMEM.
@@ -45,9 +49,7 @@ namespace mb {
 namespace {
 
 constexpr int kMThreads = 512;
-constexpr int kMARing = 5;   // staged rows: 4 in use by a step + 1 being filled
-constexpr int kMBRing = 6;   // tap tiles: the 4 taps of a group's first step + 2 ahead
-constexpr int kMAcc = 4;     // accumulators = output rows per group
+constexpr int kMBRing = 3;   // weight units in flight (a unit is 4 or 2 tap tiles)
 constexpr uint64_t kMWaitNs = 4000000000ull;
 
 // Staged pixels per row: >= 128 + 3 D, and chosen so that the 8 threads of a quarter-warp, which
@@ -65,15 +67,28 @@ struct MCfg {
     static constexpr int kARow = kChunks * kMP * 16;     // bytes per staged row
     static constexpr int kBTap = kChunks * N * 16;       // bytes per tap tile [chunk][N][16 B]
     static constexpr int kConsts = N + (HEAD ? 3 * 64 + 3 : 0);  // biases (+ head W[3][64], b[3])
+    // output rows per group = TMEM accumulators (512 columns, 64 or 128 apart)
+    static constexpr int kR = N <= 64 ? 8 : 4;
+    static constexpr int kAccStride = 512 / kR;
+    // taps per weight unit (one mbarrier, one release): a whole step's 4 taps, or 2 for the widest
+    static constexpr int kBU = KC == 4 ? 2 : 4;
+    static constexpr int kBUnit = kBU * kBTap;
+    // staged rows: kR in use by a step, the rest filled ahead (as many as fit, up to 12)
+    static constexpr int kFixed = kMBRing * kBUnit + kConsts * 4 + 16 + (2 * kMBRing + kR + 2) * 8 + 16;
+    static constexpr int kARing = (227 * 1024 - kFixed) / (kARow + 16) < 12 ? (227 * 1024 - kFixed) / (kARow + 16) : 12;
+    // producer groups taking staged rows in turn (more for the short rows of the first layer)
+    static constexpr int kGroups = KC == 1 ? 4 : 2;
+    static constexpr int kGThreads = 256 / kGroups;
     static constexpr int oA = 0;
-    static constexpr int oB = oA + kMARing * kARow;
-    static constexpr int oConst = oB + kMBRing * kBTap;
+    static constexpr int oB = oA + kARing * kARow;
+    static constexpr int oConst = oB + kMBRing * kBUnit;
     static constexpr int oBar = oConst + ((kConsts * 4 + 15) & ~15);
-    static constexpr int kBars = 2 * kMARing + 2 * kMBRing + 2 * kMAcc + 1;
+    static constexpr int kBars = 2 * kARing + 2 * kMBRing + 1 + kR + 1;
     static constexpr int oMisc = oBar + kBars * 8;
     static constexpr int kSmem = oMisc + 16;
-    static constexpr int kATasks = (kNpix * kChunks + 127) / 128;
+    static constexpr int kATasks = (kNpix * kChunks + kGThreads - 1) / kGThreads;
     static_assert(kNpix <= kMP, "staged row too short");
+    static_assert(kARing >= kR + 1, "staged-row ring");
     static_assert(N % 16 == 0 && N <= 128, "MMA N");
     static_assert(kSmem <= 227 * 1024, "shared memory");
 };
@@ -151,30 +166,28 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
     using C = MCfg<KC, N, D, HEAD>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* a_full = reinterpret_cast<uint64_t*>(smem + C::oBar);
-    uint64_t* a_empty = a_full + kMARing;
-    uint64_t* b_full = a_empty + kMARing;
+    uint64_t* a_empty = a_full + C::kARing;
+    uint64_t* b_full = a_empty + C::kARing;
     uint64_t* b_empty = b_full + kMBRing;
-    uint64_t* acc_full = b_empty + kMBRing;
-    uint64_t* acc_free = acc_full + kMAcc;
-    uint64_t* fin = acc_free + kMAcc;
+    uint64_t* acc_full = b_empty + kMBRing;  // one per CTA: a group's accumulators are complete
+    uint64_t* acc_free = acc_full + 1;       // per accumulator: drained by the epilogue
+    uint64_t* fin = acc_free + C::kR;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::oMisc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::oMisc + 4);
     const float* cst = reinterpret_cast<const float*>(smem + C::oConst);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int i = 0; i < kMARing; ++i) {
-            ptx::mbar_init(&a_full[i], 128);
+        for (int i = 0; i < C::kARing; ++i) {
+            ptx::mbar_init(&a_full[i], C::kGThreads);
             ptx::mbar_init(&a_empty[i], 1);
         }
         for (int i = 0; i < kMBRing; ++i) {
             ptx::mbar_init(&b_full[i], 1);
             ptx::mbar_init(&b_empty[i], 1);
         }
-        for (int i = 0; i < kMAcc; ++i) {
-            ptx::mbar_init(&acc_full[i], 1);
-            ptx::mbar_init(&acc_free[i], 128);
-        }
+        ptx::mbar_init(acc_full, 1);
+        for (int i = 0; i < C::kR; ++i) ptx::mbar_init(&acc_free[i], 128);
         ptx::mbar_init(fin, 1);
         *abort_flag = 0;
         ptx::mbar_fence_init();
@@ -200,68 +213,93 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
             const uint64_t adesc0 = ptx::smem_desc(sbase + C::oA, C::kMP * 16, 128);
             const uint64_t bdesc0 = ptx::smem_desc(sbase + C::oB, N * 16, 128);
             constexpr uint32_t idesc = ptx::idesc_f32acc(ptx::kFmtF16, 128, N);
-            uint32_t a_seq = 0, b_seq = 0, acc_seq = 0;
+            constexpr int kR = C::kR, kBU = C::kBU;
+            uint32_t a_seq = 0, u_seq = 0;
+            uint32_t free_par = 0;  // bit j: parity of the next use of accumulator j
             bool ok = true;
-            // output row j of the group, staged row s + j, tap kx, tap tile of sequence number bq
-            auto issue = [&](int j, int s, int kx, uint32_t bq, bool first) {
-                const uint32_t dcol = tbase + 128u * ((acc_seq + j) % kMAcc);
-                const uint32_t aslot = (a_seq + s + j) % kMARing;
-                const uint64_t ad = adesc0 + (uint64_t)((aslot * C::kARow + D * kx * 16) >> 4);
-                const uint64_t bd = bdesc0 + (uint64_t)(((bq % kMBRing) * C::kBTap) >> 4);
+            // Row j of every group accumulates in TMEM columns kAccStride j (a group always starts
+            // at accumulator 0, so a group cannot complete before the epilogue has taken the one
+            // before it). Descriptors of a step: ad[j] = staged row s + j, bu[] = weight units; the
+            // tap shift D kx and the K chunk kc are compile-time offsets.
+            uint64_t ad[kR];
+            auto mma_row = [&](int j, int kx, uint64_t bd, bool first) {
 #pragma unroll
                 for (int kc = 0; kc < KC; ++kc)
-                    ptx::mma_bf16(dcol, ad + (uint64_t)((kc * 2 * C::kMP * 16) >> 4),
-                                  bd + (uint64_t)((kc * 2 * N * 16) >> 4), idesc, (first && kc == 0) ? 0u : 1u);
+                    ptx::mma_bf16(tbase + (uint32_t)(C::kAccStride * j), ad[j] + (uint64_t)((D * kx * 16 + kc * 2 * C::kMP * 16) >> 4),
+                                  bd + (uint64_t)(((kx % kBU) * C::kBTap + kc * 2 * N * 16) >> 4), idesc,
+                                  (first && kc == 0) ? 0u : 1u);
+            };
+            auto unit_desc = [&](uint32_t q) { return bdesc0 + (uint64_t)(((q % kMBRing) * C::kBUnit) >> 4); };
+            auto wait_unit = [&](uint32_t q) {
+                ok = ok && wait_bar(&b_full[q % kMBRing], (q / kMBRing) & 1, abort_flag, p.err, p.wait_ns);
             };
             for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
                 const MeItem it = me_item<D>(p, k);
                 if (it.rows == 0) continue;
-                const int groups = (it.rows + kMAcc - 1) / kMAcc;
+                const int groups = (it.rows + kR - 1) / kR;
                 int a_known = 0;  // staged rows [0, a_known) of the item are known full
+                int a_rel = 0;    // staged rows [0, a_rel) are released
+                auto release_upto = [&](int last) {
+                    for (; a_rel <= last; ++a_rel) ptx::mma_commit(&a_empty[(a_seq + a_rel) % C::kARing]);
+                };
                 for (int g = 0; g < groups; ++g) {
-                    const int rg = min(kMAcc, it.rows - kMAcc * g);
+                    const int rg = min(kR, it.rows - kR * g);
                     for (int ky = 0; ky < 4; ++ky) {
-                        const int s = kMAcc * g + ky;  // staged rows s .. s + rg - 1
+                        const int s = kR * g + ky;  // staged rows s .. s + rg - 1
                         for (; a_known < s + rg; ++a_known) {
                             const uint32_t q = a_seq + a_known;
-                            ok = ok && wait_bar(&a_full[q % kMARing], (q / kMARing) & 1, abort_flag, p.err, p.wait_ns);
+                            ok = ok && wait_bar(&a_full[q % C::kARing], (q / C::kARing) & 1, abort_flag, p.err, p.wait_ns);
                         }
+#pragma unroll
+                        for (int j = 0; j < kR; ++j)
+                            ad[j] = adesc0 + (uint64_t)((((a_seq + s + j) % C::kARing) * C::kARow) >> 4);
+                        ptx::tc_fence_after();
                         if (ky == 0) {
-                            for (int j = 0; j < rg; ++j) {
-                                const uint32_t qa = acc_seq + j;
-                                ok = ok && wait_bar(&acc_free[qa % kMAcc], ((qa / kMAcc) & 1) ^ 1, abort_flag, p.err,
-                                                    p.wait_ns);
-                                for (int kx = 0; kx < 4; ++kx) {
-                                    if (j == 0) {
-                                        const uint32_t bq = b_seq + kx;
-                                        ok = ok && wait_bar(&b_full[bq % kMBRing], (bq / kMBRing) & 1, abort_flag,
-                                                            p.err, p.wait_ns);
+                            // rows one after the other, each waiting only for its own accumulator
+                            uint64_t bu[4 / kBU];
+#pragma unroll
+                            for (int u = 0; u < 4 / kBU; ++u) bu[u] = unit_desc(u_seq + u);
+#pragma unroll
+                            for (int j = 0; j < kR; ++j) {
+                                if (j < rg) {
+                                    ok = ok && wait_bar(&acc_free[j], ((free_par >> j) & 1) ^ 1, abort_flag, p.err,
+                                                        p.wait_ns);
+                                    free_par ^= 1u << j;
+#pragma unroll
+                                    for (int kx = 0; kx < 4; ++kx) {
+                                        if (j == 0 && kx % kBU == 0) wait_unit(u_seq + kx / kBU);
+                                        ptx::tc_fence_after();
+                                        if (ok) mma_row(j, kx, bu[kx / kBU], kx == 0);
                                     }
-                                    ptx::tc_fence_after();
-                                    if (ok) issue(j, s, kx, b_seq + kx, kx == 0);
                                 }
                             }
-                            for (int kx = 0; kx < 4; ++kx) ptx::mma_commit(&b_empty[(b_seq + kx) % kMBRing]);
-                            b_seq += 4;
+#pragma unroll
+                            for (int u = 0; u < 4 / kBU; ++u) ptx::mma_commit(&b_empty[(u_seq + u) % kMBRing]);
+                            u_seq += 4 / kBU;
                         } else {
-                            for (int kx = 0; kx < 4; ++kx) {
-                                ok = ok && wait_bar(&b_full[b_seq % kMBRing], (b_seq / kMBRing) & 1, abort_flag, p.err,
-                                                    p.wait_ns);
+#pragma unroll
+                            for (int u = 0; u < 4 / kBU; ++u) {
+                                wait_unit(u_seq);
                                 ptx::tc_fence_after();
-                                if (ok)
-                                    for (int j = 0; j < rg; ++j) issue(j, s, kx, b_seq, false);
-                                ptx::mma_commit(&b_empty[b_seq % kMBRing]);
-                                ++b_seq;
+                                const uint64_t bd = unit_desc(u_seq);
+                                if (ok) {
+#pragma unroll
+                                    for (int t = 0; t < kBU; ++t)
+#pragma unroll
+                                        for (int j = 0; j < kR; ++j)
+                                            if (j < rg) mma_row(j, u * kBU + t, bd, false);
+                                }
+                                ptx::mma_commit(&b_empty[u_seq % kMBRing]);
+                                ++u_seq;
                             }
                         }
                         // staged row s is not read by any later step
-                        ptx::mma_commit(&a_empty[(a_seq + s) % kMARing]);
+                        release_upto(s);
                     }
-                    for (int j = 0; j < rg; ++j) ptx::mma_commit(&acc_full[(acc_seq + j) % kMAcc]);
-                    acc_seq += rg;
+                    ptx::mma_commit(acc_full);
+                    // rows before the next group's first are done; after the last group, all rows
+                    release_upto(g + 1 < groups ? kR * (g + 1) - 1 : it.rows + 2);
                 }
-                // staged rows after the last step's first row (the item stages rows + 3)
-                for (int u = kMAcc * groups; u < it.rows + 3; ++u) ptx::mma_commit(&a_empty[(a_seq + u) % kMARing]);
                 a_seq += it.rows + 3;
             }
             ptx::mma_commit(fin);
@@ -278,15 +316,18 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
         // ================= epilogue ===================================================================
         const int px = tid - 128;  // TMEM lane = pixel of the strip
         const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
-        uint32_t acc_seq = 0;
+        uint32_t n_groups = 0;
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const MeItem it = me_item<D>(p, k);
             const int x = it.x0 + px;
             for (int j = 0; j < it.rows; ++j) {
-                const uint32_t qa = acc_seq + j, s = qa % kMAcc;
-                wait_bar(&acc_full[s], (qa / kMAcc) & 1, abort_flag, p.err, p.wait_ns);
-                ptx::tc_fence_after();
-                const uint32_t ta = tbase + lanes + 128u * s;
+                if (j % C::kR == 0) {  // a new group: all its accumulators are complete together
+                    wait_bar(acc_full, n_groups & 1, abort_flag, p.err, p.wait_ns);
+                    ++n_groups;
+                    ptx::tc_fence_after();
+                }
+                const uint32_t s = j % C::kR;  // accumulator of this row
+                const uint32_t ta = tbase + lanes + (uint32_t)C::kAccStride * s;
                 const int y = it.ry + D * (it.m0 + j);
                 const bool store = x < p.out_w && y < p.out_h && !*abort_flag;
                 if constexpr (HEAD) {
@@ -355,25 +396,25 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
                     }
                 }
             }
-            acc_seq += it.rows;
         }
     } else if (warp == 1) {
-        // ================= B producer: tap tiles, in the issuer's order =============================
+        // ================= B producer: weight units, in the issuer's order ==========================
         if (lane == 0) {
             uint32_t issued = 0;
             bool go = true;
             for (int k = blockIdx.x; go && k < p.n_items; k += gridDim.x) {
                 const MeItem it = me_item<D>(p, k);
                 if (it.rows == 0) continue;
-                const int groups = (it.rows + kMAcc - 1) / kMAcc;
+                const int groups = (it.rows + C::kR - 1) / C::kR;
                 for (int g = 0; go && g < groups; ++g)
-                    for (int t = 0; go && t < 16; ++t) {
+                    for (int t0 = 0; go && t0 < 16; t0 += C::kBU) {
                         const uint32_t slot = issued % kMBRing;
                         go = wait_bar(&b_empty[slot], ((issued / kMBRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
                         if (go && !p.fault_stall) {
-                            ptx::mbar_arrive_expect_tx(&b_full[slot], C::kBTap);
-                            ptx::bulk_copy_g2s(smem + C::oB + slot * C::kBTap, p.wpack + (size_t)t * C::kBTap,
-                                               C::kBTap, &b_full[slot]);
+                            ptx::mbar_arrive_expect_tx(&b_full[slot], C::kBUnit);
+                            for (int t = 0; t < C::kBU; ++t)
+                                ptx::bulk_copy_g2s(smem + C::oB + slot * C::kBUnit + t * C::kBTap,
+                                                   p.wpack + (size_t)(t0 + t) * C::kBTap, C::kBTap, &b_full[slot]);
                             ++issued;
                         }
                     }
@@ -391,25 +432,25 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
         __syncwarp();
     } else if (warp >= 8) {
         // ================= A producers: staged input rows ===========================================
-        // Group grp = warps 8-11 / 12-15 stages the rows u = grp mod 2 of every item. Task
-        // e = pt + 128 i: chunk e % kChunks of staged pixel e / kChunks (consecutive threads read
+        // Group grp (kGroups groups of 8 / kGroups warps) stages the rows u = grp mod kGroups. Task
+        // e = pt + kGThreads i: chunk e % kChunks of staged pixel e / kChunks (consecutive threads read
         // consecutive 16-byte chunks of one source pixel). All loads of a row are issued before the
         // slot wait so their latency overlaps it.
-        const int grp = (warp - 8) >> 2;
-        const int pt = tid - 256 - 128 * grp;
+        const int grp = (tid - 256) / C::kGThreads;
+        const int pt = tid - 256 - C::kGThreads * grp;
         const int64_t dxo = (int64_t)p.dm * p.cs, dyo = (int64_t)p.dm * p.in_pitch * p.cs;
         const int src_chunks = p.cs / 8;
         uint32_t a_seq = 0;
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const MeItem it = me_item<D>(p, k);
             if (it.rows == 0) continue;
-            for (int u = grp; u < it.rows + 3; u += 2) {
-                const uint32_t q = a_seq + u, slot = q % kMARing;
+            for (int u = grp; u < it.rows + 3; u += C::kGroups) {
+                const uint32_t q = a_seq + u, slot = q % C::kARing;
                 const int yin = it.ry + D * (it.m0 + u);
                 uint4 v[C::kATasks];
 #pragma unroll
                 for (int i = 0; i < C::kATasks; ++i) {
-                    const int e = pt + 128 * i;
+                    const int e = pt + C::kGThreads * i;
                     const int c = e % C::kChunks, xin = it.x0 + e / C::kChunks;
                     v[i] = make_uint4(0, 0, 0, 0);
                     if (e < C::kNpix * C::kChunks && c < src_chunks && yin < p.in_rows && xin < p.in_cols) {
@@ -425,11 +466,11 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
                         }
                     }
                 }
-                wait_bar(&a_empty[slot], ((q / kMARing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                wait_bar(&a_empty[slot], ((q / C::kARing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
                 uint8_t* dst = smem + C::oA + slot * C::kARow;
 #pragma unroll
                 for (int i = 0; i < C::kATasks; ++i) {
-                    const int e = pt + 128 * i;
+                    const int e = pt + C::kGThreads * i;
                     if (e < C::kNpix * C::kChunks)
                         *reinterpret_cast<uint4*>(dst + ((e % C::kChunks) * C::kMP + e / C::kChunks) * 16) = v[i];
                 }
