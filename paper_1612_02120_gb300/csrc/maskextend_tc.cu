@@ -39,6 +39,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -219,15 +220,19 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
             bool ok = true;
             // Row j of every group accumulates in TMEM columns kAccStride j (a group always starts
             // at accumulator 0, so a group cannot complete before the epilogue has taken the one
-            // before it). Descriptors of a step: ad[j] = staged row s + j, bu[] = weight units; the
-            // tap shift D kx and the K chunk kc are compile-time offsets.
-            uint64_t ad[kR];
-            auto mma_row = [&](int j, int kx, uint64_t bd, bool first) {
+            // before it). Rows are runtime loops and only taps and K chunks are unrolled (the tap
+            // shift D kx and the chunk kc are compile-time offsets): a short issue loop stays in
+            // the instruction cache beside the other roles' code.
+            auto mma_taps = [&](uint64_t ad, uint32_t dcol, uint64_t bd, auto kx0, auto ntaps, bool zero_first) {
 #pragma unroll
-                for (int kc = 0; kc < KC; ++kc)
-                    ptx::mma_bf16(tbase + (uint32_t)(C::kAccStride * j), ad[j] + (uint64_t)((D * kx * 16 + kc * 2 * C::kMP * 16) >> 4),
-                                  bd + (uint64_t)(((kx % kBU) * C::kBTap + kc * 2 * N * 16) >> 4), idesc,
-                                  (first && kc == 0) ? 0u : 1u);
+                for (int t = 0; t < decltype(ntaps)::value; ++t)
+#pragma unroll
+                    for (int kc = 0; kc < KC; ++kc) {
+                        const int kx = decltype(kx0)::value + t;
+                        ptx::mma_bf16(dcol, ad + (uint64_t)((D * kx * 16 + kc * 2 * C::kMP * 16) >> 4),
+                                      bd + (uint64_t)(((kx % kBU) * C::kBTap + kc * 2 * N * 16) >> 4), idesc,
+                                      (zero_first && t == 0 && kc == 0) ? 0u : 1u);
+                    }
             };
             auto unit_desc = [&](uint32_t q) { return bdesc0 + (uint64_t)(((q % kMBRing) * C::kBUnit) >> 4); };
             auto wait_unit = [&](uint32_t q) {
@@ -250,44 +255,57 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
                             const uint32_t q = a_seq + a_known;
                             ok = ok && wait_bar(&a_full[q % C::kARing], (q / C::kARing) & 1, abort_flag, p.err, p.wait_ns);
                         }
-#pragma unroll
-                        for (int j = 0; j < kR; ++j)
-                            ad[j] = adesc0 + (uint64_t)((((a_seq + s + j) % C::kARing) * C::kARow) >> 4);
-                        ptx::tc_fence_after();
+                        const uint32_t aslot0 = (a_seq + s) % C::kARing;
+                        auto arow = [&](int j) {
+                            const uint32_t sl = aslot0 + j < (uint32_t)C::kARing ? aslot0 + j : aslot0 + j - C::kARing;
+                            return adesc0 + (uint64_t)((sl * C::kARow) >> 4);
+                        };
                         if (ky == 0) {
-                            // rows one after the other, each waiting only for its own accumulator
-                            uint64_t bu[4 / kBU];
-#pragma unroll
-                            for (int u = 0; u < 4 / kBU; ++u) bu[u] = unit_desc(u_seq + u);
-#pragma unroll
-                            for (int j = 0; j < kR; ++j) {
-                                if (j < rg) {
-                                    ok = ok && wait_bar(&acc_free[j], ((free_par >> j) & 1) ^ 1, abort_flag, p.err,
-                                                        p.wait_ns);
-                                    free_par ^= 1u << j;
-#pragma unroll
-                                    for (int kx = 0; kx < 4; ++kx) {
-                                        if (j == 0 && kx % kBU == 0) wait_unit(u_seq + kx / kBU);
-                                        ptx::tc_fence_after();
-                                        if (ok) mma_row(j, kx, bu[kx / kBU], kx == 0);
+                            // the step's weight units, then rows one after the other, each waiting
+                            // only for its own accumulator
+                            for (int u = 0; u < 4 / kBU; ++u) wait_unit(u_seq + u);
+                            const uint64_t bd0 = unit_desc(u_seq), bd1 = unit_desc(u_seq + (4 / kBU) - 1);
+                            for (int j = 0; j < rg; ++j) {
+                                ok = ok && wait_bar(&acc_free[j], ((free_par >> j) & 1) ^ 1, abort_flag, p.err,
+                                                    p.wait_ns);
+                                free_par ^= 1u << j;
+                                ptx::tc_fence_after();
+                                const uint64_t ad = arow(j);
+                                const uint32_t dcol = tbase + (uint32_t)(C::kAccStride * j);
+                                if (ok) {
+                                    if constexpr (kBU == 4) {
+                                        mma_taps(ad, dcol, bd0, std::integral_constant<int, 0>{},
+                                                 std::integral_constant<int, 4>{}, true);
+                                    } else {
+                                        mma_taps(ad, dcol, bd0, std::integral_constant<int, 0>{},
+                                                 std::integral_constant<int, 2>{}, true);
+                                        mma_taps(ad, dcol, bd1, std::integral_constant<int, 2>{},
+                                                 std::integral_constant<int, 2>{}, false);
                                     }
                                 }
                             }
-#pragma unroll
                             for (int u = 0; u < 4 / kBU; ++u) ptx::mma_commit(&b_empty[(u_seq + u) % kMBRing]);
                             u_seq += 4 / kBU;
                         } else {
-#pragma unroll
                             for (int u = 0; u < 4 / kBU; ++u) {
                                 wait_unit(u_seq);
                                 ptx::tc_fence_after();
                                 const uint64_t bd = unit_desc(u_seq);
                                 if (ok) {
-#pragma unroll
-                                    for (int t = 0; t < kBU; ++t)
-#pragma unroll
-                                        for (int j = 0; j < kR; ++j)
-                                            if (j < rg) mma_row(j, u * kBU + t, bd, false);
+                                    for (int j = 0; j < rg; ++j) {
+                                        const uint64_t ad = arow(j);
+                                        const uint32_t dcol = tbase + (uint32_t)(C::kAccStride * j);
+                                        if constexpr (kBU == 4) {
+                                            mma_taps(ad, dcol, bd, std::integral_constant<int, 0>{},
+                                                     std::integral_constant<int, 4>{}, false);
+                                        } else if (u == 0) {
+                                            mma_taps(ad, dcol, bd, std::integral_constant<int, 0>{},
+                                                     std::integral_constant<int, 2>{}, false);
+                                        } else {
+                                            mma_taps(ad, dcol, bd, std::integral_constant<int, 2>{},
+                                                     std::integral_constant<int, 2>{}, false);
+                                        }
+                                    }
                                 }
                                 ptx::mma_commit(&b_empty[u_seq % kMBRing]);
                                 ++u_seq;
