@@ -565,6 +565,8 @@ def main():
             p7[name] = {
                 "mvox_s": mv, "ms": statistics.mean(ms), "steps_per_s": N7 / (statistics.mean(ms) / 1e3),
                 "tflops": MASKEXTEND_FLOP_PER_PX * mv * 1e6 / 1e12,
+                "frac_of_sustained_16bit_peak": (MASKEXTEND_FLOP_PER_PX * mv * 1e6 / 1e12 / peaks()[0]["bf16_tflops_sustained"]
+                                                 if prec == m.MB_PREC_FP16 else None),
                 "mask_fraction": float(masks7.float().mean()),
                 "error_step0_crop128": {k: v for k, v in oracle.metrics(got, ref).items()}}
             me.close()
