@@ -137,3 +137,17 @@ def test_fp16_is_maskextend_only():
     with pytest.raises(m.MembraneError) as e:
         m.mb_net_create(M, m.MB_PREC_BF16, 0)
     assert e.value.status == m.MB_ERR_UNSUPPORTED
+
+
+def test_fp16_step_at_bench_size_on_sampled_crops(net16):
+    """One step on the 512x512 window the bench times, in its launch configuration: the class
+    maps of two 96x96 crops (one at a corner, so the mirror padding is inside it) against the
+    oracle evaluated on the crops with their true context."""
+    em, memb, seeds = data(8, 512, 512, 9700)
+    masks, probs = run_gpu(net16, em, memb, seeds, 3, 1)
+    prm = me_params().astype(np.float64)
+    xp = oracle.maskextend_input(em, memb, {-1 + i: seeds[i] for i in range(4)}, 3, 54)
+    for y0, x0 in ((0, 0), (300, 181)):
+        ref = oracle.run_layers_mc(M, prm, xp[:, y0:y0 + 96 + 108, x0:x0 + 96 + 108])
+        met = oracle.metrics(probs[0][:, y0:y0 + 96, x0:x0 + 96], ref)
+        assert met["max_abs"] <= TOL["fp16"]["max_abs"] and met["mean_abs"] <= TOL["fp16"]["mean_abs"], met
