@@ -104,17 +104,20 @@ __global__ void __launch_bounds__(256) student_head_loss(float* h2, const float*
     if (threadIdx.x == 0) partial[blockIdx.x * 18 + 17] = r;
 }
 
-// conv2 weight gradient: thread (co, ci) accumulates its 9 taps over 16x16 pixel tiles.
+// conv2 weight gradient over 16x16 pixel tiles. Thread t: input channel ci = t & 15, output
+// channels co and co + 8 (co = (t >> 4) & 7), tile rows 8 (t >> 7) .. + 7. Along each row it keeps
+// the 3x3 window of h1 in registers and loads one new column (3 values) and the two dy2 values per
+// pixel for its 18 FMAs; the two row halves are added (first + second) at the end.
 // Partials per CTA: [2304 (co,ci,ky,kx)] then db2[16].
 __global__ void __launch_bounds__(256) student_grad2(const float* dy2, const float* h1, int B, int H, int W,
                                                      float* partial) {
     __shared__ __align__(16) float s_d[256 * 16];
     __shared__ __align__(16) float s_h[18 * 18 * 16];
-    const int t = threadIdx.x, co = t >> 4, ci = t & 15;
-    float acc[9];
+    const int t = threadIdx.x, ci = t & 15, co = (t >> 4) & 7, half = t >> 7;
+    float acc0[9], acc1[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
-    float db = 0.f;
+    for (int k = 0; k < 9; ++k) acc0[k] = acc1[k] = 0.f;
+    float db0 = 0.f, db1 = 0.f;
     const int tx_n = (W + 15) / 16, ty_n = (H + 15) / 16;
     const int64_t tiles = (int64_t)B * tx_n * ty_n;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -138,34 +141,74 @@ __global__ void __launch_bounds__(256) student_grad2(const float* dy2, const flo
             *reinterpret_cast<float4*>(s_h + px * 16 + 4 * q) = v;
         }
         __syncthreads();
-        for (int py = 0; py < 16; ++py)
-#pragma unroll 4
+        for (int py = 8 * half; py < 8 * half + 8; ++py) {
+            float w[3][3];  // h1 at rows py + ky, columns px + kx
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 2; ++kx) w[ky][kx + 1] = s_h[((py + ky) * 18 + kx) * 16 + ci];
+#pragma unroll
             for (int px = 0; px < 16; ++px) {
-                const float d = s_d[(py * 16 + px) * 16 + co];
-                db += d;
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky) {
+                    w[ky][0] = w[ky][1];
+                    w[ky][1] = w[ky][2];
+                    w[ky][2] = s_h[((py + ky) * 18 + px + 2) * 16 + ci];
+                }
+                const float d0 = s_d[(py * 16 + px) * 16 + co], d1 = s_d[(py * 16 + px) * 16 + co + 8];
+                db0 += d0;
+                db1 += d1;
 #pragma unroll
                 for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
-                        acc[ky * 3 + kx] = fmaf(d, s_h[((py + ky) * 18 + px + kx) * 16 + ci], acc[ky * 3 + kx]);
+                    for (int kx = 0; kx < 3; ++kx) {
+                        acc0[ky * 3 + kx] = fmaf(d0, w[ky][kx], acc0[ky * 3 + kx]);
+                        acc1[ky * 3 + kx] = fmaf(d1, w[ky][kx], acc1[ky * 3 + kx]);
+                    }
             }
+        }
     }
-    float* out = partial + (int64_t)blockIdx.x * 2320;
+    // add the second half's sums to the first's
+    __syncthreads();
+    float* x = s_d + (t & 127) * 20;
+    if (half == 1) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) out[(co * 16 + ci) * 9 + k] = acc[k];
-    if (ci == 0) out[2304 + co] = db;
+        for (int k = 0; k < 9; ++k) {
+            x[k] = acc0[k];
+            x[9 + k] = acc1[k];
+        }
+        x[18] = db0;
+        x[19] = db1;
+    }
+    __syncthreads();
+    if (half == 0) {
+        float* out = partial + (int64_t)blockIdx.x * 2320;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            out[(co * 16 + ci) * 9 + k] = acc0[k] + x[k];
+            out[((co + 8) * 16 + ci) * 9 + k] = acc1[k] + x[9 + k];
+        }
+        if (ci == 0) {
+            out[2304 + co] = db0 + x[18];
+            out[2304 + co + 8] = db1 + x[19];
+        }
+    }
 }
 
 // conv1 weight gradient over the (H+2) x (W+2) layer-1 domain; x is the input mirror-padded by 2.
-// Thread t < 144: (co, tap); t in [144,160): db1[co]. Partials per CTA: [144] then [16].
+// Thread t: output channel co = t & 15, tile row r = t >> 4; along the row it keeps the 3x3 window
+// of x in registers (one new column of 3 per pixel) for its 9 FMAs and the bias sum. At the end the
+// 16 rows' sums are added in row order. Partials per CTA: [144 (co,ky,kx)] then db1[16].
 __global__ void __launch_bounds__(256) student_grad1(const float* dy1, const uint8_t* in, const int* zmap,
                                                      int64_t in_slice, int B, int H, int W, float* partial) {
-    __shared__ __align__(16) float s_d[256 * 16];
+    // dy1 tile [row][16 px][16 co], rows 272 floats apart so the two rows of a warp use distinct banks
+    __shared__ __align__(16) float s_d[16 * 272];
     __shared__ __align__(16) float s_x[18 * 18];
-    const int t = threadIdx.x;
-    const int co = t < 144 ? t / 9 : t - 144, tap = t < 144 ? t % 9 : 0;
-    const int ky = tap / 3, kx = tap % 3;
-    float acc = 0.f;
+    const int t = threadIdx.x, co = t & 15, r = t >> 4;
+    float acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+    float db = 0.f;
     const int H1 = H + 2, W1 = W + 2;
     const int tx_n = (W1 + 15) / 16, ty_n = (H1 + 15) / 16;
     const int64_t tiles = (int64_t)B * tx_n * ty_n;
@@ -179,7 +222,7 @@ __global__ void __launch_bounds__(256) student_grad1(const float* dy1, const uin
             const int y = y0 + (px >> 4), x = x0 + (px & 15);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (y < H1 && x < W1) v = *reinterpret_cast<const float4*>(dy1 + (((int64_t)zi * H1 + y) * W1 + x) * 16 + 4 * q);
-            *reinterpret_cast<float4*>(s_d + px * 16 + 4 * q) = v;
+            *reinterpret_cast<float4*>(s_d + (px >> 4) * 272 + (px & 15) * 16 + 4 * q) = v;
         }
         const uint8_t* src = in + (int64_t)(zmap ? zmap[zi] : zi) * in_slice;
         for (int e = t; e < 18 * 18; e += 256) {
@@ -189,30 +232,60 @@ __global__ void __launch_bounds__(256) student_grad1(const float* dy1, const uin
             s_x[e] = v;
         }
         __syncthreads();
-        if (t < 160) {
-            for (int py = 0; py < 16; ++py)
-                for (int px = 0; px < 16; ++px) {
-                    const float d = s_d[(py * 16 + px) * 16 + co];
-                    acc = t < 144 ? fmaf(d, s_x[(py + ky) * 18 + px + kx], acc) : acc + d;
-                }
+        float w[3][3];  // x at rows r + ky, columns px + kx
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 2; ++kx) w[ky][kx + 1] = s_x[(r + ky) * 18 + kx];
+#pragma unroll
+        for (int px = 0; px < 16; ++px) {
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+                w[ky][0] = w[ky][1];
+                w[ky][1] = w[ky][2];
+                w[ky][2] = s_x[(r + ky) * 18 + px + 2];
+            }
+            const float d = s_d[r * 272 + px * 16 + co];
+            db += d;
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) acc[ky * 3 + kx] = fmaf(d, w[ky][kx], acc[ky * 3 + kx]);
         }
     }
-    if (t < 160) partial[(int64_t)blockIdx.x * 160 + t] = acc;
+    // rows' sums -> [r][co][10] in shared memory, then added in row order
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s_d[(r * 16 + co) * 10 + k] = acc[k];
+    s_d[(r * 16 + co) * 10 + 9] = db;
+    __syncthreads();
+    if (t < 160) {
+        const int c = t < 144 ? t / 9 : t - 144, k = t < 144 ? t % 9 : 9;
+        float sum = 0.f;
+        for (int rr = 0; rr < 16; ++rr) sum += s_d[(rr * 16 + c) * 10 + k];
+        partial[(int64_t)blockIdx.x * 160 + t] = sum;
+    }
 }
 
-// grad[off + i] = sum over CTAs (fixed order, FP64) of partial[cta][col0 + i], i < count.
+// grad[off + i] = sum over CTAs (FP64, fixed order) of partial[cta][col0 + i], i < count; with
+// loss_out, also *loss_out = inv_n x the sum of column loss_col. One warp per output: lane l adds
+// CTAs l, l + 32, ... in order, then the lanes are combined by a fixed xor-shuffle tree. Launch
+// with 256-thread blocks, ceil((count + (loss_out != nullptr)) / 8) of them.
 __global__ void reduce_partials(const float* partial, int ncta, int width, int col0, int count, float* grad, int off,
                                 float* loss_out, int loss_col, float inv_n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) {
-        double s = 0.0;
-        for (int c = 0; c < ncta; ++c) s += (double)partial[(int64_t)c * width + col0 + i];
-        grad[off + i] = (float)s;
-    }
-    if (loss_out && i == 0) {
-        double s = 0.0;
-        for (int c = 0; c < ncta; ++c) s += (double)partial[(int64_t)c * width + loss_col];
-        *loss_out = (float)(s * (double)inv_n);
+    const int o = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const bool is_loss = loss_out && o == count;
+    if (o >= count && !is_loss) return;
+    const int col = is_loss ? loss_col : col0 + o;
+    double s = 0.0;
+    for (int c = lane; c < ncta; c += 32) s += (double)partial[(int64_t)c * width + col];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) {
+        if (is_loss)
+            *loss_out = (float)(s * (double)inv_n);
+        else
+            grad[off + o] = (float)s;
     }
 }
 
@@ -343,13 +416,13 @@ static mb_status batch_grad(mb_net* s, const uint8_t* in, const float* tgt, cons
     MB_TRY((launch_conv<3, 16, 16, 8, IN_F32, OUT_ACT>(c, (int)B, st)));
     // head + loss; h2 -> dy2
     student_head_loss<<<kGridHead, 256, 0, st>>>(b.h2, tgt, zmap, H * W, (int)B, (int)H, (int)W, fwd, inv_n, b.part);
-    reduce_partials<<<1, 32, 0, st>>>(b.part, kGridHead, 18, 1, 17, b.grad, kSWH, loss_dev, 0, inv_n);
+    reduce_partials<<<(17 + 1 + 7) / 8, 256, 0, st>>>(b.part, kGridHead, 18, 1, 17, b.grad, kSWH, loss_dev, 0, inv_n);
     count_launch(2);
     // conv2 weight gradient (needs h1 intact)
     student_grad2<<<kGridG2, 256, 0, st>>>(b.h2, b.h1, (int)B, (int)H, (int)W, b.part);
-    reduce_partials<<<(2304 + 255) / 256, 256, 0, st>>>(b.part, kGridG2, 2320, 0, 2304, b.grad, kSW2, nullptr, 0, 0.f);
-    reduce_partials<<<1, 32, 0, st>>>(b.part, kGridG2, 2320, 2304, 16, b.grad, kSB2, nullptr, 0, 0.f);
-    count_launch(3);
+    static_assert(kSB2 == kSW2 + 2304, "W2 and b2 are adjacent in the parameter layout");
+    reduce_partials<<<(2320 + 7) / 8, 256, 0, st>>>(b.part, kGridG2, 2320, 0, 2320, b.grad, kSW2, nullptr, 0, 0.f);
+    count_launch(2);
     // dy1 = conv(dy2 zero-padded by 2, flipped W2) masked by h1 > 0, in place of h1
     ConvArgs d{};
     d.in = b.h2;
@@ -372,9 +445,9 @@ static mb_status batch_grad(mb_net* s, const uint8_t* in, const float* tgt, cons
     MB_TRY((launch_conv<3, 16, 16, 8, IN_F32_PAD, OUT_GRADMASK>(d, (int)B, st)));
     // conv1 weight gradient
     student_grad1<<<kGridG1, 256, 0, st>>>(b.h1, in, zmap, H * W, (int)B, (int)H, (int)W, b.part);
-    reduce_partials<<<1, 160, 0, st>>>(b.part, kGridG1, 160, 0, 144, b.grad, kSW1, nullptr, 0, 0.f);
-    reduce_partials<<<1, 32, 0, st>>>(b.part, kGridG1, 160, 144, 16, b.grad, kSB1, nullptr, 0, 0.f);
-    count_launch(3);
+    static_assert(kSB1 == kSW1 + 144, "W1 and b1 are adjacent in the parameter layout");
+    reduce_partials<<<(160 + 7) / 8, 256, 0, st>>>(b.part, kGridG1, 160, 0, 160, b.grad, kSW1, nullptr, 0, 0.f);
+    count_launch(2);
     MB_CUDA(cudaGetLastError());
     return MB_OK;
 }

@@ -5,6 +5,8 @@ volume (the generator of `synth`), so a capture of one kernel stays a few hundre
     python -m paper_1612_02120_gb300.profile_case --net fastmemb --prec bf16 --z 4 --reps 3
     python -m paper_1612_02120_gb300.profile_case --net maskextend --prec fp16 --z 4 --h 512 --w 512
       (MaskExtend: `z` transfer steps on an h x w window per rep)
+    python -m paper_1612_02120_gb300.profile_case --net student-train --z 64 --h 512 --w 512 --reps 4
+      (student training: `reps` optimiser steps, batch 32, on z slices with FP32 teacher targets)
 """
 import argparse
 import os
@@ -17,7 +19,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--net", default="teacher", choices=["teacher", "fastmemb", "maskextend"])
+    ap.add_argument("--net", default="teacher", choices=["teacher", "fastmemb", "maskextend", "student-train"])
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "fp8", "fp16", "student"])
     ap.add_argument("--z", type=int, default=4)
     ap.add_argument("--h", type=int, default=1024)
@@ -29,6 +31,18 @@ def main():
     import synth
     from paper_1612_02120_gb300 import build, membrane as m
     build.build()
+    if a.net == "student-train":
+        v = torch.from_numpy(synth.em_volume(synth.BASE_SEED + 4, a.z, a.h, a.w)).cuda()
+        tgt = torch.empty((a.z, a.h, a.w), dtype=torch.float32, device="cuda")
+        with m.Net(synth.TEACHER, m.MB_PREC_FP32, 0, synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED)) as t:
+            m.mb_infer_volume(t.handle, v, a.z, a.h, a.w, tgt)
+        sp = synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0)
+        with m.Net(synth.STUDENT, m.MB_PREC_BF16, 0, sp) as st:
+            m.mb_student_train(st.handle, v, tgt, a.z, a.h, a.w,
+                               m.train_cfg(batch=32, steps=a.reps, lr=1e-3, seed=synth.BASE_SEED + 4))
+        torch.cuda.synchronize()
+        print(f"ok student-train {a.reps} steps, batch 32 of {a.z}x{a.h}x{a.w}")
+        return
     if a.net == "maskextend":
         em = synth.em_volume(synth.BASE_SEED + 7, a.z + 4, a.h, a.w)
         d = [torch.from_numpy(arr).cuda() for arr in

@@ -43,16 +43,18 @@ def test_student_forward_matches_oracle(lib, prec):
     net.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_student_gradient_matches_oracle(lib, prec):
+@pytest.mark.parametrize("prec,shape", [("fp32", (3, 40, 52)), ("bf16", (3, 40, 52)), ("fp32", (4, 100, 130))])
+def test_student_gradient_matches_oracle(lib, prec, shape):
+    """Loss and gradient vs the FP64 oracle; (4, 100, 130) spans many 16x16 tiles per slice, with
+    ragged tiles at the bottom and right edges."""
     import torch
     m = lib
     p32 = synth.init_params(S, synth.STUDENT_WEIGHT_SEED, bias_std=0.05)
     net = make_net(S, {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16}[prec], p32)
-    v = synth.em_volume(3002, 3, 40, 52)
+    v = synth.em_volume(3002, *shape)
     tgt = np.random.default_rng(3).uniform(0.05, 0.95, size=v.shape).astype(np.float32)
     grad = torch.empty(net.n_params, dtype=torch.float32, device="cuda")
-    loss = m.mb_student_loss_grad(net.handle, torch.from_numpy(v).cuda(), torch.from_numpy(tgt).cuda(), 3, 40, 52,
+    loss = m.mb_student_loss_grad(net.handle, torch.from_numpy(v).cuda(), torch.from_numpy(tgt).cuda(), *shape,
                                   grad)
     pref = bf16_round(p32) if prec == "bf16" else p32
     loss_ref, g_ref = oracle.student_loss_grad(S, pref, v, tgt)
