@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmembrane.so")
 SOURCES = ["api.cu", "simt_conv.cu", "tc_conv.cu", "student.cu", "noalloc.cu", "fastmemb.cu", "fastmemb_tc.cu", "maskextend.cu",
-           "maskextend_tc.cu"]
+           "maskextend_tc.cu", "student_tc.cu"]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_ptx.cuh"), os.path.join(CSRC, "simt_conv.cuh"),
            os.path.join(CSRC, "fm_conv.cuh"),
            os.path.join(ROOT, "include", "membrane.h")]

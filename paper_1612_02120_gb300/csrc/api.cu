@@ -236,6 +236,16 @@ mb_status teacher_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, i
     return tc_infer_blocks(net, &b, 1, &y0, &x0, &rows, &cols, ot, st, false);
 }
 
+mb_status student_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+                         int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
+                         int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st) {
+    if (net->prec == MB_PREC_BF16)
+        return st_tc_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch, out_slice, ot,
+                            st);
+    return simt_student_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch, out_slice,
+                               ot, st);
+}
+
 static mb_status fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
                                  int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
                                  int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub = 1) {
@@ -253,7 +263,7 @@ static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h
     if (net->family == FAMILY_TEACHER)
         return teacher_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
     if (z == 0) return MB_OK;
-    return simt_student_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
+    return student_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
 }
 
 // Host-memory volumes: z-slabs through double-buffered device slabs, H2D / compute / D2H on three
@@ -454,6 +464,7 @@ mb_status mb_net_destroy(mb_net* net) {
         tc_release(net);
         fm_tc_release(net);
         me_tc_release(net);
+        st_tc_release(net);
         dev_free(net->d_params);
         dev_free(net->d_simt);
         dev_free(net->d_queue);
@@ -715,7 +726,7 @@ mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t 
             MB_TRY(fastmemb_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w, b.out,
                                    b.out_pitch, b.out_slice_pitch, out_type, st));
         } else if (b.z > 0) {
-            MB_TRY(simt_student_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w,
+            MB_TRY(student_region(net, b.in, b.z, b.h, b.w, b.in_pitch, b.in_slice_pitch, 0, 0, b.h, b.w,
                                        b.out, b.out_pitch, b.out_slice_pitch, out_type, st));
         }
     }

@@ -77,6 +77,7 @@ struct mb_net {
     void* tc_state = nullptr;    // tensor-core path state (packed operands, constants), tc_conv.cu
     void* fm_state = nullptr;    // FastMemb tensor-core state (packed operands, error word), fastmemb_tc.cu
     void* me_state = nullptr;    // MaskExtend tensor-core state (packed operands, error word), maskextend_tc.cu
+    void* st_state = nullptr;    // student tensor-core state (packed operands, error word), student_tc.cu
     float fp8_amax[2][32] = {};
     mb::Workspace ws;            // layered FP32 path activations
     mb::Workspace ws2;           // student training / cascade scratch
@@ -140,6 +141,15 @@ mb_status me_tc_layer(mb_net* net, int layer, const void* in, int64_t in_pitch, 
 mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int64_t zt, int64_t h, int64_t w,
                          const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
                          float* probs_out, cudaStream_t st);
+// BF16 student inference on the tensor cores (student_tc.cu), same arguments as simt_student_region;
+// student_region picks it for BF16 nets and the CUDA-core path for FP32 nets.
+mb_status st_tc_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+                       int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
+                       int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st);
+void st_tc_release(mb_net* net);
+mb_status student_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+                         int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
+                         int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st);
 // FP32 teacher activations after the two max-filters: per-channel amax over n slices (device out[64]).
 mb_status simt_teacher_amax(mb_net* net, const uint8_t* in, int64_t n, int64_t h, int64_t w, float* d_amax,
                             cudaStream_t st);

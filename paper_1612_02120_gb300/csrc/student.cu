@@ -619,7 +619,7 @@ mb_status cascade(mb_net* s, mb_net* t, const uint8_t* in, int64_t z, int64_t h,
         *rate = 0.0;
         return MB_OK;
     }
-    MB_TRY(simt_student_region(s, in, z, h, w, w, h * w, 0, 0, h, w, out, w, h * w, MB_OUT_F32, st));
+    MB_TRY(student_region(s, in, z, h, w, w, h * w, 0, 0, h, w, out, w, h * w, MB_OUT_F32, st));
     const int tx_n = (int)((w + tile - 1) / tile), ty_n = (int)((h + tile - 1) / tile);
     const int64_t ntiles = z * tx_n * ty_n;
     uint8_t* d_flags = nullptr;

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from _common import infer, make_net, student_params, teacher_params
+from _common import TOL, infer, make_net, student_params, teacher_params
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +31,8 @@ def lib():
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_student_forward_matches_oracle(lib, prec):
+    """FP32 student (CUDA cores) within 1e-5 of the oracle; BF16 student (BF16 weights, the fused
+    tensor-core kernel with BF16 layer-1 features) within the BF16 bar."""
     m = lib
     p32 = student_params()
     net = make_net(S, {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16}[prec], p32)
@@ -39,7 +41,11 @@ def test_student_forward_matches_oracle(lib, prec):
     pref = bf16_round(p32) if prec == "bf16" else p32
     for zi in range(2):
         ref = oracle.forward_region(S, pref, v[zi])
-        assert np.abs(out[zi] - ref).max() <= 1e-5
+        if prec == "fp32":
+            assert np.abs(out[zi] - ref).max() <= 1e-5
+        else:  # a 70x45 map: max-abs and mean-abs (agreement is asserted on maps >= 4096 px)
+            met = oracle.metrics(out[zi], ref)
+            assert met["max_abs"] <= TOL["bf16"]["max_abs"] and met["mean_abs"] <= TOL["bf16"]["mean_abs"], met
     net.close()
 
 
