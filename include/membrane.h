@@ -77,7 +77,9 @@ typedef enum {
  * dilation and maxout_groups 0 are read as 1.
  * Supported networks: the teacher (conv5x5 1->32 ReLU, maxfilter 2, conv5x5 32->32 ReLU,
  * maxfilter 2, conv5x5 32->32 ReLU, head 32->1) in FP32, BF16 and FP8; the student (conv3x3
- * 1->16 ReLU, conv3x3 16->16 ReLU, head 16->1) in FP32 and BF16; and FastMemb in dense form
+ * 1->16 ReLU, conv3x3 16->16 ReLU, head 16->1) in FP32 and BF16 (BF16 weights; its inference runs
+ * on the tensor cores with BF16 layer-1 features and FP32 accumulation, its training forward in
+ * FP32 arithmetic); and FastMemb in dense form
  * (Sec. 2.2: conv4x4 1->32 G=2 d=1, maxfilter d=1, conv4x4 32->32 G=2 d=2, maxfilter d=2,
  * conv4x4 32->32 G=2 d=4, maxfilter d=4, softmax head conv4x4 32->2 d=8; no ReLU; radius 26,
  * so its slices need h, w >= 27) and FastMemb_3nm (Sec. 2.2, "A subsampling CNN for 3 nm data":
