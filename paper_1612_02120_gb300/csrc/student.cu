@@ -639,37 +639,71 @@ mb_status cascade(mb_net* s, mb_net* t, const uint8_t* in, int64_t z, int64_t h,
         if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data(), d_flags, (size_t)ntiles, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { rc = cuda_fail(e, "tile flags", __FILE__, __LINE__); break; }
-        // the teacher recomputes every flagged tile with its true context, writing into out
+        // the teacher recomputes every flagged tile with its true context, writing into out. Runs of
+        // flagged tiles along a tile row, and runs of such rows with the same column span, are
+        // recomputed as one region (the teacher's output at a pixel does not depend on the region
+        // around it, so this only removes strip and launch overheads).
+        struct Region {
+            int64_t zi, y0, rows, x0, cols;
+        };
+        std::vector<Region> regions;
+        int64_t nflag = 0;
+        for (int64_t zi = 0; zi < z; ++zi) {
+            std::vector<Region> open;  // regions that may extend into the next tile row
+            for (int64_t ty = 0; ty < ty_n; ++ty) {
+                const int64_t y0 = ty * tile, th = std::min<int64_t>(tile, h - y0);
+                std::vector<Region> spans;
+                for (int64_t tx = 0; tx < tx_n; ++tx) {
+                    if (!hf[(size_t)((zi * ty_n + ty) * tx_n + tx)]) continue;
+                    ++nflag;
+                    const int64_t x0 = tx * tile, tw = std::min<int64_t>(tile, w - x0);
+                    if (!spans.empty() && spans.back().x0 + spans.back().cols == x0)
+                        spans.back().cols += tw;
+                    else
+                        spans.push_back({zi, y0, th, x0, tw});
+                }
+                std::vector<Region> next;
+                for (const Region& sp : spans) {
+                    bool merged = false;
+                    for (Region& o : open)
+                        if (!merged && o.x0 == sp.x0 && o.cols == sp.cols && o.y0 + o.rows == sp.y0) {
+                            o.rows += sp.rows;
+                            next.push_back(o);
+                            o.cols = 0;  // taken over by next
+                            merged = true;
+                        }
+                    if (!merged) next.push_back(sp);
+                }
+                for (const Region& o : open)
+                    if (o.cols > 0) regions.push_back(o);
+                open.swap(next);
+            }
+            for (const Region& o : open) regions.push_back(o);
+        }
         std::vector<mb_block> blocks;
         std::vector<int64_t> ry, rx, rr, rcn;
-        int64_t nflag = 0;
-        for (int64_t k = 0; k < ntiles; ++k) {
-            if (!hf[(size_t)k]) continue;
-            ++nflag;
-            const int64_t zi = k / ((int64_t)tx_n * ty_n), rem = k % ((int64_t)tx_n * ty_n);
-            const int64_t y0 = (rem / tx_n) * tile, x0 = (rem % tx_n) * tile;
-            const int64_t th = std::min<int64_t>(tile, h - y0), tw = std::min<int64_t>(tile, w - x0);
+        for (const Region& g : regions) {
             if (t->prec == MB_PREC_FP32) {
-                rc = simt_teacher_region(t, in + zi * h * w, 1, h, w, w, h * w, y0, x0, th, tw,
-                                         out + zi * h * w + y0 * w + x0, w, h * w, MB_OUT_F32, st);
+                rc = simt_teacher_region(t, in + g.zi * h * w, 1, h, w, w, h * w, g.y0, g.x0, g.rows, g.cols,
+                                         out + g.zi * h * w + g.y0 * w + g.x0, w, h * w, MB_OUT_F32, st);
                 if (rc != MB_OK) break;
                 continue;
             }
             mb_block b;
-            b.in = in + zi * h * w;
+            b.in = in + g.zi * h * w;
             b.z = 1;
             b.h = h;
             b.w = w;
             b.in_pitch = w;
             b.in_slice_pitch = h * w;
-            b.out = out + zi * h * w + y0 * w + x0;
+            b.out = out + g.zi * h * w + g.y0 * w + g.x0;
             b.out_pitch = w;
             b.out_slice_pitch = h * w;
             blocks.push_back(b);
-            ry.push_back(y0);
-            rx.push_back(x0);
-            rr.push_back(th);
-            rcn.push_back(tw);
+            ry.push_back(g.y0);
+            rx.push_back(g.x0);
+            rr.push_back(g.rows);
+            rcn.push_back(g.cols);
         }
         if (rc != MB_OK) break;
         if (!blocks.empty())
