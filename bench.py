@@ -413,7 +413,7 @@ def main():
         teacher32 = m.Net(synth.TEACHER, m.MB_PREC_FP32, local, params)
         m.mb_infer_volume(teacher32.handle, tv, n_tr, s_tr, s_tr, tgt)
         teacher32.close()
-        sp = synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0)
+        sp = synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0, centred_input=True)
         student = m.Net(synth.STUDENT, m.MB_PREC_BF16, local, sp)
         untrained = m.Net(synth.STUDENT, m.MB_PREC_BF16, local, sp)
         cfg = m.train_cfg(batch=32, steps=2000, lr=1e-3, seed=synth.BASE_SEED + 4)

@@ -217,6 +217,9 @@ mb_status mb_student_loss_grad(mb_net* student, const uint8_t* in, const float* 
  * Train a student net in place on n slices (device in[n][h][w], target[n][h][w] float32 teacher
  * maps): cfg->steps Adam steps on batches of cfg->batch slices sampled with replacement
  * (seeded); FP32 master weights, m and v; the forward copy is rounded to BF16 for BF16 nets.
+ * Layer 1 is optimised in centred-input coordinates: Adam updates W1 and c1 = b1 + sum(W1)/2
+ * (the same network written for the input x - 1/2, a standard preconditioning of gradient
+ * training); the weights stay stored for x = u/255, and m, v hold the centred moments.
  * loss_curve (HOST, may be NULL) receives one loss per step run. With ckpt_path (HOST string,
  * may be NULL), a checkpoint {step, master weights, m, v, sampler state} is written every
  * cfg->ckpt_every steps; with cfg->resume the run continues from it, bitwise as if never

@@ -5,7 +5,8 @@ baseline leg of ``bench.py``; never by the library. It shares no code with the C
 only shared module is ``synth`` (seeded inputs).
 
 ``liboracle.so`` is compiled on first use from ``oracle.c`` (gcc, OpenMP over output channels,
-no FMA contraction). Every function here marshals numpy arrays into that library.
+no FMA contraction). Every function here marshals numpy arrays into that library, except the
+student's change of coordinates for its training update (a few lines of numpy).
 """
 from __future__ import annotations
 
@@ -290,6 +291,46 @@ def adam_step(w, m, v, g, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     _chk(_load().oracle_adam_step(w.ctypes.data, m.ctypes.data, v.ctypes.data, g.ctypes.data, w.size, step,
                                   lr, b1, b2, eps), "adam_step")
     return w, m, v
+
+
+def centred_layer1(layers, w):
+    """Map student parameters to the coordinates in which layer 1 is optimised: the network
+    rewritten for the zero-centred input x - 1/2. Correlating the mirror-padded input shifted by
+    -1/2 with W1 shifts every output by -(1/2) sum W1, so the same map has bias
+    c1 = b1 + (1/2) sum_k W1[co][k]; every other parameter is unchanged."""
+    _, k, cin, cout = layers[0][:4]
+    nw = cout * cin * k * k
+    th = _f64(w).copy()
+    th[nw:nw + cout] += 0.5 * th[:nw].reshape(cout, -1).sum(axis=1)
+    return th
+
+
+def plain_layer1(layers, th):
+    """Inverse of centred_layer1: b1 = c1 - (1/2) sum_k W1[co][k]."""
+    _, k, cin, cout = layers[0][:4]
+    nw = cout * cin * k * k
+    w = _f64(th).copy()
+    w[nw:nw + cout] -= 0.5 * w[:nw].reshape(cout, -1).sum(axis=1)
+    return w
+
+
+def centred_grad(layers, g):
+    """Gradient in the centred coordinates by the chain rule through b1 = c1 - (1/2) sum W1:
+    dL/dW1[co][k] - (1/2) dL/db1[co] for the weights, dL/db1 for c1, the rest unchanged."""
+    _, k, cin, cout = layers[0][:4]
+    nw = cout * cin * k * k
+    gc = _f64(g).copy()
+    gc[:nw] = (gc[:nw].reshape(cout, -1) - 0.5 * gc[nw:nw + cout, None]).reshape(-1)
+    return gc
+
+
+def student_adam_step(layers, w, m, v, g, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One student training update: Adam (Kingma & Ba 2014) in the coordinates of centred_layer1,
+    i.e. the step of training the same network on the centred input x - 1/2, mapped back to the
+    stored form (input u/255). m and v are the moments of the centred gradients. Returns
+    (w, m, v)."""
+    th, m, v = adam_step(centred_layer1(layers, w), m, v, centred_grad(layers, g), step, lr, b1, b2, eps)
+    return plain_layer1(layers, th), m, v
 
 
 def metrics(p_gpu, p_ref) -> dict:

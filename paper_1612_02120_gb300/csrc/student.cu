@@ -12,8 +12,9 @@
 // Every reduction runs in a fixed order (per-CTA partials over a fixed grid, then a per-parameter
 // sum over CTAs in FP64), so a run is bitwise reproducible and a resumed run equals an
 // uninterrupted one.
-// Adam (Kingma and Ba, 2014): FP32 master weights, first/second moments, bias correction; the
-// forward copy is rounded to BF16 for BF16 students.
+// Adam (Kingma and Ba, 2014): FP32 master weights, first/second moments, bias correction, with
+// layer 1 optimised in centred-input coordinates (see adam_step); the forward copy is rounded to
+// BF16 for BF16 students.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -310,18 +311,46 @@ __global__ void student_pack(const float* master, float* fwd, float* w2f, int bf
     }
 }
 
-__global__ void adam_step(float* w, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
-                          float eps, float c1, float c2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
+// Adam (Kingma & Ba 2014) with bias correction, one thread per parameter, except layer 1, which is
+// optimised in centred coordinates: Adam updates W1 and c1 = b1 + (1/2) sum_k W1[co][k], the bias
+// of the same network written for the zero-centred input x - 1/2 (conv(pad(x) - 1/2) =
+// conv(pad(x)) - (1/2) sum W, since the mirror pad of a constant shift is the same shift). In those
+// coordinates the gradients are g_W1 - g_b1 / 2 and g_b1, and the update maps back to the stored
+// form as W1 -= dW, b1 -= dc - (1/2) sum_k dW: the trajectory of training on a centred input,
+// while the stored network keeps the input u/255. Threads 0..15: one layer-1 output channel each
+// (its 9 weights and its bias); the rest: parameters kSW2 .. n-1.
+__device__ __forceinline__ float adam_delta(float* m, float* v, int i, float gi, float lr, float b1, float b2,
+                                            float eps, float c1, float c2) {
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
     const float mh = mi / c1, vh = vi / c2;
-    w[i] -= lr * mh / (sqrtf(vh) + eps);
+    return lr * mh / (sqrtf(vh) + eps);
 }
+
+__global__ void adam_step(float* w, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
+                          float eps, float c1, float c2) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 16) {
+        const float gb = g[kSB1 + t];
+        float dsum = 0.f;
+        for (int k = 0; k < 9; ++k) {
+            const int i = kSW1 + 9 * t + k;
+            const float d = adam_delta(m, v, i, g[i] - 0.5f * gb, lr, b1, b2, eps, c1, c2);
+            w[i] -= d;
+            dsum += d;
+        }
+        const float dc = adam_delta(m, v, kSB1 + t, gb, lr, b1, b2, eps, c1, c2);
+        w[kSB1 + t] -= dc - 0.5f * dsum;
+        return;
+    }
+    const int i = kSW2 + t - 16;
+    if (i >= n) return;
+    w[i] -= adam_delta(m, v, i, g[i], lr, b1, b2, eps, c1, c2);
+}
+static_assert(kSW2 == kSB1 + 16, "layer-1 biases are followed by layer 2");
+constexpr int kAdamThreads = 16 + kSN - kSW2;
 
 // Device buffers of one training shape.
 struct StudentBufs {
@@ -567,7 +596,7 @@ mb_status student_train(mb_net* s, const uint8_t* in, const float* tgt, int64_t 
         MB_TRY(batch_grad(s, in, tgt, b.zmap + k * B, B, h, w, b, b.losses + k, st));
         const double c1 = 1.0 - std::pow((double)cfg->beta1, (double)step);
         const double c2 = 1.0 - std::pow((double)cfg->beta2, (double)step);
-        adam_step<<<(kSN + 255) / 256, 256, 0, st>>>(s->d_params, b.m, b.v, b.grad, kSN, cfg->lr, cfg->beta1,
+        adam_step<<<(kAdamThreads + 255) / 256, 256, 0, st>>>(s->d_params, b.m, b.v, b.grad, kSN, cfg->lr, cfg->beta1,
                                                      cfg->beta2, cfg->eps, (float)c1, (float)c2);
         count_launch();
         MB_CUDA(cudaGetLastError());

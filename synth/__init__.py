@@ -191,12 +191,16 @@ def param_count(layers) -> int:
     return n
 
 
-def init_params(layers, seed: int, bias_std: float = 0.01, center_head: bool = False) -> np.ndarray:
+def init_params(layers, seed: int, bias_std: float = 0.01, center_head: bool = False,
+                centred_input: bool = False) -> np.ndarray:
     """He-normal FP32 parameters for `layers`, packed per parameterised layer as
     W[cout*G][cin][k][k] then b[cout*G] (G max-out groups); parameterised layer number l draws
     from seed + l. bias_std 0 gives zero biases. center_head: the last layer's filters are
     shifted to zero mean over their input channels at every tap (a distribution choice that keeps
-    a deep max-out stack's map away from saturation)."""
+    a deep max-out stack's map away from saturation). centred_input: the first layer's biases are
+    drawn for the input x - 1/2 instead of x and stored for x, i.e. each becomes
+    b - (1/2) sum of its filter, so that mid-grey input puts every first-layer unit at its bias
+    rather than far on one side of its ReLU."""
     parts = []
     l = 0
     n_par = sum(1 for layer in layers if layer[0] in (CONV, HEAD_SIGMOID, HEAD_SOFTMAX2, HEAD_SOFTMAX))
@@ -208,6 +212,8 @@ def init_params(layers, seed: int, bias_std: float = 0.01, center_head: bool = F
             if center_head and l == n_par - 1:
                 w4 = w.reshape(co, cin, k * k)
                 w = (w4 - w4.mean(axis=1, keepdims=True)).reshape(-1)
+            if centred_input and l == 0:
+                b = (b.astype(np.float64) - 0.5 * w.reshape(co, -1).astype(np.float64).sum(axis=1)).astype(np.float32)
             parts += [w, b]
             l += 1
     return np.concatenate(parts).astype(np.float32)

@@ -20,7 +20,7 @@ def teacher_params():
 
 
 def student_params():
-    return synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0)
+    return synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0, centred_input=True)
 
 
 def make_net(layers, prec, params):

@@ -86,7 +86,7 @@ def test_adam_first_step_matches_oracle(lib):
     m.mb_get_weights(net.handle, w)
     _, g_ref = oracle.student_loss_grad(S, p32, v[:1], tgt[:1])
     z = np.zeros(net.n_params)
-    w_ref, _, _ = oracle.adam_step(p32.astype(np.float64), z, z, g_ref, step=1, lr=1e-3)
+    w_ref, _, _ = oracle.student_adam_step(S, p32.astype(np.float64), z, z, g_ref, step=1, lr=1e-3)
     assert np.abs(w - w_ref).max() <= 2e-5 * 1e-3 + 1e-7
     net.close()
 

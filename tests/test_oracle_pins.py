@@ -194,6 +194,65 @@ def test_student_gradient_matches_central_differences():
         assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), abs(g[i])) + 1e-11, (i, fd, g[i])
 
 
+def test_centred_layer1_is_the_same_network_on_a_centred_input():
+    """c1 = b1 + sum(W1)/2 makes the first layer on the mirror-padded x - 1/2 equal the first
+    layer on x with b1 (numpy padding and scipy correlation, not the oracle's loops)."""
+    from scipy.signal import correlate2d
+    params = synth.init_params(S, synth.STUDENT_WEIGHT_SEED, bias_std=0.05).astype(np.float64)
+    th = oracle.centred_layer1(S, params)
+    np.testing.assert_array_equal(th[160:], params[160:])
+    np.testing.assert_allclose(oracle.plain_layer1(S, th), params, rtol=0, atol=1e-15)
+    x = synth.em_slice(21, 11, 13).astype(np.float64) / 255.0
+    xp = np.pad(x, 1, mode="reflect")
+    xc = np.pad(x - 0.5, 1, mode="reflect")
+    W1 = params[:144].reshape(16, 3, 3)
+    for co in range(16):
+        a = correlate2d(xp, W1[co], mode="valid") + params[144 + co]
+        b = correlate2d(xc, W1[co], mode="valid") + th[144 + co]
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+def test_centred_gradient_matches_central_differences():
+    """The training update's gradient (layer 1 in centred coordinates) equals central differences
+    of the loss as a function of those coordinates."""
+    rng = np.random.default_rng(8)
+    params = synth.init_params(S, synth.STUDENT_WEIGHT_SEED, bias_std=0.05).astype(np.float64)
+    imgs = rng.integers(0, 256, size=(2, 6, 6), dtype=np.uint8)
+    tgt = rng.uniform(0.1, 0.9, size=(2, 6, 6))
+    _, g = oracle.student_loss_grad(S, params, imgs, tgt)
+    gc = oracle.centred_grad(S, g)
+    th = oracle.centred_layer1(S, params)
+
+    def loss_c(t):
+        return oracle.student_loss_grad(S, oracle.plain_layer1(S, t), imgs, tgt)[0]
+
+    h = 1e-6
+    for i in list(range(0, 160)) + [160, 1000, params.size - 1]:
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (loss_c(tp) - loss_c(tm)) / (2 * h)
+        assert abs(fd - gc[i]) <= 1e-6 * max(abs(fd), abs(gc[i])) + 1e-11, (i, fd, gc[i])
+
+
+def test_student_first_update_closed_form():
+    """From zero moments every centred coordinate moves by -lr g/(|g| + eps); mapped back, each
+    layer-1 bias moves by its own step plus half the sum of its channel's weight steps."""
+    rng = np.random.default_rng(9)
+    params = synth.init_params(S, synth.STUDENT_WEIGHT_SEED, bias_std=0.05).astype(np.float64)
+    g = rng.normal(size=params.size)
+    z = np.zeros(params.size)
+    w, m, v = oracle.student_adam_step(S, params, z, z, g, step=1, lr=1e-3)
+    gw = g[:144].reshape(16, 9) - 0.5 * g[144:160, None]
+    dw = 1e-3 * gw / (np.abs(gw) + 1e-8)
+    db = 1e-3 * g[144:160] / (np.abs(g[144:160]) + 1e-8)
+    np.testing.assert_allclose(w[:144], params[:144] - dw.reshape(-1), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(w[144:160], params[144:160] - db + 0.5 * dw.sum(axis=1), rtol=0, atol=1e-14)
+    rest = 1e-3 * g[160:] / (np.abs(g[160:]) + 1e-8)
+    np.testing.assert_allclose(w[160:], params[160:] - rest, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(m[:144], 0.1 * gw.reshape(-1), rtol=1e-14)
+
+
 def test_student_loss_is_mse():
     params = synth.init_params(S, synth.STUDENT_WEIGHT_SEED).astype(np.float64)
     imgs = synth.em_volume(3, 2, 10, 12)

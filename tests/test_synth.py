@@ -59,3 +59,11 @@ def test_centred_head_has_zero_channel_mean_and_leaves_other_layers():
     np.testing.assert_array_equal(a[-2:], b[-2:])
     w = b[-n_head:-2].reshape(2, 32, 16).astype(np.float64)
     assert np.abs(w.mean(axis=1)).max() < 1e-6
+
+
+def test_centred_input_init_only_moves_first_layer_biases():
+    a = synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0)
+    b = synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0, centred_input=True)
+    np.testing.assert_array_equal(a[:144], b[:144])
+    np.testing.assert_array_equal(a[160:], b[160:])
+    np.testing.assert_allclose(b[144:160], -0.5 * a[:144].reshape(16, 9).astype(np.float64).sum(axis=1), rtol=1e-6)
