@@ -482,23 +482,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         __syncwarp();
         } else if (warp == 1) {
         // ================= input loader ======================================================
+        // Each lane owns columns lane + 32 i of the 132 read per row. The bytes of row u+1 are
+        // requested before waiting for row u's ring slot, so one row's global latency overlaps the
+        // wait and the conversion of the row before it.
         uint32_t in_seq = 0;
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const ItemInfo it = decode_item(p, k);
             const TcBlockDesc& d = p.blk[it.b];
             const uint8_t* src = d.in + (int64_t)it.zi * d.in_slice;
             const int nrows = it.rows + 14;
-            for (int u = 0; u < nrows; ++u) {
-                const uint32_t q = in_seq + u, s = q % kInRing;
-                wait_phase(&B.in_empty[s], ((q / kInRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+            int sx[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) sx[i] = refl_clamp(d.rx0 + it.x0 - 7 + lane + 32 * i, d.w);
+            auto load_row = [&](int u, uint32_t (&v)[5]) {
                 const int sy = refl_clamp(d.ry0 + it.y0 - 7 + u, d.h);
                 const uint8_t* row = src + (int64_t)sy * d.in_pitch;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) v[i] = (lane + 32 * i < kInCols) ? (uint32_t)__ldg(row + sx[i]) : 0u;
+            };
+            uint32_t v[5];
+            load_row(0, v);
+            for (int u = 0; u < nrows; ++u) {
+                uint32_t nv[5];
+                load_row(u + 1 < nrows ? u + 1 : u, nv);
+                const uint32_t q = in_seq + u, s = q % kInRing;
+                wait_phase(&B.in_empty[s], ((q / kInRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
                 float* dst = in_ring + s * kPitch;
-                for (int c = lane; c < kInCols; c += 32) {
-                    const int sx = refl_clamp(d.rx0 + it.x0 - 7 + c, d.w);
-                    dst[c] = (float)__ldg(row + sx) / 255.0f;
-                }
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+                    if (lane + 32 * i < kInCols) dst[lane + 32 * i] = (float)v[i] / 255.0f;
                 if (!p.fault_stall) ptx::mbar_arrive(&B.in_full[s]);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) v[i] = nv[i];
             }
             in_seq += nrows;
         }
