@@ -266,8 +266,9 @@ static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h
     return student_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
 }
 
-// Host-memory volumes: z-slabs through double-buffered device slabs, H2D / compute / D2H on three
-// streams so copies overlap compute.
+// Host-memory volumes: z-slabs through double-buffered device slabs, H2D / compute / D2H on their
+// own streams so copies overlap compute (the tensor-core teacher computes on two alternating
+// streams, so one slab's launch tail overlaps the next launch).
 static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,
                                    mb_out_type ot) {
     const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
@@ -284,8 +285,12 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
     const size_t slab_bytes = (in_slice + out_slice) * (size_t)slab;
     MB_TRY(net->slab_ws.ensure(NB * slab_bytes));
     cudaStream_t* s = net->slab_streams;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 4; ++i)
         if (!s[i]) MB_CUDA(cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking));
+    // The fused tensor-core teacher keeps no device state between launches, so consecutive slabs
+    // may compute on two streams: the next slab's CTAs start on the SMs the previous launch's
+    // tail leaves idle. Paths with a shared workspace compute their slabs in order on one stream.
+    const bool overlap = net->family == FAMILY_TEACHER && net->prec != MB_PREC_FP32;
     cudaEvent_t* ev_in = net->slab_events;
     cudaEvent_t* ev_comp = ev_in + NB;
     cudaEvent_t* ev_out = ev_comp + NB;
@@ -305,15 +310,16 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
         if (k >= NB) e = cudaStreamWaitEvent(s[0], ev_comp[b], 0);  // input buffer free
         if (e == cudaSuccess) e = cudaMemcpyAsync(din, in + z0 * in_slice, in_slice * nz, cudaMemcpyHostToDevice, s[0]);
         if (e == cudaSuccess) e = cudaEventRecord(ev_in[b], s[0]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s[1], ev_in[b], 0);
-        if (e == cudaSuccess && k >= NB) e = cudaStreamWaitEvent(s[1], ev_out[b], 0);  // output buffer free
+        cudaStream_t cs = overlap && (k & 1) ? s[3] : s[1];
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in[b], 0);
+        if (e == cudaSuccess && k >= NB) e = cudaStreamWaitEvent(cs, ev_out[b], 0);  // output buffer free
         if (e != cudaSuccess) {
             fail(e, "slab H2D");
             break;
         }
-        rc = net_region(net, din, nz, h, w, 0, 0, h, w, dout, ot, s[1]);
+        rc = net_region(net, din, nz, h, w, 0, 0, h, w, dout, ot, cs);
         if (rc != MB_OK) break;
-        e = cudaEventRecord(ev_comp[b], s[1]);
+        e = cudaEventRecord(ev_comp[b], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s[2], ev_comp[b], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + z0 * out_slice, dout, out_slice * nz,
@@ -321,7 +327,7 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
         if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], s[2]);
         if (e != cudaSuccess) fail(e, "slab D2H");
     }
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         cudaError_t e = cudaStreamSynchronize(s[i]);
         if (e != cudaSuccess && rc == MB_OK) fail(e, "cudaStreamSynchronize");
     }

@@ -82,7 +82,7 @@ struct mb_net {
     mb::Workspace ws;            // layered FP32 path activations
     mb::Workspace ws2;           // student training / cascade scratch
     mb::Workspace slab_ws;       // host-buffer streaming: double-buffered device slabs
-    cudaStream_t slab_streams[3] = {nullptr, nullptr, nullptr};  // H2D, compute, D2H
+    cudaStream_t slab_streams[4] = {};  // H2D, compute, D2H, second compute stream (overlapping slabs)
     cudaEvent_t slab_events[6] = {};                              // per buffer: in, comp, out
     // persistent kernel tuning
     int rows_per_item = 64;
