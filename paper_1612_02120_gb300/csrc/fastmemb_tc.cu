@@ -45,22 +45,28 @@ constexpr int kFP = 178;                 // pixels per staged row (>= 128 + 3*16
                                          // the 4 chunk planes of one pixel pair over distinct banks
 constexpr int kFSlot = 4 * kFP * 16;     // bytes per staged row (4 chunks of 8 BF16 channels)
 constexpr int kFRing = 8;                // staged rows in flight
-constexpr int kFAcc = 4;                 // TMEM accumulators
+constexpr int kFAcc = 4;                 // TMEM accumulators of the 32->64 layers
+constexpr int kHAcc = 8;                 // head: ring of row accumulators (16 columns each)
 constexpr int kFTasks = 6;               // producer tasks per thread and row: ceil(4 * 176 / 128)
 constexpr int kFPrefetch = 4;            // staged rows between a row's L2 prefetch and its loads
 constexpr uint64_t kFWaitNs = 4000000000ull;
 
 template <bool HEAD>
 struct FCfg {
-    static constexpr int N = HEAD ? 16 : 128;          // MMA N
-    static constexpr int kBlock = 2 * N * 16;          // one (tap, K-half) B block: [2 chunks][N][16 B]
-    static constexpr int kBBytes = 32 * kBlock;
-    static constexpr int kTmemCols = HEAD ? 64 : 512;
+    // Layers: N = 128 per output row, one B block per (tap, K-half): [2 chunks][128 rows][16 B].
+    // Head: the 4 row taps are stacked along N, 16 rows each (4 used), one B block per (column
+    // tap, K-half): [2 chunks][64 rows][16 B]; a staged row's MMA covers up to 4 output rows.
+    static constexpr int N = HEAD ? 16 : 128;          // accumulator width per output row
+    static constexpr int kBRows = HEAD ? 64 : 128;     // B rows per block
+    static constexpr int kBlock = 2 * kBRows * 16;
+    static constexpr int kBBytes = (HEAD ? 8 : 32) * kBlock;
+    static constexpr int kAcc = HEAD ? kHAcc : kFAcc;
+    static constexpr int kTmemCols = HEAD ? 128 : 512;
     static constexpr int oB = 0;
     static constexpr int oRing = oB + kBBytes;
     static constexpr int oBias = oRing + kFRing * kFSlot;
     static constexpr int oBar = oBias + 64 * 4;
-    static constexpr int kBars = 2 * kFRing + 2 * kFAcc + 1;
+    static constexpr int kBars = 2 * kFRing + 2 * kAcc + 1;
     static constexpr int oMisc = oBar + kBars * 8;
     static constexpr int kSmem = oMisc + 16;
     static_assert(kSmem <= 227 * 1024, "shared memory");
@@ -145,8 +151,8 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
     uint64_t* row_full = reinterpret_cast<uint64_t*>(smem + C::oBar);
     uint64_t* row_empty = row_full + kFRing;
     uint64_t* acc_full = row_empty + kFRing;
-    uint64_t* acc_free = acc_full + kFAcc;
-    uint64_t* fin = acc_free + kFAcc;
+    uint64_t* acc_free = acc_full + C::kAcc;
+    uint64_t* fin = acc_free + C::kAcc;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::oMisc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::oMisc + 4);
     const float* bias = reinterpret_cast<const float*>(smem + C::oBias);
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
             ptx::mbar_init(&row_full[i], 128);
             ptx::mbar_init(&row_empty[i], 1);
         }
-        for (int i = 0; i < kFAcc; ++i) {
+        for (int i = 0; i < C::kAcc; ++i) {
             ptx::mbar_init(&acc_full[i], 1);
             ptx::mbar_init(&acc_free[i], 128);
         }
@@ -184,12 +190,23 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
     const uint32_t tbase = *tmem_slot;
     const uint32_t sbase = ptx::smem_u32(smem);
     const int d = p.d;
+    if constexpr (HEAD) {
+        // the head's MMAs only accumulate (a staged row adds to up to 4 rows at once): its used
+        // accumulator columns start at zero, and the epilogue re-zeroes them after each drain
+        if (warp >= 4 && warp < 8) {
+            const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
+            for (int sl = 0; sl < C::kAcc; ++sl) ptx::tmem_st4_zero(tbase + lanes + (uint32_t)C::N * sl);
+        }
+        ptx::tc_fence_before();
+        __syncthreads();
+        ptx::tc_fence_after();
+    }
 
     if (warp == 0) {
         // ================= MMA issuer ================================================================
         if (lane == 0) {
             const uint64_t adesc0 = ptx::smem_desc(sbase + C::oRing, kFP * 16, 128);
-            const uint64_t bdesc0 = ptx::smem_desc(sbase + C::oB, C::N * 16, 128);
+            const uint64_t bdesc0 = ptx::smem_desc(sbase + C::oB, C::kBRows * 16, 128);
             constexpr uint32_t idesc = ptx::idesc_f32acc(ptx::kFmtBF16, 128, C::N);
             uint32_t row_seq = 0, acc_seq = 0;
             bool ok = true;
@@ -220,6 +237,59 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                         }
                 }
             };
+            if constexpr (HEAD) {
+                // Staged row u of an item feeds output rows u - ky for ky = 0..3 (the row taps stacked
+                // along N): one MMA per (column tap, K-half) with D = the accumulators of rows u, u-1,
+                // u-2, u-3. Output row sequence q lives in ring slot K-1 - q mod K, so these rows sit in
+                // increasing slots; a window that wraps the ring is split in two MMAs. Only the rows of
+                // the item are written (N = 16 x the valid taps).
+                constexpr int K = C::kAcc;
+                auto slot_of = [](uint32_t q) { return (uint32_t)(K - 1) - q % (uint32_t)K; };
+                const uint64_t adesc = ptx::smem_desc(sbase + C::oRing, kFP * 16, 128);
+                const uint64_t bdesc = ptx::smem_desc(sbase + C::oB, C::kBRows * 16, 128);
+                const uint32_t idn[4] = {ptx::idesc_f32acc(ptx::kFmtBF16, 128, 16),
+                                         ptx::idesc_f32acc(ptx::kFmtBF16, 128, 32),
+                                         ptx::idesc_f32acc(ptx::kFmtBF16, 128, 48),
+                                         ptx::idesc_f32acc(ptx::kFmtBF16, 128, 64)};
+                for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+                    const FmItem it = fm_item(p, k);
+                    if (it.rows == 0) continue;
+                    const int nst = it.rows + 3;
+                    for (int u = 0; u < nst; ++u) {
+                        const int blo = max(0, u - it.rows + 1), bhi = min(3, u);
+                        wait_row(row_seq + u);
+                        if (blo == 0) {  // output row u starts here: its slot must have been drained
+                            const uint32_t q = acc_seq + u;
+                            ok = ok && wait_bar(&acc_free[slot_of(q)], ((q / K) & 1) ^ 1, abort_flag, p.err,
+                                                p.wait_ns);
+                        }
+                        ptx::tc_fence_after();
+                        if (ok) {
+                            const uint32_t s0 = slot_of(acc_seq + u - blo);
+                            const int nb = bhi - blo + 1;
+                            const int n1 = min(nb, K - (int)s0);  // taps before the ring wraps
+                            const uint64_t arow =
+                                adesc + (uint64_t)((((row_seq + u) % kFRing) * kFSlot) >> 4);
+#pragma unroll
+                            for (int kx = 0; kx < 4; ++kx)
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    const uint64_t ad = arow + (uint64_t)((h * 2 * kFP * 16 + d * kx * 16) >> 4);
+                                    const uint64_t bg = bdesc + (uint64_t)(((kx * 2 + h) * C::kBlock) >> 4);
+                                    ptx::mma_bf16(tbase + (uint32_t)C::N * s0, ad, bg + (uint64_t)((blo * 256) >> 4),
+                                                  idn[n1 - 1], 1u);
+                                    if (n1 < nb)
+                                        ptx::mma_bf16(tbase, ad, bg + (uint64_t)(((blo + n1) * 256) >> 4),
+                                                      idn[nb - n1 - 1], 1u);
+                                }
+                        }
+                        ptx::mma_commit(&row_empty[(row_seq + u) % kFRing]);
+                        if (u >= 3) ptx::mma_commit(&acc_full[slot_of(acc_seq + u - 3)]);
+                    }
+                    row_seq += nst;
+                    acc_seq += it.rows;
+                }
+            } else
             for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
                 const FmItem it = fm_item(p, k);
                 if (it.rows == 0) continue;
@@ -262,8 +332,9 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
             const FmItem it = fm_item(p, k);
             const int x = it.x0 + px;
             for (int j = 0; j < it.rows; ++j) {
-                const uint32_t qa = acc_seq + j, s = qa % kFAcc;
-                wait_bar(&acc_full[s], (qa / kFAcc) & 1, abort_flag, p.err, p.wait_ns);
+                const uint32_t qa = acc_seq + j;
+                const uint32_t s = HEAD ? (uint32_t)(C::kAcc - 1) - qa % (uint32_t)C::kAcc : qa % (uint32_t)C::kAcc;
+                wait_bar(&acc_full[s], (qa / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
                 ptx::tc_fence_after();
                 const uint32_t ta = tbase + lanes + (uint32_t)C::N * s;
                 const int y = it.ry + d * (it.m0 + j);
@@ -271,6 +342,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                 if constexpr (HEAD) {
                     float c[4];
                     ptx::tmem_ld4(ta, c);
+                    ptx::tmem_st4_zero(ta);
                     ptx::tc_fence_before();
                     ptx::mbar_arrive(&acc_free[s]);
                     const float z0 = (c[0] + c[2]) + bias[0], z1 = (c[1] + c[3]) + bias[1];
@@ -396,9 +468,10 @@ float bf16_value(uint16_t b) {
     return f;
 }
 
-// Pack a conv 4x4 32->C layer W[c][ci][ky][kx], b[c] as B operands: block (tap t = 4 ky + kx,
-// K-half h) = [chunk kc][row][8 BF16], ci = 16 h + 8 kc + e. Row of (channel c, part) comes from
-// row_of(c, part): part 0 = BF16(W), part 1 = BF16(W - BF16(W)). Then 64 FP32 biases.
+// Pack a conv 4x4 32->C layer W[c][ci][ky][kx], b[c] as B operands: blocks of [chunk kc][row][8
+// BF16], ci = 16 h + 8 kc + e, per (tap t = 4 ky + kx, K-half h) for the layers and per (column tap
+// kx, K-half h) for the head, whose row taps are stacked along the rows. Part 0 of a weight is
+// BF16(W), part 1 BF16(W - BF16(W)). Then 64 FP32 biases.
 template <bool HEAD>
 void fm_pack(const float* W, const float* b, int channels, std::vector<uint8_t>& out) {
     using C = FCfg<HEAD>;
@@ -411,8 +484,11 @@ void fm_pack(const float* W, const float* b, int channels, std::vector<uint8_t>&
                     const float w = W[((c * 32 + ci) * 4 + ky) * 4 + kx];
                     const uint16_t whi = bf16_bits_rn(w);
                     const uint16_t wlo = bf16_bits_rn(w - bf16_value(whi));
-                    const int rhi = c, rlo = HEAD ? 2 + c : 64 + c;
-                    uint8_t* blk = out.data() + (t * 2 + h) * C::kBlock + kc * C::N * 16;
+                    // layers: block (tap, K-half), rows c (hi) and 64 + c (lo); head: block (column
+                    // tap, K-half), rows 16 ky + c (hi) and 16 ky + 2 + c (lo)
+                    const int rhi = HEAD ? 16 * ky + c : c, rlo = HEAD ? 16 * ky + 2 + c : 64 + c;
+                    const int blk_i = HEAD ? kx * 2 + h : t * 2 + h;
+                    uint8_t* blk = out.data() + blk_i * C::kBlock + kc * C::kBRows * 16;
                     memcpy(blk + rhi * 16 + e * 2, &whi, 2);
                     memcpy(blk + rlo * 16 + e * 2, &wlo, 2);
                 }

@@ -199,5 +199,15 @@ __device__ __forceinline__ void tmem_st32_zero(uint32_t taddr) {
         : "memory");
 }
 
+// Zero 32 lanes x 4 consecutive 32-bit columns per warp, with its wait.
+__device__ __forceinline__ void tmem_st4_zero(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %1, %1, %1};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
 }  // namespace ptx
 }  // namespace mb
