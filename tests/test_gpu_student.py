@@ -91,6 +91,39 @@ def test_adam_first_step_matches_oracle(lib):
     net.close()
 
 
+def test_two_training_steps_match_oracle(lib):
+    """Two updates on one slice: from step 2 the Adam moments (of the centred layer-1 gradients)
+    enter the update, so this pins the moments' coordinates as well as the step."""
+    import torch
+    m = lib
+    p32 = synth.init_params(S, synth.STUDENT_WEIGHT_SEED, bias_std=0.05, centred_input=True)
+    net = make_net(S, m.MB_PREC_FP32, p32)
+    v = synth.em_volume(3005, 1, 40, 36)
+    tgt = np.random.default_rng(5).uniform(0.1, 0.9, size=v.shape).astype(np.float32)
+    cfg = m.train_cfg(batch=1, steps=2, lr=1e-3, seed=13)
+    m.mb_student_train(net.handle, torch.from_numpy(v).cuda(), torch.from_numpy(tgt).cuda(), 1, 40, 36, cfg)
+    w = np.empty(net.n_params, dtype=np.float32)
+    m.mb_get_weights(net.handle, w)
+    wr = p32.astype(np.float64)
+    mo = np.zeros(net.n_params)
+    vo = np.zeros(net.n_params)
+    for step in (1, 2):
+        # the FP32 GPU forward uses the FP32 weights, so the oracle takes them unrounded
+        _, g = oracle.student_loss_grad(S, wr.astype(np.float32), v, tgt)
+        if step == 1:
+            g1 = np.abs(oracle.centred_grad(S, g))
+        wr, mo, vo = oracle.student_adam_step(S, wr, mo, vo, g, step=step, lr=1e-3)
+    # The first step moves a parameter by about lr * sign(g): where the centred gradient is within
+    # the GPU gradient's tolerance (1e-4 of the largest) of zero its sign is not determined, and the
+    # parameter may legitimately land up to 2 lr per step away. Everywhere else: tight.
+    sure = g1 > 1e-3 * g1.max()
+    err = np.abs(w - wr)
+    assert err[sure].max() <= 2 * (2e-5 * 1e-3) + 2e-7, err[sure].max()
+    assert err.max() <= 4e-3 + 1e-6
+    assert sure.sum() >= 0.8 * net.n_params * (g1 > 0).mean()
+    net.close()
+
+
 def _train(m, prec, v, tgt, steps, seed, ckpt=None, ckpt_every=0, resume=0, batch=4, params=None):
     import torch
     net = make_net(S, prec, student_params() if params is None else params)
