@@ -300,10 +300,25 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
     auto fail = [&](cudaError_t e, const char* what) {
         rc = cuda_fail(e, what, __FILE__, __LINE__);
     };
-    const int64_t nslab = (z + slab - 1) / slab;
+    // Slab boundaries: with three or more slabs the first and the last are halved, so less of the
+    // first upload and of the last download stays outside the overlap.
+    std::vector<int64_t> zb{0};
+    {
+        const int64_t full = (z + slab - 1) / slab;
+        const int64_t half = (slab + 1) / 2;
+        if (full >= 3 && slab >= 2) {
+            zb.push_back(half);
+            while (zb.back() + slab < z - half) zb.push_back(zb.back() + slab);
+            if (z - zb.back() > slab) zb.push_back(z - half);
+        } else {
+            while (zb.back() + slab < z) zb.push_back(zb.back() + slab);
+        }
+        zb.push_back(z);
+    }
+    const int64_t nslab = (int64_t)zb.size() - 1;
     for (int64_t k = 0; k < nslab && rc == MB_OK; ++k) {
         const int b = (int)(k % NB);
-        const int64_t z0 = k * slab, nz = std::min<int64_t>(slab, z - z0);
+        const int64_t z0 = zb[(size_t)k], nz = zb[(size_t)k + 1] - z0;
         uint8_t* din = static_cast<uint8_t*>(net->slab_ws.ptr) + b * slab_bytes;
         uint8_t* dout = din + in_slice * slab;
         cudaError_t e = cudaSuccess;
