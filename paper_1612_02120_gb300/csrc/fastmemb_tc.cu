@@ -14,7 +14,12 @@
 // Weights are split W = W_hi + W_lo, both BF16 (W_lo = BF16(W - W_hi)), and stacked along N, so
 // each MMA applies both and the result carries BF16 activation rounding only:
 //   layers: N = 128, columns n (hi) and 64 + n (lo) of conv channel n
-//   head:   N = 16,  columns 0, 1 (hi of classes 0, 1) and 2, 3 (lo); the rest zero
+//   head:   16 columns per row tap ky: 0, 1 (hi of classes 0, 1) and 2, 3 (lo); the rest zero.
+//           The 4 row taps are stacked along N instead of issued per output row: staged row u is
+//           multiplied once per (kx, K-half) into the accumulators of output rows u .. u-3, a
+//           ring of 8 row accumulators (N = 16 x the taps that fall inside the item, split where
+//           the window wraps the ring); every head MMA accumulates, and the epilogue zeroes the 4
+//           used columns of a row's accumulator after draining it.
 //
 // Warp roles (512 threads, 1 CTA per SM, persistent over work items):
 //   warp 0      TMEM owner; lane 0 issues the MMAs (BF16 -> FP32 in TMEM)
