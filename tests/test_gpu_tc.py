@@ -135,18 +135,21 @@ def test_fp8_uncalibrated_is_not_ready():
 
 
 def test_host_streaming_over_several_slabs_equals_device_path():
-    """1024x1024x20 from pinned host buffers streams as slabs of 8, 8 and 4 slices (the third
-    reuses the first slab's buffers); the maps equal the device-resident call bitwise."""
+    """1024x1024x30 from pinned host buffers streams as slabs of 4, 8, 8, 6 and 4 slices (half-size
+    first and last slabs, a ragged one before the last; slabs alternate between two buffers and,
+    for this tensor-core net, two compute streams); the maps equal the device-resident call
+    bitwise."""
     import torch
     from paper_1612_02120_gb300 import build, membrane as m
     build.build()
     net = make_net(T, m.MB_PREC_BF16, teacher_params())
-    v = synth.em_volume(5100, 20, 1024, 1024)
+    z = 30
+    v = synth.em_volume(5100, z, 1024, 1024)
     dev = infer(net, v)
     pin_in = torch.from_numpy(v).pin_memory()
-    pin_out = torch.empty((20, 1024, 1024), dtype=torch.float32).pin_memory()
+    pin_out = torch.empty((z, 1024, 1024), dtype=torch.float32).pin_memory()
     for _ in range(2):  # the second call reuses the net's slab buffers, streams and events
         pin_out.fill_(-1.0)
-        m.mb_infer_volume(net.handle, pin_in, 20, 1024, 1024, pin_out)
+        m.mb_infer_volume(net.handle, pin_in, z, 1024, 1024, pin_out)
         np.testing.assert_array_equal(pin_out.numpy(), dev)
     net.close()
