@@ -199,8 +199,9 @@ mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t 
  * per work item (64 .. 1024) on a synthetic h x w x z workload on `stream`, keeps the fastest in
  * the net, and records it in the JSON cache at cache_path (HOST string, may be NULL) keyed on
  * GPU name, precision and shape. A cached entry is reused without timing. choice_out (HOST, may
- * be NULL) receives {rows_per_item, stages (the activation-ring depth, fixed), from_cache}.
- * Synchronous.
+ * be NULL) receives {rows_per_item, stages (the activation-ring depth, fixed), from_cache}. FP8
+ * nets split a launch's rows evenly over the CTAs instead (measured faster for FP8, slower for
+ * BF16): for them nothing is timed and rows_per_item is reported as 0. Synchronous.
  */
 mb_status mb_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path,
                       int32_t* choice_out, void* stream);

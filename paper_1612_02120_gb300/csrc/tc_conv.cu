@@ -57,6 +57,7 @@ struct TcBlockDesc {
     int h, w;               // source slice size (mirror padding range)
     int ry0, rx0, rh, rw;   // output region
     int z, n_strips, n_chunks, item_start;
+    int64_t row_start;      // FP8 split: first strip-row of the block in (block, slice, strip, row) order
 };
 
 // Per-channel constants, staged into shared memory at kernel start (floats):
@@ -69,6 +70,7 @@ struct TcParams {
     const uint8_t* wpack;   // global: packed B operands of layers 2 and 3, then the constants
     int* err;               // error word (MB_ERR_TIMEOUT on a timed-out wait)
     int n_blocks, n_items, rows_per_item, lag, out_u8;  // lag: unused (one issuer per layer)
+    int64_t total_rows;     // FP8 split: strip-rows of the launch
     int fault_stall;        // test injection: the input loader withholds its arrivals
     uint64_t wait_ns;       // limit of every device-side wait
     TcBlockDesc blk[kMaxBlocks];
@@ -171,6 +173,38 @@ __device__ __forceinline__ ItemInfo decode_item(const TcParams& p, int k) {
     it.y0 = chunk * p.rows_per_item;
     it.rows = min(p.rows_per_item, d.rh - it.y0);
     return it;
+}
+
+// Work split of the FP8 kernel: the launch's strip-rows, in (block, slice, strip, row) order, are
+// cut into one equal contiguous range per CTA, so every CTA computes the same number of rows and
+// no tail wave remains; a CTA's items are the parts of its range in one (block, slice, strip)
+// column. (The BF16 kernel walks round-robin items instead: measured 4.9 % faster for FP8 and
+// 1.4 % slower for BF16 on 1024x1024x32.) Every role of a CTA walks the same sequence.
+struct RangeIter {
+    int64_t r, hi;  // next strip-row, end of this CTA's range
+};
+
+__device__ __forceinline__ RangeIter range_begin(const TcParams& p) {
+    RangeIter s;
+    s.r = p.total_rows * (int64_t)blockIdx.x / gridDim.x;
+    s.hi = p.total_rows * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    return s;
+}
+
+__device__ __forceinline__ bool range_next(const TcParams& p, RangeIter& s, ItemInfo& it) {
+    if (s.r >= s.hi) return false;
+    int b = 0;
+    while (b + 1 < p.n_blocks && p.blk[b + 1].row_start <= s.r) ++b;
+    const TcBlockDesc& d = p.blk[b];
+    const int64_t off = s.r - d.row_start;
+    const int64_t col = off / d.rh;
+    it.b = b;
+    it.zi = (int)(col / d.n_strips);
+    it.x0 = (int)(col % d.n_strips) * kStrip;
+    it.y0 = (int)(off - col * d.rh);
+    it.rows = (int)min((int64_t)(d.rh - it.y0), s.hi - s.r);
+    s.r += it.rows;
+    return true;
 }
 
 // Pack 8 consecutive channels (BF16) or 16 (E4M3) of one pixel into a 16-byte ring row.
@@ -440,8 +474,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             auto wait_acc = [&](uint32_t qa) {
                 ok = ok && wait_phase(&afree[qa % C::kAcc], ((qa / C::kAcc) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
             };
-            for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-                const ItemInfo it = decode_item(p, k);
+            RangeIter range = range_begin(p);
+            ItemInfo it;
+            for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+                if constexpr (!FP8) it = decode_item(p, k);
                 const int NR = it.rows;
                 const int n_in = l2 ? NR + 9 : NR + 4;   // input rows of this layer
                 const int n_out = l2 ? NR + 5 : NR;      // output rows of this layer
@@ -486,8 +522,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         // requested before waiting for row u's ring slot, so one row's global latency overlaps the
         // wait and the conversion of the row before it.
         uint32_t in_seq = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const ItemInfo it = decode_item(p, k);
+        RangeIter range = range_begin(p);
+        ItemInfo it;
+        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!FP8) it = decode_item(p, k);
             const TcBlockDesc& d = p.blk[it.b];
             const uint8_t* src = d.in + (int64_t)it.zi * d.in_slice;
             const int nrows = it.rows + 14;
@@ -527,8 +565,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         float* stage = reinterpret_cast<float*>(smem + C::oSt2);
         uint32_t a2_seq = 0, m2_seq = 0;
         float prev[32];
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const ItemInfo it = decode_item(p, k);
+        RangeIter range = range_begin(p);
+        ItemInfo it;
+        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!FP8) it = decode_item(p, k);
             const int N2 = it.rows + 5;
             for (int j = 0; j < N2; ++j) {
                 const uint32_t q = a2_seq + j, s = q % C::kAcc;
@@ -575,8 +615,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         const int c = tid - 256;
         const int pw = warp - 8;
         uint32_t a3_seq = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const ItemInfo it = decode_item(p, k);
+        RangeIter range = range_begin(p);
+        ItemInfo it;
+        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!FP8) it = decode_item(p, k);
             const TcBlockDesc& d = p.blk[it.b];
             const int NR = it.rows;
             const bool col_ok = c < kStrip && it.x0 + c < d.rw;
@@ -615,8 +657,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         const int c0 = 4 * lane;
         uint32_t in_seq = 0, m1_seq = 0;
         float prev[4][8], cur[4][8];
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const ItemInfo it = decode_item(p, k);
+        RangeIter range = range_begin(p);
+        ItemInfo it;
+        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!FP8) it = decode_item(p, k);
             const int NR = it.rows;
             const int M1 = NR + 9;
             for (int t = -1; t < M1; ++t) {
@@ -901,7 +945,9 @@ static mb_status launch_tc(mb_net* net, TcParams& prm, cudaStream_t st) {
         MB_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     }
     const int smem = fp8 ? Cfg<true>::kSmem : Cfg<false>::kSmem;
-    const int grid = std::max(1, std::min(prm.n_items, g_num_sms));
+    // FP8 (even split of the rows): one CTA per SM, or fewer when a CTA would get under 64 rows
+    const int grid = fp8 ? (int)std::max<int64_t>(1, std::min<int64_t>(g_num_sms, (prm.total_rows + 63) / 64))
+                         : std::max(1, std::min(prm.n_items, g_num_sms));
     if (fp8) {
         static bool attr = false;
         if (!attr) {
@@ -927,6 +973,7 @@ static int fill_blocks(mb_net* net, TcParams& prm, const mb_block* blocks, int n
                        const int64_t* y0, const int64_t* x0, const int64_t* rows, const int64_t* cols,
                        mb_out_type ot) {
     int nb = 0, items = 0;
+    int64_t total = 0;
     // Rows per work item: the tuned value, unless the launch would not fill one wave of CTAs (a
     // streamed slab, a few small blocks). Then the candidates R, R/2, .. 64 are compared by the
     // predicted time, waves x (rows + 9) (each item restarts the layer-2 row pipeline, 9 extra
@@ -986,10 +1033,13 @@ static int fill_blocks(mb_net* net, TcParams& prm, const mb_block* blocks, int n
         d.n_chunks = (d.rh + R - 1) / R;
         d.item_start = items;
         items += d.z * d.n_strips * d.n_chunks;
+        d.row_start = total;
+        total += (int64_t)d.z * d.n_strips * d.rh;
         ++nb;
     }
     prm.n_blocks = nb;
     prm.n_items = items;
+    prm.total_rows = total;
     prm.rows_per_item = R;
     prm.lag = 0;
     prm.out_u8 = ot == MB_OUT_U8;
@@ -1156,6 +1206,15 @@ static void cache_store(const char* path, const std::string& key, int rows, int 
 
 mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path, int32_t* choice,
                       cudaStream_t st) {
+    if (net->prec == MB_PREC_FP8) {
+        // FP8 launches split their rows evenly over the CTAs: there is no item length to tune
+        if (choice) {
+            choice[0] = 0;
+            choice[1] = net->stages;
+            choice[2] = 0;
+        }
+        return MB_OK;
+    }
     int dev = 0;
     MB_CUDA(cudaGetDevice(&dev));
     const std::string key = tune_key(dev, net->prec, z, h, w);
