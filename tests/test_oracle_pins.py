@@ -283,3 +283,57 @@ def test_adam_constant_gradient_bias_correction():
         w, m, v = oracle.adam_step(w, m, v, g, step=t, lr=1e-2)
     expect = -5 * 1e-2 * g / (np.abs(g) + 1e-8)
     np.testing.assert_allclose(w, expect, rtol=1e-12)
+
+
+def _centred_student_loss(theta, imgs, tgt):
+    """The student written for the centred input x - 1/2 in plain numpy/scipy (no oracle code):
+    mirror pad 2 (reflect-101), conv3x3 1->16 + c1, ReLU, conv3x3 16->16 + b2, ReLU, 1x1 + bh,
+    sigmoid, mean squared error. theta uses the parameter layout with c1 in place of b1."""
+    from scipy.signal import correlate2d
+    W1 = theta[:144].reshape(16, 3, 3)
+    c1 = theta[144:160]
+    W2 = theta[160:2464].reshape(16, 16, 3, 3)
+    b2 = theta[2464:2480]
+    wh, bh = theta[2480:2496], theta[2496]
+    se, n = 0.0, 0
+    for img, t in zip(imgs, tgt):
+        x = np.pad(img.astype(np.float64) / 255.0 - 0.5, 2, mode="reflect")
+        h1 = np.stack([np.maximum(correlate2d(x, W1[c], mode="valid") + c1[c], 0.0) for c in range(16)])
+        h2 = np.stack([np.maximum(sum(correlate2d(h1[i], W2[c, i], mode="valid") for i in range(16)) + b2[c], 0.0)
+                       for c in range(16)])
+        p = 1.0 / (1.0 + np.exp(-(np.tensordot(wh, h2, axes=1) + bh)))
+        se += float(((p - t) ** 2).sum())
+        n += p.size
+    return se / n
+
+
+def test_centred_update_is_adam_on_the_centred_input_network():
+    """Two training updates of the stored network (oracle.student_adam_step) equal two plain Adam
+    steps on the network that takes x - 1/2 as input (gradients by central differences, numpy
+    only), mapped back by b1 = c1 - sum(W1)/2."""
+    rng = np.random.default_rng(11)
+    w = synth.init_params(S, synth.STUDENT_WEIGHT_SEED, bias_std=0.05, centred_input=True).astype(np.float64)
+    imgs = rng.integers(0, 256, size=(2, 5, 6), dtype=np.uint8)
+    tgt = rng.uniform(0.1, 0.9, size=(2, 5, 6))
+    th = oracle.centred_layer1(S, w)
+    assert abs(_centred_student_loss(th, imgs, tgt) - oracle.student_loss_grad(S, w, imgs, tgt)[0]) <= 1e-13
+    m = np.zeros(w.size)
+    v = np.zeros(w.size)
+    mc = np.zeros(w.size)
+    vc = np.zeros(w.size)
+    h = 1e-6
+    for step in (1, 2):  # from step 2 the moments enter
+        _, g = oracle.student_loss_grad(S, w, imgs, tgt)
+        w, m, v = oracle.student_adam_step(S, w, m, v, g, step=step, lr=1e-3)
+        gc = np.empty(th.size)
+        for i in range(th.size):
+            tp, tm = th.copy(), th.copy()
+            tp[i] += h
+            tm[i] -= h
+            gc[i] = (_centred_student_loss(tp, imgs, tgt) - _centred_student_loss(tm, imgs, tgt)) / (2 * h)
+        mc = 0.9 * mc + 0.1 * gc
+        vc = 0.999 * vc + 0.001 * gc * gc
+        th = th - 1e-3 * (mc / (1 - 0.9 ** step)) / (np.sqrt(vc / (1 - 0.999 ** step)) + 1e-8)
+    # differences of the order of the finite-difference error only (a wrong factor or sign in the
+    # change of coordinates moves parameters by ~lr = 1e-3)
+    assert np.abs(oracle.plain_layer1(S, th) - w).max() <= 2e-6
