@@ -65,7 +65,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms during a timed region."""
+    """nvidia-smi samples every 25 ms during a timed region. The region starts only once the
+    sampler has written its first sample (nvidia-smi takes a while to start), so that the samples
+    fall inside it."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,8 +82,13 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
+            self.f.flush()
+            self.skip = os.path.getsize(self.path)  # bytes written before the timed region
         except Exception:
             self.proc = None
         return self
@@ -98,9 +105,18 @@ class ClockSampler:
     def summary(self):
         if not self.proc or not self.path:
             return None
-        rows = [[p.strip() for p in line.split(",")] for line in open(self.path)]
-        rows = [r for r in rows if len(r) >= 9]
+        with open(self.path) as fh:
+            text = fh.read()
         os.unlink(self.path)
+        skip = min(getattr(self, "skip", 0), len(text))
+
+        def parse(t):
+            rows = [[p.strip() for p in line.split(",")] for line in t.splitlines()]
+            return [r for r in rows if len(r) >= 9]
+        rows = parse(text[skip:])
+        in_region = len(rows)
+        if not rows:  # a region shorter than one sampling interval: the sample taken just before it
+            rows = parse(text[:skip])
         if not rows:
             return None
 
@@ -114,7 +130,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": in_region}
 
 
 def cpu_cores():
