@@ -222,7 +222,8 @@ mb_status mb_student_loss_grad(mb_net* student, const uint8_t* in, const float* 
  * (the same network written for the input x - 1/2, a standard preconditioning of gradient
  * training); the weights stay stored for x = u/255, and m, v hold the centred moments.
  * loss_curve (HOST, may be NULL) receives one loss per step run. With ckpt_path (HOST string,
- * may be NULL), a checkpoint {step, master weights, m, v, sampler state} is written every
+ * may be NULL), a checkpoint {step, master weights, m, v, sampler state} (format version 2: m and
+ * v of the centred coordinates) is written every
  * cfg->ckpt_every steps; with cfg->resume the run continues from it, bitwise as if never
  * interrupted. Synchronous.
  */

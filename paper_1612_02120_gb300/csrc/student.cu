@@ -505,7 +505,7 @@ mb_status student_loss_grad(mb_net* s, const uint8_t* in, const float* tgt, int6
 
 // ---- checkpoint file: header + master weights + m + v ------------------------------------------
 struct CkptHeader {
-    char magic[8];      // "MBCKPT01"
+    char magic[8];      // "MBCKPT02": m and v are the moments of the centred layer-1 coordinates
     int64_t step;       // optimiser steps completed
     int64_t n_params;
     uint64_t sampler;   // SplitMix64 state after the last completed step
@@ -545,7 +545,7 @@ static bool read_ckpt(const char* path, CkptHeader& hd, std::vector<float>& buf)
     FILE* f = fopen(path, "rb");
     if (!f) return false;
     buf.resize(3 * (size_t)kSN);
-    bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "MBCKPT01", 8) == 0 && hd.n_params == kSN &&
+    bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "MBCKPT02", 8) == 0 && hd.n_params == kSN &&
               fread(buf.data(), 4, buf.size(), f) == buf.size();
     fclose(f);
     return ok;
@@ -558,7 +558,7 @@ mb_status student_train(mb_net* s, const uint8_t* in, const float* tgt, int64_t 
     MB_TRY(ensure_bufs(s, B, h, w, cfg->steps, b));
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, "MBCKPT01", 8);
+    memcpy(hd.magic, "MBCKPT02", 8);
     hd.n_params = kSN;
     hd.seed = cfg->seed;
     hd.sampler = cfg->seed ^ 0x5A17E5EEDULL;
