@@ -225,7 +225,9 @@ mb_status mb_student_loss_grad(mb_net* student, const uint8_t* in, const float* 
  * may be NULL), a checkpoint {step, master weights, m, v, sampler state} (format version 2: m and
  * v of the centred coordinates) is written every
  * cfg->ckpt_every steps; with cfg->resume the run continues from it, bitwise as if never
- * interrupted. Synchronous.
+ * interrupted. With cfg->resume and no file at ckpt_path the run starts fresh; a file there that
+ * is not a complete format-2 checkpoint of this student returns MB_ERR_INVALID_ARG before any
+ * step and leaves the file unchanged. Synchronous.
  */
 mb_status mb_student_train(mb_net* student, const uint8_t* in, const float* target, int64_t n, int64_t h,
                            int64_t w, const mb_train_cfg* cfg, const char* ckpt_path, float* loss_curve,
@@ -252,8 +254,11 @@ mb_status mb_infer_cascade(mb_net* student, mb_net* teacher, const uint8_t* in, 
  * FP32 teacher nets only; device pointers in[z][h][w] -> out[z][h][w] (float32 or uint8 as in
  * mb_infer_volume); asynchronous on `stream`.
  * Scratch: a fixed 64 MiB array in the library's device memory, held by every GPU that loads the
- * library until exit. Slices are processed in row bands that fit it; a width needing more than
- * 64 MiB for a single-row band (w > 30,832) returns MB_ERR_SHAPE. The first call on each
+ * library until exit. A band of r output rows of n slices needs
+ * n * ((r + 10)(w + 10) + (r + 5)(w + 5)) * 32 floats of it; slices are processed in the largest
+ * row band that fits (all h rows if they fit), as many slices of that band per launch sequence as
+ * fit, three kernel launches per band. A width needing more than 64 MiB for a single-row band
+ * (w > 30,832), or h or w above 2^20, returns MB_ERR_SHAPE. The first call on each
  * device looks up the array's device address; make that first call before any stream capture.
  * All calls on a device share the array: calls that overlap on the GPU (other streams or host
  * threads) race and must be serialised by the caller. Nothing in the array needs clearing.

@@ -48,7 +48,10 @@ static mb_status noalloc_scratch(int dev, float** out) {
     return MB_OK;
 }
 
-// Scratch floats for `nz` slices of a band of `rows` output rows and `cols` columns.
+// Scratch floats for `nz` slices of a band of `rows` output rows and `cols` columns: the layer-1
+// activations (rows + 10) x (cols + 10) and the layer-2 activations (rows + 5) x (cols + 5), 32
+// channels each. A call uses the largest band of a slice that fits (all h rows if they do), then
+// as many slices of that band per launch as fit.
 static size_t band_floats(int64_t nz, int64_t rows, int64_t cols) {
     return (size_t)nz * (size_t)((rows + 10) * (cols + 10) + (rows + 5) * (cols + 5)) * 32;
 }
@@ -149,6 +152,10 @@ extern "C" mb_status mb_infer_volume_noalloc(mb_net* net, const uint8_t* in, int
         set_error("mb_infer_volume_noalloc: bad volume %lldx%lldx%lld (slices need h, w >= 8)", (long long)z,
                   (long long)h, (long long)w);
         return z < 0 ? MB_ERR_INVALID_ARG : MB_ERR_SHAPE;
+    }
+    if (h > (1 << 20) || w > (1 << 20)) {
+        set_error("mb_infer_volume_noalloc: slice %lldx%lld exceeds 2^20 per side", (long long)h, (long long)w);
+        return MB_ERR_SHAPE;
     }
     const size_t cap = kNoAllocScratchBytes / sizeof(float);
     if (band_floats(1, 1, w) > cap) {

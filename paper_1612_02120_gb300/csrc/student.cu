@@ -17,6 +17,7 @@
 // BF16 for BF16 students.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <errno.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -541,14 +542,24 @@ static mb_status write_ckpt(const char* path, const CkptHeader& hd, const float*
     return MB_OK;
 }
 
-static bool read_ckpt(const char* path, CkptHeader& hd, std::vector<float>& buf) {
+// Result of looking for a checkpoint to resume from.
+enum class CkptRead { kAbsent, kOk, kInvalid };
+
+// A file that does not exist means a fresh start; a file that exists but is not a complete
+// checkpoint of this format (another version, another parameter count, truncated) is an error,
+// so that a later checkpoint write never overwrites a file the caller meant to resume from.
+static CkptRead read_ckpt(const char* path, CkptHeader& hd, std::vector<float>& buf) {
     FILE* f = fopen(path, "rb");
-    if (!f) return false;
+    if (!f) return errno == ENOENT ? CkptRead::kAbsent : CkptRead::kInvalid;
     buf.resize(3 * (size_t)kSN);
     bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "MBCKPT02", 8) == 0 && hd.n_params == kSN &&
               fread(buf.data(), 4, buf.size(), f) == buf.size();
+    if (ok) {
+        char extra;
+        ok = fread(&extra, 1, 1, f) == 0;  // nothing after the moments
+    }
     fclose(f);
-    return ok;
+    return ok ? CkptRead::kOk : CkptRead::kInvalid;
 }
 
 mb_status student_train(mb_net* s, const uint8_t* in, const float* tgt, int64_t n, int64_t h, int64_t w,
@@ -564,7 +575,14 @@ mb_status student_train(mb_net* s, const uint8_t* in, const float* tgt, int64_t 
     hd.sampler = cfg->seed ^ 0x5A17E5EEDULL;
     int64_t start = 0;
     std::vector<float> buf;
-    if (ckpt && cfg->resume && read_ckpt(ckpt, hd, buf)) {
+    const CkptRead found = (ckpt && cfg->resume) ? read_ckpt(ckpt, hd, buf) : CkptRead::kAbsent;
+    if (found == CkptRead::kInvalid) {
+        set_error("checkpoint %s exists but is not a format-2 checkpoint of this student (version, parameter "
+                  "count or size); it was left unchanged",
+                  ckpt);
+        return MB_ERR_INVALID_ARG;
+    }
+    if (found == CkptRead::kOk) {
         if (hd.seed != cfg->seed || hd.step > cfg->steps) {
             set_error("checkpoint %s does not match this run (seed or step count)", ckpt);
             return MB_ERR_INVALID_ARG;

@@ -1,18 +1,19 @@
-"""Small, fixed inference case for profilers: `reps` launches of one path on a z x h x w synthetic
-volume (the generator of `synth`), so a capture of one kernel stays a few hundred MB on the device.
+"""Bench helper, not part of the library: small, fixed inference cases for profilers (ncu
+captures of one kernel). `reps` launches of one path on a z x h x w synthetic volume (the
+generator of `synth`), so a capture of one kernel stays a few hundred MB on the device.
 
-    python -m paper_1612_02120_gb300.profile_case --prec bf16 --z 4 --h 1024 --w 1024 --reps 3
-    python -m paper_1612_02120_gb300.profile_case --net fastmemb --prec bf16 --z 4 --reps 3
-    python -m paper_1612_02120_gb300.profile_case --net maskextend --prec fp16 --z 4 --h 512 --w 512
+    python profile_case.py --prec bf16 --z 4 --h 1024 --w 1024 --reps 3
+    python profile_case.py --net fastmemb --prec bf16 --z 4 --reps 3
+    python profile_case.py --net maskextend --prec fp16 --z 4 --h 512 --w 512
       (MaskExtend: `z` transfer steps on an h x w window per rep)
-    python -m paper_1612_02120_gb300.profile_case --net student-train --z 64 --h 512 --w 512 --reps 4
+    python profile_case.py --net student-train --z 64 --h 512 --w 512 --reps 4
       (student training: `reps` optimiser steps, batch 32, on z slices with FP32 teacher targets)
 """
 import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -174,6 +174,27 @@ def test_resume_from_checkpoint_is_bitwise_identical(lib, small_data, tmp_path):
         n.close()
 
 
+def test_resume_rejects_a_checkpoint_of_another_format(lib, small_data, tmp_path):
+    """A file at the checkpoint path that is not a format-2 checkpoint of this student (an older
+    version, or a truncated file) is an error, and the file is left as it was."""
+    m = lib
+    v, tgt = small_data
+    import struct
+    for name, blob in (("v1.ckpt", b"MBCKPT01" + struct.pack("<qqqq", 10, 0, 6, 0) + bytes(64)),
+                       ("short.ckpt", b"MBCKPT02" + bytes(40))):
+        ck = tmp_path / name
+        ck.write_bytes(blob)
+        with pytest.raises(m.MembraneError) as e:
+            _train(m, m.MB_PREC_BF16, v, tgt, 4, seed=6, ckpt=str(ck), ckpt_every=2, resume=1)
+        assert e.value.status == m.MB_ERR_INVALID_ARG
+        assert ck.read_bytes() == blob
+    # without resume, or with no file at the path, training starts fresh
+    fresh = tmp_path / "absent.ckpt"
+    net, _, _ = _train(m, m.MB_PREC_BF16, v, tgt, 2, seed=6, ckpt=str(fresh), ckpt_every=2, resume=1)
+    assert fresh.exists()
+    net.close()
+
+
 def test_training_gains_over_untrained_student(lib, small_data):
     """What the trained network gains: its error against the teacher drops well below the
     untrained student's, on held-out slices."""

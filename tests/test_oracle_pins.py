@@ -337,3 +337,43 @@ def test_centred_update_is_adam_on_the_centred_input_network():
     # differences of the order of the finite-difference error only (a wrong factor or sign in the
     # change of coordinates moves parameters by ~lr = 1e-3)
     assert np.abs(oracle.plain_layer1(S, th) - w).max() <= 2e-6
+
+
+def _numpy_teacher_maxfilter_maps(params, slice_u8, y0, x0, h, w):
+    """The stand-in teacher up to its second max-filter, written with numpy and scipy only: the
+    region's 7-px context (numpy 'reflect' = reflect-101 at the slice borders), scipy correlation
+    per channel pair, ReLU, and numpy sliding 2x2 maxima."""
+    signal = pytest.importorskip("scipy.signal")
+    (W1, b1), (W2, b2) = split_params(T, params)[:2]
+    xp = np.pad(slice_u8.astype(np.float64) / 255.0, 7, mode="reflect")[y0:y0 + h + 14, x0:x0 + w + 14]
+
+    def conv_relu(x, W, b):
+        return np.maximum(np.stack([b[co] + sum(signal.correlate2d(x[ci], W[co, ci], mode="valid")
+                                                for ci in range(W.shape[1])) for co in range(W.shape[0])]), 0.0)
+
+    def maxf(x):
+        return np.lib.stride_tricks.sliding_window_view(x, (2, 2), axis=(1, 2)).max(axis=(-1, -2))
+
+    m1 = maxf(conv_relu(xp[None], W1, b1))
+    m2 = maxf(conv_relu(m1, W2, b2))
+    return m1, m2
+
+
+@pytest.mark.parametrize("region", [None, (5, 9, 14, 17)])
+def test_maxfilter_amax_matches_numpy_chain(region):
+    """The FP8 calibration statistic (per-channel maximum after the first and after the second
+    max-filter, over the whole padded extent the layers compute) equals an independent numpy
+    evaluation: row m of the result is the m-th max-filter and column c its channel c. Pins the
+    layer chain (the second maxima depend on the first max-filter's output) and the m * C + c
+    indexing, for the whole slice and for a region with true context."""
+    params = teacher_params()
+    sl = synth.em_volume(synth.BASE_SEED + 11, 1, 26, 31)[0]
+    y0, x0, h, w = region if region else (0, 0, 26, 31)
+    got = oracle.maxfilter_amax(T, params, sl, y0, x0, h, w)
+    m1, m2 = _numpy_teacher_maxfilter_maps(params, sl, y0, x0, h, w)
+    assert got.shape == (2, 32)
+    assert m1.shape[1:] == (h + 9, w + 9) and m2.shape[1:] == (h + 4, w + 4)
+    np.testing.assert_allclose(got[0], m1.reshape(32, -1).max(axis=1), rtol=1e-12, atol=0)
+    np.testing.assert_allclose(got[1], m2.reshape(32, -1).max(axis=1), rtol=1e-12, atol=0)
+    # the channels differ from one another, so a permuted or transposed result would not pass
+    assert np.unique(np.round(got, 9)).size >= 40
