@@ -13,6 +13,9 @@ the same through the C ABI with pinned HOST buffers (copies inside the timed reg
         memory; errors on 3 seeded 512x512 crops (true context);
   cfg4  student training (200 x 512^2, batch 32, lr 1e-3, 2000 steps) on FP32-teacher maps, then
         student-only and cascade (teacher fallback on 256^2 tiles) on the cfg3 volume;
+  cfg8  the second teacher workload: the stand-in with its head fitted to the generator's membrane
+        truth (a map that straddles 0.5): FP32/BF16/FP8 errors and accuracy against the truth, a
+        student distilled from it, and the cascade under the stated rule on the cfg3 volume;
   cfg6  FastMemb_3nm (one more stage, 109 field of view) on 2048x2048x8 (3 nm images), FP32 and
         BF16, dense and sub-sampled by 2 (a 6 nm output map), errors on 2 seeded 256x256 crops;
   cfg7  MaskExtend (Sec. 3.2): the +z transfer recursion on a 512x512 window for 16 sections
@@ -228,6 +231,30 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "Mvox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def truth_head_fixture():
+    with open(os.path.join(ROOT, "tests", "golden", "truth_head.json")) as f:
+        return json.load(f)
+
+
+def truth_head_params(params):
+    """The second teacher workload: the stand-in's layers 1-3 with the head fitted to the
+    generator's membrane truth (a stored fixture written from the FP64 oracle's features)."""
+    import numpy as np
+    fx = truth_head_fixture()
+    p = np.array(params, dtype=np.float32, copy=True)
+    p[-33:-1] = np.asarray(fx["head_w"], dtype=np.float32)
+    p[-1] = np.float32(fx["head_b"])
+    return p
+
+
+def truth_accuracy(maps, truths):
+    """Fraction of pixels where (p >= 0.5) equals the generator's membrane flag."""
+    import numpy as np
+    a = np.concatenate([np.asarray(m).ravel() >= 0.5 for m in maps])
+    t = np.concatenate([np.asarray(x).ravel() > 0 for x in truths])
+    return float((a == t).mean())
+
+
 def max_over_ranks(x, dist, device="cuda"):
     """This rank's time -> the maximum over all ranks (the whole job finishes with its slowest
     rank); unchanged on a single process."""
@@ -278,7 +305,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--configs", default="1,2,3,4,5,6,7", help="extra configurations measured after the headline")
+    ap.add_argument("--configs", default="1,2,3,4,8,5,6,7", help="extra configurations measured after the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -433,7 +460,7 @@ def main():
 
     # ---- cfg3: 4096x4096x64, FP8 and BF16, resident and streamed --------------------------------
     big = None
-    if "3" in configs or "4" in configs:
+    if "3" in configs or "4" in configs or "8" in configs:
         Z3, H3, W3 = 64, 4096, 4096
         big = torch.empty((Z3, H3, W3), dtype=torch.uint8, pin_memory=True)
         synth.em_volume(synth.BASE_SEED + 3, Z3, H3, W3, out=big.numpy())
@@ -538,6 +565,92 @@ def main():
         student.close()
         untrained.close()
         teacher.close()
+    # ---- cfg8: the second teacher workload, a head fitted to the generator's membrane truth ------
+    if "8" in configs:
+        tparams = truth_head_params(params)
+        p8 = {"head": "stand-in layers 1-3, head fitted to the generator's membrane flag (L2 logistic "
+                      "regression, held-out accuracy %.4f)" % truth_head_fixture()["held_out_accuracy"]}
+        zs = [int(z) for z in np.random.default_rng(synth.BASE_SEED + 8).choice(Z, 2, replace=False)]
+        truth = [synth.em_slice_truth(synth.slice_seed(synth.BASE_SEED + 1, 0, z), H, W)[1] for z in zs]
+        refs = [oracle.forward_region(synth.TEACHER, tparams, vol[z]) for z in zs]
+        p8["oracle_accuracy_vs_truth"] = truth_accuracy(refs, truth)
+        t_ms = {}
+        for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16), ("fp8", m.MB_PREC_FP8)):
+            n8 = m.Net(synth.TEACHER, prec, local, tparams)
+            if prec == m.MB_PREC_FP8:
+                m.mb_calibrate_fp8(n8.handle, x[:4], 4, H, W, stream=stream)
+            k, w0 = (3, 1) if prec == m.MB_PREC_FP32 else (args.steps, 3)
+            with torch.cuda.stream(stream):
+                ms = time_device(lambda: m.mb_infer_volume(n8.handle, x, Z, H, W, out, m.MB_OUT_F32, stream), k, w0,
+                                 stream, flush)
+            got = [out[z].cpu().numpy() for z in zs]
+            t_ms[name] = statistics.mean(ms)
+            p8[name] = {"mvox_s": vox / (t_ms[name] / 1e3) / 1e6, "error": err_metrics(got, refs, TOL[name]),
+                        "accuracy_vs_truth": truth_accuracy(got, truth)}
+            n8.close()
+        p8["slices_1024"] = zs
+        # the student distilled from this teacher's FP32 maps (the configuration's training recipe)
+        n_tr, s_tr = 200, 512
+        tv = torch.from_numpy(synth.em_volume(synth.BASE_SEED + 4, n_tr, s_tr, s_tr)).cuda()
+        tgt = torch.empty((n_tr, s_tr, s_tr), dtype=torch.float32, device="cuda")
+        with m.Net(synth.TEACHER, m.MB_PREC_FP32, local, tparams) as t32:
+            m.mb_infer_volume(t32.handle, tv, n_tr, s_tr, s_tr, tgt)
+        sp = synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0, centred_input=True)
+        student = m.Net(synth.STUDENT, m.MB_PREC_BF16, local, sp)
+        curve = np.zeros(2000, dtype=np.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.mb_student_train(student.handle, tv, tgt, n_tr, s_tr, s_tr,
+                           m.train_cfg(batch=32, steps=2000, lr=1e-3, seed=synth.BASE_SEED + 4), None, curve)
+        p8["train"] = {"seconds": time.perf_counter() - t0, "loss_first10": float(curve[:10].mean()),
+                       "loss_last10": float(curve[-10:].mean())}
+        del tv, tgt
+        Z3, H3, W3 = 64, 4096, 4096
+        v3 = Z3 * H3 * W3
+        c_truth = [synth.em_slice_truth(synth.slice_seed(synth.BASE_SEED + 3, 0, z), H3, W3)[1][y:y + 512, x0:x0 + 512]
+                   for z, y, x0 in crops]
+        c_refs = [oracle.forward_region(synth.TEACHER, tparams, big[z].numpy(), y, x0, 512, 512) for z, y, x0 in crops]
+
+        def crops_of(t):
+            return [t[z, y:y + 512, x0:x0 + 512].cpu().numpy() for z, y, x0 in crops]
+        teacher = m.Net(synth.TEACHER, m.MB_PREC_BF16, local, tparams)
+        m.mb_autotune(teacher.handle, 4, H3, W3, tune_cache, stream)
+        with torch.cuda.stream(stream):
+            ms_t = time_device(lambda: m.mb_infer_volume(teacher.handle, xb, Z3, H3, W3, ob, m.MB_OUT_F32, stream),
+                               3, 1, stream, flush)
+        t_map = crops_of(ob)
+        with torch.cuda.stream(stream):
+            ms_s = time_device(lambda: m.mb_infer_volume(student.handle, xb, Z3, H3, W3, ob, m.MB_OUT_F32, stream),
+                               3, 1, stream, flush)
+        s_map = crops_of(ob)
+        teacher_mvox = v3 / (statistics.mean(ms_t) / 1e3) / 1e6
+        p8["teacher_bf16_4096x4096x64_mvox_s"] = teacher_mvox
+        p8["student_only"] = {"mvox_s": v3 / (statistics.mean(ms_s) / 1e3) / 1e6,
+                              "vs_teacher": err_metrics(s_map, t_map, TOL["student"]),
+                              "vs_oracle": err_metrics(s_map, c_refs, TOL["student"]),
+                              "accuracy_vs_truth": truth_accuracy(s_map, c_truth),
+                              "ambiguous_fraction": float(np.mean([((a >= 0.3) & (a <= 0.7)).mean() for a in s_map]))}
+        p8["teacher_bf16_crops"] = {"vs_oracle": err_metrics(t_map, c_refs, TOL["bf16"]),
+                                    "accuracy_vs_truth": truth_accuracy(t_map, c_truth)}
+        p8["oracle_crops_accuracy_vs_truth"] = truth_accuracy(c_refs, c_truth)
+        casc = []
+        for lo, hi, frac in ((0.3, 0.7, 0.05), (0.3, 0.7, 0.02), (0.3, 0.7, 0.1), (0.1, 0.9, 0.05)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rate = m.mb_infer_cascade(student.handle, teacher.handle, xb, Z3, H3, W3, ob, 256, lo, hi, frac,
+                                      stream=stream)
+            dt = time.perf_counter() - t0
+            c_map = crops_of(ob)
+            casc.append({"band": [lo, hi], "tile": 256, "max_frac": frac, "stated_rule": (lo, hi, frac) == (0.3, 0.7, 0.05),
+                         "fallback_rate": rate, "mvox_s": v3 / dt / 1e6, "speedup_vs_teacher": v3 / dt / 1e6 / teacher_mvox,
+                         "vs_teacher": err_metrics(c_map, t_map, TOL["student"]),
+                         "vs_oracle": err_metrics(c_map, c_refs, TOL["student"]),
+                         "accuracy_vs_truth": truth_accuracy(c_map, c_truth)})
+        p8["cascade"] = casc
+        p8["crops"] = crops
+        student.close()
+        teacher.close()
+        paths["cfg8_truth_head_teacher"] = p8
     # ---- cfg5: FastMemb dense form on the cfg1 volume ------------------------------------------------
     if "5" in configs:
         fm_params = synth.init_params(synth.FASTMEMB, synth.FASTMEMB_WEIGHT_SEED)

@@ -259,6 +259,32 @@ def patch_pixel(layers, params, slice_u8, i, j) -> float:
     return float(out[0])
 
 
+def features(layers, params, slice_u8, y0=0, x0=0, h=None, w=None) -> np.ndarray:
+    """Activations entering the head of a conv / max-filter stack ([C][h][w], FP64) for the region
+    [y0, y0+h) x [x0, x0+w) of one slice: the mirror-padded input through every layer but the
+    last, composed from this module's conv and max-filter (dilation 1, no max-out)."""
+    s = _u8(slice_u8)
+    H, W = s.shape
+    h = H - y0 if h is None else h
+    w = W - x0 if w is None else w
+    R = net_radius(layers)
+    x = pad_region(s, y0, x0, h, w, R)[None]
+    prm = _f64(params)
+    o = 0
+    for layer in layers[:-1]:
+        kind, k, cin, cout = (int(v) for v in layer[:4])
+        assert (len(layer) < 6 or int(layer[5]) == 1) and (len(layer) < 7 or int(layer[6]) == 1), layer
+        if kind == CONV:
+            nw = cout * cin * k * k
+            x = conv(x, prm[o:o + nw].reshape(cout, cin, k, k), prm[o + nw:o + nw + cout], bool(layer[4]))
+            o += nw + cout
+        elif kind == MAXF:
+            x = maxfilter2(x)
+        else:
+            raise ValueError(f"features: layer kind {kind} before the head")
+    return x
+
+
 def maxfilter_amax(layers, params, slice_u8, y0=0, x0=0, h=None, w=None, n_maxf=2, channels=32):
     d, prm, s = _desc(layers), _f64(params), _u8(slice_u8)
     H, W = s.shape

@@ -116,11 +116,12 @@ def _load():
             lib.synth_slice_seed.argtypes = [u64, u64, u64]
             lib.synth_slice_seed.restype = u64
             lib.synth_em_slice.argtypes = [u64, i64, i64, i64, p, i64]
+            lib.synth_em_slice_truth.argtypes = [u64, i64, i64, i64, p, i64, p]
             lib.synth_em_volume.argtypes = [u64, u64, i64, i64, i64, i64, p, i64, i64]
             lib.synth_he_normal.argtypes = [u64, i64, i64, p, i64, p, ctypes.c_double]
             lib.synth_uniform_ints.argtypes = [u64, i64, i64, i64, p]
             lib.synth_uniform_floats.argtypes = [u64, i64, ctypes.c_double, ctypes.c_double, p]
-            for f in ("synth_em_slice", "synth_em_volume", "synth_he_normal", "synth_uniform_ints",
+            for f in ("synth_em_slice", "synth_em_slice_truth", "synth_em_volume", "synth_he_normal", "synth_uniform_ints",
                       "synth_uniform_floats"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
@@ -144,6 +145,15 @@ def em_slice(seed: int, h: int, w: int, n_cells: int = 0) -> np.ndarray:
     out = np.empty((h, w), dtype=np.uint8)
     _check(_load().synth_em_slice(seed, h, w, n_cells, out.ctypes.data, w), "synth_em_slice")
     return out
+
+
+def em_slice_truth(seed: int, h: int, w: int, n_cells: int = 0):
+    """(slice, truth): em_slice(seed, h, w) and the generator's membrane flag per pixel (0/1)."""
+    out = np.empty((h, w), dtype=np.uint8)
+    truth = np.empty((h, w), dtype=np.uint8)
+    _check(_load().synth_em_slice_truth(seed, h, w, n_cells, out.ctypes.data, w, truth.ctypes.data),
+           "synth_em_slice_truth")
+    return out, truth
 
 
 def em_volume(base: int, z: int, h: int, w: int, block: int = 0, n_cells: int = 0,

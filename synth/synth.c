@@ -79,8 +79,11 @@ uint64_t synth_slice_seed(uint64_t base, uint64_t block, uint64_t z) {
 /*
  * One EM-like slice. out[y * pitch + x], 0 <= y < h, 0 <= x < w.
  * n_cells <= 0 selects the default density. Needs h, w >= 4 (blur radius 3).
+ * truth (may be NULL): the generator's own membrane flag of step 3 per pixel (0/1, same layout),
+ * i.e. the ground truth a membrane classifier is meant to recover.
  */
-int synth_em_slice(uint64_t seed, int64_t h, int64_t w, int64_t n_cells, uint8_t* out, int64_t pitch) {
+int synth_em_slice_truth(uint64_t seed, int64_t h, int64_t w, int64_t n_cells, uint8_t* out, int64_t pitch,
+                         uint8_t* truth) {
     if (!out || h < 4 || w < 4 || pitch < w) return SYNTH_ERR_ARG;
     int64_t n = n_cells > 0 ? n_cells : synth_default_cells(h, w);
     if (n < 2) n = 2;
@@ -166,6 +169,7 @@ int synth_em_slice(uint64_t seed, int64_t h, int64_t w, int64_t n_cells, uint8_t
             uint64_t lo = (uint64_t)(i1 < i2 ? i1 : i2), hi = (uint64_t)(i1 < i2 ? i2 : i1);
             double width = 2.0 + u01(mix64(width_key ^ (lo * 0x9E3779B97F4A7C15ULL) ^ (hi << 21) ^ hi));
             int membrane = dist < 0.5 * width;
+            if (truth) truth[y * pitch + x] = (uint8_t)membrane;
             uint64_t ctr = noise_key + 2ULL * (uint64_t)(y * w + x);
             double z = box_muller(mix64(ctr), mix64(ctr + 1ULL));
             img[y * w + x] = membrane ? 60.0 + 15.0 * z : 170.0 + 20.0 * z;
@@ -196,6 +200,10 @@ int synth_em_slice(uint64_t seed, int64_t h, int64_t w, int64_t n_cells, uint8_t
 
     free(px); free(py); free(img); free(tmp); free(bstart); free(bitems); free(bfill);
     return SYNTH_OK;
+}
+
+int synth_em_slice(uint64_t seed, int64_t h, int64_t w, int64_t n_cells, uint8_t* out, int64_t pitch) {
+    return synth_em_slice_truth(seed, h, w, n_cells, out, pitch, NULL);
 }
 
 /* z slices of one block; slice zi uses synth_slice_seed(base, block, zi). */

@@ -19,6 +19,19 @@ def teacher_params():
     return synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED)
 
 
+def truth_head_teacher_params():
+    """The second teacher workload: the stand-in teacher with its head fitted to the generator's
+    membrane truth (tests/golden/truth_head.json, written by fit_truth_head.py from the oracle)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "truth_head.json")) as f:
+        fx = json.load(f)
+    p = teacher_params().copy()
+    p[-33:-1] = np.asarray(fx["head_w"], dtype=np.float32)
+    p[-1] = np.float32(fx["head_b"])
+    return p
+
+
 def student_params():
     return synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED, bias_std=0.0, centred_input=True)
 

@@ -377,3 +377,28 @@ def test_maxfilter_amax_matches_numpy_chain(region):
     np.testing.assert_allclose(got[1], m2.reshape(32, -1).max(axis=1), rtol=1e-12, atol=0)
     # the channels differ from one another, so a permuted or transposed result would not pass
     assert np.unique(np.round(got, 9)).size >= 40
+
+
+def test_truth_head_fixture_is_a_membrane_classifier():
+    """The second teacher workload's head (tests/golden/truth_head.json) recovers the generator's
+    own membrane flag on a slice it was not fitted or selected on: well above the 82 % that a
+    constant 'no membrane' answer scores, with about the true membrane fraction marked; and its
+    regularisation strength follows the stated rule from the recorded held-out accuracies."""
+    import json
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from _common import truth_head_teacher_params
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "truth_head.json")) as f:
+        fx = json.load(f)
+    accs = {float(k): v for k, v in fx["held_out_accuracy_by_lambda"].items()}
+    best = max(accs.values())
+    assert fx["lambda"] == max(lam for lam, a in accs.items() if a >= best - 1e-3)
+    p = truth_head_teacher_params()
+    s, truth = synth.em_slice_truth(synth.slice_seed(synth.BASE_SEED + 23, 0, 0), 192, 192)
+    prob = oracle.forward_region(T, p, s)
+    acc = ((prob >= 0.5) == (truth > 0)).mean()
+    assert acc >= 0.95, acc
+    assert abs((prob >= 0.5).mean() - truth.mean()) < 0.03
+    # the map straddles the decision threshold: confident on most pixels, ambiguous on a few
+    assert ((prob >= 0.3) & (prob <= 0.7)).mean() < 0.1 and (prob < 0.05).mean() > 0.5
