@@ -297,6 +297,22 @@ mb_status mb_mask_extend(mb_net* net, const uint8_t* em, const float* membrane, 
                          const uint8_t* seed_masks, int64_t z0, int64_t n_steps, float threshold, uint8_t* masks_out,
                          float* probs_out, void* stream);
 
+/*
+ * The MaskExtend recursion in either direction (Sec. 3.2: the algorithm continues iteratively in
+ * z+ or z-). direction = +1 is mb_mask_extend. direction = -1 mirrors every offset of the transfer
+ * equation: for z = z0, z0-1, .., z0-n_steps+1,
+ *   Mask_z = J(CNN(Mask_{z+4..z+1}, EM_{z+1..z-1}, FastMemb_{z+2..z-2}))
+ * (the same 12-channel order, each map taken at the mirrored section), which is the z+ recursion of
+ * the stack read backwards. seed_masks[i] is the mask of section z0 + direction (i - 4), i.e. the
+ * four sections before z0 along the direction of travel (z0+4 .. z0+1 for -1). masks_out[s] and
+ * probs_out[s] belong to step s, section z0 + direction s. Needs the sections read,
+ * z0-2 .. z0+n_steps+1 (+1) or z0-n_steps-1 .. z0+2 (-1), inside the stack (else MB_ERR_SHAPE);
+ * a direction other than +1 or -1 returns MB_ERR_INVALID_ARG. Otherwise as mb_mask_extend.
+ */
+mb_status mb_mask_extend_dir(mb_net* net, const uint8_t* em, const float* membrane, int64_t z, int64_t h, int64_t w,
+                             const uint8_t* seed_masks, int64_t z0, int64_t n_steps, int32_t direction, float threshold,
+                             uint8_t* masks_out, float* probs_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -209,25 +209,34 @@ def smooth_threshold(p, thr=0.5) -> np.ndarray:
     return m
 
 
-def maskextend_input(em_u8, memb, masks, z, R):
+def maskextend_input(em_u8, memb, masks, z, R, direction=1):
     """The 12-map input stack of MaskExtend at section z (Sec. 3.2), mirror-padded (reflect-101)
-    by R: EM z-1..z+1 (u/255), the object masks z-4..z-1 (0/1), membrane maps z-2..z+2.
+    by R. The maps sit at offsets k along the direction of travel s = +1 (z+) or -1 (z-), i.e. at
+    sections z + s k: EM k = -1, 0, 1 (u/255), the object masks k = -4 .. -1 (0/1, the sections
+    already extended), membrane maps k = -2 .. 2. For z+ that is EM z-1..z+1, masks z-4..z-1,
+    membrane z-2..z+2; extending in z- mirrors the offsets (masks z+4..z+1).
     em_u8, memb: [Z][H][W]; masks: dict section -> [H][W] 0/1."""
-    maps = [em_u8[z + k].astype(np.float64) / 255.0 for k in (-1, 0, 1)]
-    maps += [np.asarray(masks[z + k], dtype=np.float64) for k in (-4, -3, -2, -1)]
-    maps += [np.asarray(memb[z + k], dtype=np.float64) for k in (-2, -1, 0, 1, 2)]
+    s = 1 if direction >= 0 else -1
+    maps = [em_u8[z + s * k].astype(np.float64) / 255.0 for k in (-1, 0, 1)]
+    maps += [np.asarray(masks[z + s * k], dtype=np.float64) for k in (-4, -3, -2, -1)]
+    maps += [np.asarray(memb[z + s * k], dtype=np.float64) for k in (-2, -1, 0, 1, 2)]
     return np.stack([np.pad(m, R, mode="reflect") for m in maps])
 
 
-def mask_extend(layers, params, em_u8, memb, seed_masks, z0, n_steps, thr=0.5):
-    """The MaskExtend recursion in +z (Sec. 3.2): Mask_z = J(CNN(masks z-4..z-1, EM z-1..z+1,
-    membrane z-2..z+2)) for z = z0 .. z0+n_steps-1; seed_masks are the masks of z0-4 .. z0-1.
-    Returns (masks [n][H][W] uint8, class probabilities [n][3][H][W])."""
+def mask_extend(layers, params, em_u8, memb, seed_masks, z0, n_steps, thr=0.5, direction=1):
+    """The MaskExtend recursion (Sec. 3.2, transfer equation), in z+ (direction 1) or z- (-1):
+    with s the direction, Mask_z = J(CNN(masks at z + s k for k = -4..-1, EM at z + s k for
+    k = -1..1, membrane at z + s k for k = -2..2)) for z = z0, z0 + s, ..., z0 + s (n_steps - 1).
+    seed_masks[i] is the mask of section z0 + s (i - 4), i.e. the four sections before z0 in the
+    direction of travel (z0-4 .. z0-1 for z+, z0+4 .. z0+1 for z-).
+    Returns (masks [n][H][W] uint8, class probabilities [n][3][H][W]) in the order computed."""
+    s = 1 if direction >= 0 else -1
     R = net_radius(layers)
-    masks = {z0 - 4 + i: np.asarray(seed_masks[i]) for i in range(4)}
+    masks = {z0 + s * (i - 4): np.asarray(seed_masks[i]) for i in range(4)}
     out_m, out_p = [], []
-    for z in range(z0, z0 + n_steps):
-        p = run_layers_mc(layers, params, maskextend_input(em_u8, memb, masks, z, R))
+    for t in range(n_steps):
+        z = z0 + s * t
+        p = run_layers_mc(layers, params, maskextend_input(em_u8, memb, masks, z, R, s))
         masks[z] = smooth_threshold(p[0], thr)
         out_m.append(masks[z])
         out_p.append(p)

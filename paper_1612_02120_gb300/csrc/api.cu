@@ -833,24 +833,29 @@ mb_status mb_infer_cascade(mb_net* student, mb_net* teacher, const uint8_t* in, 
                    (cudaStream_t)stream);
 }
 
-mb_status mb_mask_extend(mb_net* net, const uint8_t* em, const float* membrane, int64_t z, int64_t h, int64_t w,
-                         const uint8_t* seed_masks, int64_t z0, int64_t n_steps, float threshold, uint8_t* masks_out,
-                         float* probs_out, void* stream) {
+mb_status mb_mask_extend_dir(mb_net* net, const uint8_t* em, const float* membrane, int64_t z, int64_t h, int64_t w,
+                             const uint8_t* seed_masks, int64_t z0, int64_t n_steps, int32_t direction, float threshold,
+                             uint8_t* masks_out, float* probs_out, void* stream) {
     API_BEGIN
     MB_TRY(check_ready(net));
     if (net->family != FAMILY_MASKEXTEND) {
         set_error("mb_mask_extend: not a MaskExtend net");
         return MB_ERR_UNSUPPORTED;
     }
-    if (!em || !membrane || !seed_masks || (!masks_out && n_steps > 0) || n_steps < 0 || !(threshold == threshold)) {
-        set_error("mb_mask_extend: null buffer or bad arguments");
+    if (!em || !membrane || !seed_masks || (!masks_out && n_steps > 0) || n_steps < 0 || !(threshold == threshold) ||
+        (direction != 1 && direction != -1)) {
+        set_error("mb_mask_extend: null buffer or bad arguments (direction must be +1 or -1)");
         return MB_ERR_INVALID_ARG;
     }
     MB_TRY(check_slice(z, h, w));
     MB_TRY(check_net_slice(net, h, w));
-    if (n_steps > 0 && (z0 < 2 || z0 + n_steps + 2 > z)) {
-        set_error("mb_mask_extend: sections z0-2 .. z0+n_steps+1 must lie in the stack of %lld (z0 %lld, %lld steps)",
-                  (long long)z, (long long)z0, (long long)n_steps);
+    // sections read: membrane maps 2 before z0 .. 2 after the last step, along the direction
+    const int64_t lo = direction > 0 ? z0 - 2 : z0 - n_steps - 1;
+    const int64_t hi = direction > 0 ? z0 + n_steps + 1 : z0 + 2;
+    if (n_steps > 0 && (lo < 0 || hi >= z)) {
+        set_error("mb_mask_extend: sections %lld .. %lld must lie in the stack of %lld (z0 %lld, %lld steps, "
+                  "direction %d)",
+                  (long long)lo, (long long)hi, (long long)z, (long long)z0, (long long)n_steps, (int)direction);
         return MB_ERR_SHAPE;
     }
     if (n_steps == 0) return MB_OK;
@@ -860,8 +865,15 @@ mb_status mb_mask_extend(mb_net* net, const uint8_t* em, const float* membrane, 
         set_error("mb_mask_extend: device pointers only");
         return MB_ERR_INVALID_ARG;
     }
-    return maskextend_run(net, em, membrane, z, h, w, seed_masks, z0, n_steps, threshold, masks_out, probs_out,
-                          (cudaStream_t)stream);
+    return maskextend_run(net, em, membrane, z, h, w, seed_masks, z0, n_steps, (int)direction, threshold, masks_out,
+                          probs_out, (cudaStream_t)stream);
+}
+
+mb_status mb_mask_extend(mb_net* net, const uint8_t* em, const float* membrane, int64_t z, int64_t h, int64_t w,
+                         const uint8_t* seed_masks, int64_t z0, int64_t n_steps, float threshold, uint8_t* masks_out,
+                         float* probs_out, void* stream) {
+    return mb_mask_extend_dir(net, em, membrane, z, h, w, seed_masks, z0, n_steps, 1, threshold, masks_out,
+                              probs_out, stream);
 }
 
 }  // extern "C"

@@ -139,7 +139,7 @@ mb_status me_tc_layer(mb_net* net, int layer, const void* in, int64_t in_pitch, 
                       int dm, void* out, int64_t out_pitch, int out_h, int out_w, float* probs, int64_t probs_plane,
                       cudaStream_t st);
 mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int64_t zt, int64_t h, int64_t w,
-                         const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
+                         const uint8_t* seeds, int64_t z0, int64_t n_steps, int dz, float thr, uint8_t* masks_out,
                          float* probs_out, cudaStream_t st);
 // BF16 student inference on the tensor cores (student_tc.cu), same arguments as simt_student_region;
 // student_region picks it for BF16 nets and the CUDA-core path for FP32 nets.

@@ -1,6 +1,7 @@
 // maskextend.cu - MaskExtend (Sec. 3.2) on CUDA cores (FP32): the transfer
 //   Mask_z = J(CNN(masks z-4..z-1, EM z-1..z+1, membrane maps z-2..z+2))
-// recursed in +z. CNN is the dense form of the max-out network: five 4x4 convs with max-out 2
+// recursed in +z, or in -z with every offset mirrored (masks z+4..z+1, EM z+1..z-1, membrane
+// maps z+2..z-2: the algorithm continues in either direction). CNN is the dense form of the max-out network: five 4x4 convs with max-out 2
 // (32, 40, 48, 56, 64 features; the first four followed by 2x2 pools, i.e. dilations 1, 2, 4, 8,
 // 16 with dilated max-filters in between), then a 1x1 head to 3 classes (object, other neurons,
 // membrane) with a softmax. J is a 3x3 mean of the object probability (reflect-101 borders)
@@ -32,14 +33,15 @@ constexpr int kMeR = 54;
 constexpr int kMeCin = 16;  // 12 maps padded to 16 channels
 
 struct MeMasks {
-    const uint8_t* m[4];  // masks of sections z-4 .. z-1, [h][w]
+    const uint8_t* m[4];  // masks of sections z + dz k for k = -4 .. -1, [h][w]
 };
 
 // Mirror-padded input stack of section z: out[(r, c)][ch] for r < h + 108, c < w + 108, FP32 or
-// (for the tensor-core path) FP16.
+// (for the tensor-core path) FP16. dz = +1 or -1 is the direction of travel: the maps at offset k
+// of the transfer equation are read from section z + dz k.
 template <typename T>
 __global__ void me_assemble(const uint8_t* __restrict__ em, const float* __restrict__ memb, MeMasks mk, int64_t z,
-                            int h, int w, T* __restrict__ out) {
+                            int dz, int h, int w, T* __restrict__ out) {
     const int pw = w + 2 * kMeR, ph = h + 2 * kMeR;
     const int64_t n = (int64_t)ph * pw;
     const int64_t hw = (int64_t)h * w;
@@ -49,11 +51,11 @@ __global__ void me_assemble(const uint8_t* __restrict__ em, const float* __restr
         const int64_t o = (int64_t)y * w + x;
         float v[16];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) v[k] = (float)em[(z - 1 + k) * hw + o] / 255.0f;
+        for (int k = 0; k < 3; ++k) v[k] = (float)em[(z + dz * (k - 1)) * hw + o] / 255.0f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[3 + k] = (float)mk.m[k][o];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) v[7 + k] = memb[(z - 2 + k) * hw + o];
+        for (int k = 0; k < 5; ++k) v[7 + k] = memb[(z + dz * (k - 2)) * hw + o];
 #pragma unroll
         for (int k = 12; k < 16; ++k) v[k] = 0.f;
         if constexpr (sizeof(T) == 4) {
@@ -142,6 +144,15 @@ void me_pack(const mb_net* net, const float* params, std::vector<float>& out) {
     }
 }
 
+// Masks read by step s (the section z0 + dz s): the four sections before it along the direction of
+// travel, step s + k - 4 for k = 0 .. 3; steps before the first are the seeds (seed i = step i - 4).
+static void me_masks(MeMasks& mk, const uint8_t* seeds, const uint8_t* masks_out, int64_t s, int64_t hw) {
+    for (int k = 0; k < 4; ++k) {
+        const int64_t t = s + k - 4;
+        mk.m[k] = t < 0 ? seeds + (t + 4) * hw : masks_out + t * hw;
+    }
+}
+
 static int me_grid(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
 }
@@ -149,8 +160,8 @@ static int me_grid(int64_t n) {
 // FP16 tensor-core form of the recursion: the same stack in FP16, the five convs on the tensor cores
 // (maskextend_tc.cu; the last one with the head and the softmax), then J.
 static mb_status maskextend_run_tc(mb_net* net, const uint8_t* em, const float* memb, int64_t h, int64_t w,
-                                   const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
-                                   float* probs_out, cudaStream_t st) {
+                                   const uint8_t* seeds, int64_t z0, int64_t n_steps, int dz, float thr,
+                                   uint8_t* masks_out, float* probs_out, cudaStream_t st) {
     MB_TRY(me_tc_poll_error(net));  // a wait that timed out in an earlier call on this net
     const int64_t r[5] = {h + 105, h + 98, h + 84, h + 56, h}, c[5] = {w + 105, w + 98, w + 84, w + 56, w};
     const int d[5] = {1, 2, 4, 8, 16}, dm[5] = {0, 1, 2, 4, 8};
@@ -172,13 +183,10 @@ static mb_status maskextend_run_tc(mb_net* net, const uint8_t* em, const float* 
     float* prob_tmp = reinterpret_cast<float*>(act[3] + n_act[3]);
     const int64_t hw = h * w;
     for (int64_t s = 0; s < n_steps; ++s) {
-        const int64_t z = z0 + s;
+        const int64_t z = z0 + dz * s;
         MeMasks mk;
-        for (int k = 0; k < 4; ++k) {
-            const int64_t zz = z - 4 + k;
-            mk.m[k] = zz < z0 ? seeds + (zz - (z0 - 4)) * hw : masks_out + (zz - z0) * hw;
-        }
-        me_assemble<__half><<<me_grid((h + 108) * (w + 108)), 256, 0, st>>>(em, memb, mk, z, (int)h, (int)w, xin);
+        me_masks(mk, seeds, masks_out, s, hw);
+        me_assemble<__half><<<me_grid((h + 108) * (w + 108)), 256, 0, st>>>(em, memb, mk, z, dz, (int)h, (int)w, xin);
         count_launch();
         MB_CUDA(cudaGetLastError());
         float* probs = probs_out ? probs_out + s * 3 * hw : prob_tmp;
@@ -198,12 +206,12 @@ static mb_status maskextend_run_tc(mb_net* net, const uint8_t* em, const float* 
 }
 
 mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int64_t zt, int64_t h, int64_t w,
-                         const uint8_t* seeds, int64_t z0, int64_t n_steps, float thr, uint8_t* masks_out,
+                         const uint8_t* seeds, int64_t z0, int64_t n_steps, int dz, float thr, uint8_t* masks_out,
                          float* probs_out, cudaStream_t st) {
     (void)zt;
     if (n_steps == 0) return MB_OK;
     if (net->prec == MB_PREC_FP16)
-        return maskextend_run_tc(net, em, memb, h, w, seeds, z0, n_steps, thr, masks_out, probs_out, st);
+        return maskextend_run_tc(net, em, memb, h, w, seeds, z0, n_steps, dz, thr, masks_out, probs_out, st);
     // geometry (dense): conv outputs and their input domains
     const int64_t r[5] = {h + 105, h + 98, h + 84, h + 56, h}, c[5] = {w + 105, w + 98, w + 84, w + 56, w};
     const int d[5] = {1, 2, 4, 8, 16}, dm[5] = {0, 1, 2, 4, 8};
@@ -239,13 +247,10 @@ mb_status maskextend_run(mb_net* net, const uint8_t* em, const float* memb, int6
     const float* head = bs[4] + 2 * cout[4];
     const int64_t hw = h * w;
     for (int64_t s = 0; s < n_steps; ++s) {
-        const int64_t z = z0 + s;
+        const int64_t z = z0 + dz * s;
         MeMasks mk;
-        for (int k = 0; k < 4; ++k) {
-            const int64_t zz = z - 4 + k;
-            mk.m[k] = zz < z0 ? seeds + (zz - (z0 - 4)) * hw : masks_out + (zz - z0) * hw;
-        }
-        me_assemble<float><<<me_grid((h + 108) * (w + 108)), 256, 0, st>>>(em, memb, mk, z, (int)h, (int)w, xin);
+        me_masks(mk, seeds, masks_out, s, hw);
+        me_assemble<float><<<me_grid((h + 108) * (w + 108)), 256, 0, st>>>(em, memb, mk, z, dz, (int)h, (int)w, xin);
         count_launch();
         MB_CUDA(cudaGetLastError());
         for (int k = 0; k < 5; ++k) {

@@ -23,6 +23,7 @@ EXPORTED = (
     "mb_calibrate_fp8", "mb_infer_volume", "mb_infer_region", "mb_infer_batch", "mb_infer_batch_per_block",
     "mb_autotune", "mb_student_loss_grad", "mb_student_train", "mb_infer_cascade", "mb_status_string",
     "mb_last_error", "mb_launch_count", "mb_infer_volume_noalloc", "mb_infer_volume_subsampled", "mb_mask_extend",
+    "mb_mask_extend_dir",
 )
 
 
@@ -83,6 +84,7 @@ def load() -> ctypes.CDLL:
         "mb_infer_volume_noalloc": ([p, p, i64, i64, i64, p, i32, p], st),
         "mb_infer_volume_subsampled": ([p, p, i64, i64, i64, i32, p, i32, p], st),
         "mb_mask_extend": ([p, p, p, i64, i64, i64, p, i64, i64, ctypes.c_float, p, p, p], st),
+        "mb_mask_extend_dir": ([p, p, p, i64, i64, i64, p, i64, i64, i32, ctypes.c_float, p, p, p], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +193,14 @@ def mb_mask_extend(net, em, membrane, z, h, w, seed_masks, z0, n_steps, masks_ou
     """MaskExtend transfer recursion in +z (device tensors)."""
     check(load().mb_mask_extend(net, ptr(em), ptr(membrane), z, h, w, ptr(seed_masks), z0, n_steps, float(threshold),
                                 ptr(masks_out), ptr(probs_out), stream_handle(stream)), "mb_mask_extend")
+
+
+def mb_mask_extend_dir(net, em, membrane, z, h, w, seed_masks, z0, n_steps, direction, masks_out, probs_out=None,
+                       threshold=0.5, stream=None) -> None:
+    """MaskExtend transfer recursion in z+ (direction 1) or z- (direction -1), device tensors."""
+    check(load().mb_mask_extend_dir(net, ptr(em), ptr(membrane), z, h, w, ptr(seed_masks), z0, n_steps, direction,
+                                    float(threshold), ptr(masks_out), ptr(probs_out), stream_handle(stream)),
+          "mb_mask_extend_dir")
 
 
 def mb_infer_volume_noalloc(net, inp, z, h, w, out, out_type=MB_OUT_F32, stream=None) -> None:

@@ -151,3 +151,25 @@ def test_fp16_step_at_bench_size_on_sampled_crops(net16):
         ref = oracle.run_layers_mc(M, prm, xp[:, y0:y0 + 96 + 108, x0:x0 + 96 + 108])
         met = oracle.metrics(probs[0][:, y0:y0 + 96, x0:x0 + 96], ref)
         assert met["max_abs"] <= TOL["fp16"]["max_abs"] and met["mean_abs"] <= TOL["fp16"]["mean_abs"], met
+
+
+def test_fp16_minus_z_steps_match_oracle(net16):
+    """The z- recursion on the tensor cores: each step against the oracle's z- step fed the GPU's
+    own earlier masks, at the 16-bit bar."""
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    em, memb, seeds = data(9, 72, 140, 8800)
+    Z, h, w = em.shape
+    z0, n = 6, 3
+    d_em, d_memb, d_seeds = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (em, memb, seeds))
+    masks = torch.zeros((n, h, w), dtype=torch.uint8, device="cuda")
+    pr = torch.zeros((n, 3, h, w), dtype=torch.float32, device="cuda")
+    m.mb_mask_extend_dir(net16.handle, d_em, d_memb, Z, h, w, d_seeds, z0, n, -1, masks, pr)
+    torch.cuda.synchronize()
+    masks, pr = masks.cpu().numpy(), pr.cpu().numpy()
+    prm = me_params().astype(np.float64)
+    known = {z0 + 4 - i: seeds[i] for i in range(4)}
+    for s in range(n):
+        ref_p = oracle.run_layers_mc(M, prm, oracle.maskextend_input(em, memb, known, z0 - s, 54, direction=-1))
+        check_step(masks[s], pr[s], ref_p)
+        known[z0 - s] = masks[s]

@@ -96,3 +96,30 @@ def test_recursion_feeds_each_mask_into_the_next_step():
     known[6] = 1 - masks[0]
     alt = oracle.run_layers_mc(M, prm, oracle.maskextend_input(em, memb, known, 7, 54))
     assert not np.array_equal(alt, probs[1])
+
+
+def test_input_stack_sections_minus_z():
+    """Extending in z- (Sec. 3.2: the algorithm continues in either z+ or z-) mirrors every offset
+    of the transfer equation: at section 5 the stack holds EM 6, 5, 4, the masks of the sections
+    already extended, 9, 8, 7, 6, and the membrane maps 7, 6, 5, 4, 3, in that channel order."""
+    em, memb, seeds = inputs()
+    known = {9: seeds[0], 8: seeds[1], 7: seeds[2], 6: seeds[3]}
+    x = oracle.maskextend_input(em, memb, known, 5, 2, direction=-1)
+    c = x[:, 2:-2, 2:-2]
+    np.testing.assert_array_equal(c[0:3], em[[6, 5, 4]] / 255.0)
+    np.testing.assert_array_equal(c[3:7], seeds.astype(np.float64))
+    np.testing.assert_array_equal(c[7:12], memb[[7, 6, 5, 4, 3]].astype(np.float64))
+
+
+def test_minus_z_recursion_is_plus_z_on_the_reversed_stack():
+    """The z- recursion from z0 equals the z+ recursion on the stack read backwards, from the
+    mirrored section, with the same seeds (their order is along the direction of travel)."""
+    prm = me_params()
+    em, memb, seeds = inputs(z=10, h=30, w=28, seed=8150)
+    m_dn, p_dn = oracle.mask_extend(M, prm, em, memb, seeds, 6, 3, direction=-1)
+    m_up, p_up = oracle.mask_extend(M, prm, em[::-1].copy(), memb[::-1].copy(), seeds, 10 - 1 - 6, 3)
+    np.testing.assert_array_equal(m_dn, m_up)
+    np.testing.assert_array_equal(p_dn, p_up)
+    # and it is not the z+ recursion from the same section (the direction matters)
+    _, p_same = oracle.mask_extend(M, prm, em, memb, seeds, 6, 1)
+    assert np.abs(p_same[0] - p_dn[0]).max() > 1e-3
