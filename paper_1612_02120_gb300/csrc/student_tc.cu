@@ -2,18 +2,28 @@
 // in one fused kernel on the 5th-generation tensor cores, for BF16 student nets:
 //   x = u/255 (mirror-padded by 2) -> conv3x3 1->16 + b, ReLU -> conv3x3 16->16 + b, ReLU
 //   -> conv1x1 16->1 + b -> sigmoid
-// Layer 1 runs on CUDA cores in FP32 (packed FP32x2 FMAs) and is rounded to BF16 into a ring of
-// staged rows; layer 2 is an implicit GEMM per output row and 128-pixel strip:
-//   D[128 px][16 co] = sum over taps (ky, kx) of A_{ky,kx}[128 px][16 ci] x B_{ky,kx}[16 co][16 ci]^T
-// where A_{ky,kx} is staged row y - 1 + ky at pixels kx .. kx + 127 (a kx x 16-byte shift of the
-// descriptor start in the no-swizzle K-major layout [8-channel chunk][pixel][16 B]). The epilogue
-// adds the bias, applies ReLU, the head and the sigmoid in FP32 and stores the probability.
+// Both convolutions are implicit GEMMs per 128-pixel strip row (M = 128 pixels, operands in the
+// no-swizzle K-major layout [8-element chunk][pixel][16 B]):
+//   layer 1  D1[px][co] = sum_kx A1[px + kx][ky] x W1[co][ky][kx] with A1[q][ky] = u(r - 1 + ky, q):
+//            the three row taps are stacked along K (an input byte is exact in BF16), the column tap
+//            kx is a kx x 16-byte shift of the descriptor start; 3 MMAs (N = 16, K = 16) per row.
+//            The epilogue scales by 1/255 in FP32, adds the bias, applies ReLU and rounds to BF16
+//            into a ring of staged feature rows.
+//   layer 2  each staged row r is multiplied once per column tap kx with the three row taps stacked
+//            along N (N = 48: blocks for output rows r-2, r-1, r with row taps 2, 1, 0), accumulating
+//            into a ring of 8 row accumulators (windows that wrap the ring are split in two MMAs).
+//            The epilogue adds the bias, applies ReLU, the head and the sigmoid in FP32 and stores.
+// A strip covers 126 output columns (128 layer-1 pixels, the last two only feed the column taps).
 //
-// Warp roles (256 threads, several CTAs per SM, persistent over work items):
-//   warp 0      TMEM owner (128 columns: 8 accumulators of 16); lane 0 issues the MMAs
-//   warps 1-3   layer-1 producers: 130 pixels x 2 channel halves per staged row, from input rows
-//               staged once each in shared memory
-//   warps 4-7   epilogue: TMEM lane = pixel of the strip
+// Warp roles (384 threads, two CTAs per SM, persistent over work items):
+//   warp 0      TMEM owner (256 columns: layer-2 ring 0..127, layer-1 ring 128..191); lane 0
+//               issues the layer-1 MMAs
+//   warp 3      lane 0 issues the layer-2 MMAs (a thread stalls ~200 cycles on each commit; with
+//               two issuing threads the tensor core keeps working meanwhile)
+//   warps 1-2   operand builders: keep three input rows per column in registers and write the
+//               layer-1 operand row (one 16-byte store per pixel per row)
+//   warps 4-7   layer-1 epilogue (TMEM lane = layer-1 pixel)
+//   warps 8-11  layer-2 epilogue and head (TMEM lane = output pixel)
 // Every mbarrier wait is bounded (a global-timer limit), after which the CTA records
 // MB_ERR_TIMEOUT in a mapped host word, stops issuing work and frees its TMEM.
 #include <cuda_bf16.h>
@@ -29,34 +39,45 @@ namespace mb {
 
 namespace {
 
-constexpr int kSThreads = 256;
-constexpr int kSP = 132;                  // staged pixels per row (>= 130; 132 mod 8 = 4 spreads the
-                                          // two chunk planes of 4 consecutive pixels over distinct banks)
-constexpr int kSRow = 2 * kSP * 16;       // bytes per staged row
-constexpr int kSRing = 8;                 // staged rows
-constexpr int kSAcc = 8;                  // accumulators, 16 TMEM columns each
-constexpr int kSTmem = 128;
-constexpr int kSB = 9 * 2 * 16 * 16;      // B: 9 taps x [2 chunks][16 co][16 B]
-constexpr int kSConst = 193;              // W1t[9][16], b1[16], b2[16], wh[16], bh
-constexpr int oSB = 0;
-constexpr int oSRing = oSB + kSB;
-constexpr int oSConst = oSRing + kSRing * kSRow;
-constexpr int oSIn = oSConst + ((kSConst * 4 + 15) & ~15);  // 4 input rows x 136 floats
-constexpr int oSBar = oSIn + 4 * 136 * 4;
-constexpr int kSBars = 2 * kSRing + 2 * kSAcc + 1;
+constexpr int kSThreads = 384;
+constexpr int kSW = 126;                  // output columns per strip
+constexpr int kSPitch = 136;              // pixels per operand row (128 + the column taps' overrun)
+constexpr int kSRowB = 2 * kSPitch * 16;  // bytes per operand row: 2 chunks (K = 16 BF16)
+constexpr int kNA1 = 4;                   // layer-1 operand rows in flight
+constexpr int kNS = 6;                    // staged layer-1 feature rows
+constexpr int kKL = 4;                    // layer-1 accumulators, 16 TMEM columns each
+constexpr int kKA = 8;                    // layer-2 row accumulators, 16 TMEM columns each
+constexpr int kSTmem = 256;
+constexpr int kL1Col = 128;               // first TMEM column of the layer-1 ring
+constexpr int kB1 = 3 * 2 * 16 * 16;      // per column tap: [2 chunks][16 co][16 B]
+constexpr int kB2Group = 2 * 48 * 16;     // per column tap: [2 chunks][48 rows][16 B]
+constexpr int kB2 = 3 * kB2Group;
+constexpr int kSConst = 64;               // b1[16] | b2[16] | head w[16] | head b | 1/255
+constexpr int kCB1 = 0, kCB2 = 16, kCWH = 32, kCBH = 48, kCInv = 49;
+constexpr int oSB1 = 0;
+constexpr int oSB2 = oSB1 + kB1;
+constexpr int oSA1 = oSB2 + kB2;
+constexpr int oSS = oSA1 + kNA1 * kSRowB;
+constexpr int oSConst = oSS + kNS * kSRowB;
+constexpr int oSBar = oSConst + kSConst * 4;
+constexpr int kSBars = 2 * kNA1 + 2 * kKL + 2 * kNS + 2 * kKA + 2;
 constexpr int oSMisc = oSBar + kSBars * 8;
-constexpr int kSSmem = oSMisc + 16;
-constexpr int kSProdThreads = 96;
-constexpr int kSTasks = (130 * 2 + kSProdThreads - 1) / kSProdThreads;
+constexpr int kSUsed = oSMisc + 16;
+// Requested shared memory: at most two CTAs fit on an SM, so their TMEM (2 x 256 columns) always
+// fits and no CTA waits in tcgen05.alloc.
+constexpr int kSSmem = 80 * 1024;
+constexpr int kWpack = kB1 + kB2 + kSConst * 4;
 constexpr uint64_t kSWaitNs = 4000000000ull;
 // forward layout of the student's parameters (as packed for the CUDA-core path)
 constexpr int kFW1 = 0, kFB1 = 144, kFW2 = 160, kFB2 = 2464, kFWH = 2480, kFBH = 2496;
-static_assert(kSSmem <= 100 * 1024, "shared memory");
+static_assert(kSUsed <= kSSmem && 3 * kSSmem > 227 * 1024, "shared memory");
+static_assert(oSA1 % 16 == 0 && oSS % 16 == 0 && oSBar % 8 == 0, "alignment");
+static_assert(2 * kSTmem <= 512, "TMEM of two CTAs");
 
 struct StTcParams {
     const uint8_t* in;        // slice z at in + z in_slice; row pitch in_pitch
     void* out;                // region output, [z][rows][cols] with out_pitch / out_slice
-    const uint8_t* wpack;     // B tiles then the FP32 constants
+    const uint8_t* wpack;     // B operands then the FP32 constants
     int* err;
     int64_t in_slice, in_pitch, out_slice, out_pitch;
     int h, w;                 // slice
@@ -73,14 +94,15 @@ __device__ __forceinline__ uint64_t gtime() {
     return t;
 }
 
+// A completed phase costs one poll: the abort flag is read only once the phase is found incomplete.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                          uint64_t limit_ns) {
-    if (*abort_flag) return false;
     if (ptx::mbar_test(bar, parity)) return true;
+    if (*abort_flag) return false;
     const uint64_t t0 = gtime();
     uint32_t n = 0;
+    // mbarrier.try_wait suspends the thread for a while by itself; no extra sleep between polls
     while (!ptx::mbar_test(bar, parity)) {
-        __nanosleep(32);
         if ((++n & 255u) == 0) {
             if (*abort_flag) return false;
             if (gtime() - t0 > limit_ns) {
@@ -107,43 +129,68 @@ __device__ __forceinline__ StItem st_item(const StTcParams& p, int k) {
     it.z = k / p.n_strips;
     it.m0 = chunk * p.rows_per_item;
     it.rows = max(0, min(p.rows_per_item, p.rows - it.m0));
-    it.s0 = strip * 128;
-    it.ncol = min(128, p.cols - it.s0);
+    it.s0 = strip * kSW;
+    it.ncol = min(kSW, p.cols - it.s0);
     return it;
+}
+
+// BF16 bits of a byte value (exact: every integer up to 256 has at most 8 significant bits).
+__device__ __forceinline__ uint32_t bf16_of_byte(uint32_t v) { return __float_as_uint((float)v) >> 16; }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
 }
 
 __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constant__ StTcParams p) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t* a_full = reinterpret_cast<uint64_t*>(smem + oSBar);
-    uint64_t* a_empty = a_full + kSRing;
-    uint64_t* acc_full = a_empty + kSRing;
-    uint64_t* acc_free = acc_full + kSAcc;
-    uint64_t* fin = acc_free + kSAcc;
+    uint64_t* a1_full = reinterpret_cast<uint64_t*>(smem + oSBar);
+    uint64_t* a1_empty = a1_full + kNA1;
+    uint64_t* l1_full = a1_empty + kNA1;
+    uint64_t* l1_free = l1_full + kKL;
+    uint64_t* s_full = l1_free + kKL;
+    uint64_t* s_empty = s_full + kNS;
+    uint64_t* l2_full = s_empty + kNS;
+    uint64_t* l2_free = l2_full + kKA;
+    uint64_t* fin = l2_free + kKA;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + oSMisc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + oSMisc + 4);
     const float* cst = reinterpret_cast<const float*>(smem + oSConst);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int i = 0; i < kSRing; ++i) {
-            ptx::mbar_init(&a_full[i], kSProdThreads);
-            ptx::mbar_init(&a_empty[i], 1);
+        for (int i = 0; i < kNA1; ++i) {
+            ptx::mbar_init(&a1_full[i], 64);
+            ptx::mbar_init(&a1_empty[i], 1);
         }
-        for (int i = 0; i < kSAcc; ++i) {
-            ptx::mbar_init(&acc_full[i], 1);
-            ptx::mbar_init(&acc_free[i], 128);
+        for (int i = 0; i < kKL; ++i) {
+            ptx::mbar_init(&l1_full[i], 1);
+            ptx::mbar_init(&l1_free[i], 128);
+        }
+        for (int i = 0; i < kNS; ++i) {
+            ptx::mbar_init(&s_full[i], 128);
+            ptx::mbar_init(&s_empty[i], 1);
+        }
+        for (int i = 0; i < kKA; ++i) {
+            ptx::mbar_init(&l2_full[i], 1);
+            ptx::mbar_init(&l2_free[i], 128);
         }
         ptx::mbar_init(fin, 1);
+        ptx::mbar_init(fin + 1, 1);
         *abort_flag = 0;
         ptx::mbar_fence_init();
     }
     {
         const uint4* src = reinterpret_cast<const uint4*>(p.wpack);
-        uint4* dst = reinterpret_cast<uint4*>(smem + oSB);
-        for (int i = tid; i < kSB / 16; i += kSThreads) dst[i] = __ldg(src + i);
-        const float* csrc = reinterpret_cast<const float*>(p.wpack + kSB);
+        uint4* dst = reinterpret_cast<uint4*>(smem + oSB1);
+        for (int i = tid; i < (kB1 + kB2) / 16; i += kSThreads) dst[i] = __ldg(src + i);
+        const float* csrc = reinterpret_cast<const float*>(p.wpack + kB1 + kB2);
         float* cdst = reinterpret_cast<float*>(smem + oSConst);
         for (int i = tid; i < kSConst; i += kSThreads) cdst[i] = __ldg(csrc + i);
+        // both operand rings start zero: the second K chunk of the layer-1 operand and the pixels
+        // past 127 of every row (read by the column taps, never written) stay zero
+        uint4* r = reinterpret_cast<uint4*>(smem + oSA1);
+        for (int i = tid; i < (kNA1 + kNS) * kSRowB / 16; i += kSThreads) r[i] = make_uint4(0, 0, 0, 0);
     }
     if (warp == 0) {
         ptx::tmem_alloc(tmem_slot, kSTmem);
@@ -155,51 +202,88 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
     ptx::tc_fence_after();
     const uint32_t tbase = *tmem_slot;
     const uint32_t sbase = ptx::smem_u32(smem);
+    if (warp >= 8) {
+        // every layer-2 accumulator starts at zero (its MMAs only accumulate)
+        const uint32_t lanes = (uint32_t)(32 * (warp - 8)) << 16;
+        for (int sl = 0; sl < kKA; ++sl) ptx::tmem_st16_zero(tbase + lanes + 16u * sl);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
 
-    if (warp == 0) {
-        // ================= MMA issuer ================================================================
+    if (warp == 0 || warp == 3) {
+        // ================= MMA issuers: warp 0 lane 0 layer 1, warp 3 lane 0 layer 2 ================
+        // Each issues, commits and finally drains only its own MMAs; they meet only through the
+        // layer-1 epilogue (layer 1 runs ahead as far as its 4 accumulators allow).
         if (lane == 0) {
-            const uint64_t adesc0 = ptx::smem_desc(sbase + oSRing, kSP * 16, 128);
-            const uint64_t bdesc0 = ptx::smem_desc(sbase + oSB, 16 * 16, 128);
-            constexpr uint32_t idesc = ptx::idesc_f32acc(ptx::kFmtBF16, 128, 16);
-            uint32_t a_seq = 0, acc_seq = 0;
+            const bool l1 = warp == 0;
+            const uint64_t a1d = ptx::smem_desc(sbase + oSA1, kSPitch * 16, 128);
+            const uint64_t sd = ptx::smem_desc(sbase + oSS, kSPitch * 16, 128);
+            const uint64_t b1d = ptx::smem_desc(sbase + oSB1, 16 * 16, 128);
+            const uint64_t b2d = ptx::smem_desc(sbase + oSB2, 48 * 16, 128);
+            constexpr uint32_t id16 = ptx::idesc_f32acc(ptx::kFmtBF16, 128, 16);
+            uint32_t rq = 0, aq = 0;  // operand / staged rows and layer-2 accumulator rows so far
             bool ok = true;
-            auto wait_row = [&](uint32_t q) {
-                ok = ok && wait_bar(&a_full[q % kSRing], (q / kSRing) & 1, abort_flag, p.err, p.wait_ns);
+            auto layer1 = [&](uint32_t q) {
+                const uint32_t sa = q % kNA1, sl = q % kKL;
+                ok = ok && wait_bar(&a1_full[sa], (q / kNA1) & 1, abort_flag, p.err, p.wait_ns);
+                ok = ok && wait_bar(&l1_free[sl], ((q / kKL) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                ptx::tc_fence_after();
+                if (ok) {
+                    const uint64_t arow = a1d + (uint64_t)((sa * kSRowB) >> 4);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx)
+                        ptx::mma_bf16(tbase + kL1Col + 16u * sl, arow + (uint64_t)kx,
+                                      b1d + (uint64_t)((kx * 512) >> 4), id16, kx ? 1u : 0u);
+                }
+                ptx::mma_commit(&a1_empty[sa]);
+                ptx::mma_commit(&l1_full[sl]);
+            };
+            // staged row u (sequence q) feeds output rows u-2+i, i = 0..2, with row tap 2-i
+            auto layer2 = [&](uint32_t q, int u, int R) {
+                const uint32_t ss = q % kNS;
+                ok = ok && wait_bar(&s_full[ss], (q / kNS) & 1, abort_flag, p.err, p.wait_ns);
+                if (u < R) {  // output row u starts here: its accumulator must have been drained
+                    const uint32_t qa = aq + (uint32_t)u;
+                    ok = ok && wait_bar(&l2_free[qa % kKA], ((qa / kKA) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                }
+                ptx::tc_fence_after();
+                const int ilo = max(0, 2 - u), ihi = min(2, R + 1 - u);
+                if (ok && ilo <= ihi) {
+                    const int s_lo = (int)((aq + (uint32_t)(u - 2 + ilo)) % kKA);
+                    const int iw = ilo + (kKA - s_lo);  // first block whose slot wraps to 0
+                    const int hi0 = iw <= ihi ? iw - 1 : ihi;
+                    const uint64_t arow = sd + (uint64_t)((ss * kSRowB) >> 4);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const uint64_t bg = b2d + (uint64_t)((kx * kB2Group) >> 4);
+                        ptx::mma_bf16(tbase + 16u * s_lo, arow + (uint64_t)kx, bg + (uint64_t)(16 * ilo),
+                                      ptx::idesc_f32acc(ptx::kFmtBF16, 128, (uint32_t)(16 * (hi0 - ilo + 1))), 1u);
+                        if (iw <= ihi)
+                            ptx::mma_bf16(tbase, arow + (uint64_t)kx, bg + (uint64_t)(16 * iw),
+                                          ptx::idesc_f32acc(ptx::kFmtBF16, 128, (uint32_t)(16 * (ihi - iw + 1))), 1u);
+                    }
+                }
+                ptx::mma_commit(&s_empty[ss]);
+                if (u >= 2 && u - 2 < R) ptx::mma_commit(&l2_full[(aq + (uint32_t)(u - 2)) % kKA]);
             };
             for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
                 const StItem it = st_item(p, k);
                 if (it.rows == 0) continue;
-                wait_row(a_seq);
-                wait_row(a_seq + 1);
-                for (int j = 0; j < it.rows; ++j) {
-                    wait_row(a_seq + j + 2);
-                    const uint32_t qa = acc_seq + j, s = qa % kSAcc;
-                    ok = ok && wait_bar(&acc_free[s], ((qa / kSAcc) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                    ptx::tc_fence_after();
-                    if (ok) {
-                        const uint32_t dcol = tbase + 16u * s;
-#pragma unroll
-                        for (int ky = 0; ky < 3; ++ky) {
-                            const uint64_t arow =
-                                adesc0 + (uint64_t)((((a_seq + j + ky) % kSRing) * kSRow) >> 4);
-#pragma unroll
-                            for (int kx = 0; kx < 3; ++kx)
-                                ptx::mma_bf16(dcol, arow + (uint64_t)kx, bdesc0 + (uint64_t)(((ky * 3 + kx) * 512) >> 4),
-                                              idesc, (ky | kx) ? 1u : 0u);
-                        }
-                    }
-                    ptx::mma_commit(&acc_full[s]);
-                    ptx::mma_commit(&a_empty[(a_seq + j) % kSRing]);  // staged row j is done
+                const int R = it.rows, n_rows = R + 2;
+                for (int u = 0; u < n_rows; ++u) {
+                    if (l1)
+                        layer1(rq + (uint32_t)u);
+                    else
+                        layer2(rq + (uint32_t)u, u, R);
                 }
-                ptx::mma_commit(&a_empty[(a_seq + it.rows) % kSRing]);
-                ptx::mma_commit(&a_empty[(a_seq + it.rows + 1) % kSRing]);
-                a_seq += it.rows + 2;
-                acc_seq += it.rows;
+                rq += (uint32_t)n_rows;
+                aq += (uint32_t)R;
             }
-            ptx::mma_commit(fin);
+            uint64_t* f = fin + (l1 ? 0 : 1);
+            ptx::mma_commit(f);
             const uint64_t t0 = gtime();
-            while (!ptx::mbar_test(fin, 0)) {
+            while (!ptx::mbar_test(f, 0)) {
                 if (gtime() - t0 > p.wait_ns) {
                     *(volatile int*)p.err = MB_ERR_TIMEOUT;
                     break;
@@ -207,150 +291,129 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
             }
         }
         __syncwarp();
-    } else if (warp < 4) {
-        // ================= layer-1 producers ========================================================
-        // Staged row u of an item is layer-1 row r = y0 + m0 - 1 + u of the slice, at columns
-        // c = x0 + s0 - 1 + px (px < 130), computed from input rows r - 1 .. r + 1 (reflect-101).
-        // Input rows go through a ring of 4 rows of x = u/255 in shared memory (columns c - 1 .. c + 1
-        // of every staged pixel: 132 values from x0 + s0 - 2); each is loaded once, one row ahead
-        // (its loads are in flight while the current row is computed). The three producer warps
-        // synchronise on named barrier 1. Task e = pt + 96 i: staged pixel e >> 1, channels 8 (e & 1)..+7.
-        const int pt = tid - 32;
-        float* xr = reinterpret_cast<float*>(smem + oSIn);
-        // a thread's tasks all have channel half pt & 1 (96 is even): its 72 weights and 8 biases
-        // stay in registers
-        const int hf = pt & 1;
-        float2 wr[9][4], br[4];  // channel pairs, for packed FP32x2 FMAs
-#pragma unroll
-        for (int t = 0; t < 9; ++t)
-#pragma unroll
-            for (int o = 0; o < 4; ++o) wr[t][o] = make_float2(cst[t * 16 + 8 * hf + 2 * o], cst[t * 16 + 8 * hf + 2 * o + 1]);
-#pragma unroll
-        for (int o = 0; o < 4; ++o) br[o] = make_float2(cst[kFB1 + 8 * hf + 2 * o], cst[kFB1 + 8 * hf + 2 * o + 1]);
-        uint32_t a_seq = 0;
-        auto bar_prod = [] { asm volatile("bar.sync 1, 96;" ::: "memory"); };
+    } else if (warp == 1 || warp == 2) {
+        // ================= layer-1 operand builder ====================================================
+        // Operand row u of an item belongs to layer-1 row r = y0 + m0 - 1 + u: pixel q holds the input
+        // bytes of rows r - 1 .. r + 1 (elements 0..2 of K chunk 0) at column x0 + s0 - 2 + q, both
+        // mirror-padded at the slice borders. Builder thread b (warps 1-2) owns pixels b + 64 k; it
+        // keeps its three rows in registers and has the loads of the kLd rows after them in flight
+        // (one thread also bulk-prefetches rows into L2).
+        const int bt = tid - 32;
+        uint32_t rq = 0;
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const StItem it = st_item(p, k);
             if (it.rows == 0) continue;
+            const int R = it.rows, n_rows = R + 2, last = R + 3;  // input rows 0 .. R + 3 of the item
             const uint8_t* src = p.in + (int64_t)it.z * p.in_slice;
-            const int c0 = p.x0 + it.s0 - 2;           // input column of ring entry 0
-            const int nin = min(132, it.ncol + 4);     // input columns this strip needs
-            const int rfirst = p.y0 + it.m0 - 2;       // input row feeding staged row 0's ky = 0
-            // input row i (slice row rfirst + i) -> registers, as raw bytes (converted to x = u/255 when
-            // put into the ring, so the loads stay in flight meanwhile): columns pt, pt + 96 of the ring
-            // row; the item reads input rows 0 .. rows + 3
-            auto load_in = [&](int i, uint32_t (&v)[2]) {
-                const bool need = i <= it.rows + 3;
-                const int row = refl(rfirst + min(i, it.rows + 3), p.h);
+            const int c0 = p.x0 + it.s0 - 2;
+            const int nin = min(130, it.ncol + 4);  // input columns the strip's outputs depend on
+            const int rbase = p.y0 + it.m0 - 2;
+            int col[3];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int j = pt + 96 * q;
-                    v[q] = need && j < nin ? (uint32_t)src[(int64_t)row * p.in_pitch + refl(c0 + j, p.w)] : 0u;
-                }
-            };
-            auto put_in = [&](int i, const uint32_t (&v)[2]) {
+            for (int i = 0; i < 3; ++i) col[i] = bt + 64 * i < nin ? refl(c0 + bt + 64 * i, p.w) : -1;
+            auto load_row = [&](int i, uint32_t (&v)[3]) {
+                const uint8_t* row = src + (int64_t)refl(rbase + min(i, last), p.h) * p.in_pitch;
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int j = pt + 96 * q;
-                    if (j < 132) xr[(i & 3) * 136 + j] = (float)v[q] / 255.0f;
-                }
+                for (int j = 0; j < 3; ++j) v[j] = col[j] >= 0 ? bf16_of_byte((uint32_t)__ldg(row + col[j])) : 0u;
             };
-            // input rows come from DRAM on first touch: one thread bulk-prefetches the strip of the
-            // row kPf staged rows ahead into L2, so the loads issued one staged row ahead hit L2
             constexpr int kPf = 8;
-            auto prefetch_in = [&](int i) {
-                if (pt != 0 || i > it.rows + 3) return;
-                const int row = refl(rfirst + i, p.h);
-                const uint8_t* base = src + (int64_t)row * p.in_pitch;
+            auto prefetch_row = [&](int i) {
+                if (bt != 0 || i > last) return;
+                const uint8_t* base = src + (int64_t)refl(rbase + i, p.h) * p.in_pitch;
                 const uintptr_t lo = (uintptr_t)(base + max(0, c0)) & ~(uintptr_t)15;
                 const uintptr_t hi = (uintptr_t)(base + min(p.w, c0 + nin)) & ~(uintptr_t)15;
                 if (hi > lo) ptx::prefetch_l2_bulk((const void*)lo, (uint32_t)(hi - lo));
             };
-            {
-                for (int i = 3; i < 3 + kPf; ++i) prefetch_in(i);
-                uint32_t v0[2], v1[2], v2[2];
-                load_in(0, v0);
-                load_in(1, v1);
-                load_in(2, v2);
-                bar_prod();  // the previous item's readers are done with the ring
-                put_in(0, v0);
-                put_in(1, v1);
-                put_in(2, v2);
-            }
-            for (int u = 0; u < it.rows + 2; ++u) {
-                const uint32_t q = a_seq + u, slot = q % kSRing;
-                uint32_t nxt[2];
-                load_in(u + 3, nxt);  // the input row of the next staged row
-                prefetch_in(u + 3 + kPf);
-                bar_prod();  // input rows u .. u + 2 are in the ring
-                const float* x0r = xr + (u & 3) * 136;
-                const float* x1r = xr + ((u + 1) & 3) * 136;
-                const float* x2r = xr + ((u + 2) & 3) * 136;
-                uint4 v[kSTasks];
+            for (int i = 3; i < 3 + kPf; ++i) prefetch_row(i);
+            constexpr int kLd = 4;  // input rows whose loads are in flight
+            uint32_t w0[3], w1[3], w2[3], pend[kLd][3];
+            load_row(0, w0);
+            load_row(1, w1);
+            load_row(2, w2);
 #pragma unroll
-                for (int i = 0; i < kSTasks; ++i) {
-                    const int e = pt + kSProdThreads * i;
-                    const int px = e >> 1;
-                    v[i] = make_uint4(0, 0, 0, 0);
-                    if (e < 260 && px < it.ncol + 2) {
-                        float x[9];
+            for (int t = 0; t < kLd; ++t) load_row(3 + t, pend[t]);  // rows past the last are clamped to it
+            for (int u0 = 0; u0 < n_rows; u0 += kLd) {
 #pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) {
-                            x[kx] = x0r[px + kx];
-                            x[3 + kx] = x1r[px + kx];
-                            x[6 + kx] = x2r[px + kx];
-                        }
-                        float2 a[4];
+                for (int t = 0; t < kLd; ++t) {
+                    const int u = u0 + t;
+                    if (u >= n_rows) break;
+                    prefetch_row(u + 3 + kPf);
+                    const uint32_t q = rq + (uint32_t)u, slot = q % kNA1;
+                    wait_bar(&a1_empty[slot], ((q / kNA1) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                    uint8_t* dst = smem + oSA1 + slot * kSRowB;
 #pragma unroll
-                        for (int o = 0; o < 4; ++o) a[o] = br[o];
-#pragma unroll
-                        for (int t = 0; t < 9; ++t) {
-                            const float2 xv = make_float2(x[t], x[t]);
-#pragma unroll
-                            for (int o = 0; o < 4; ++o) a[o] = __ffma2_rn(wr[t][o], xv, a[o]);
-                        }
-                        uint32_t wd[4];
-#pragma unroll
-                        for (int o = 0; o < 4; ++o) {
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(a[o].x, 0.f), fmaxf(a[o].y, 0.f));
-                            wd[o] = *reinterpret_cast<uint32_t*>(&b2);
-                        }
-                        v[i] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                    for (int j = 0; j < 3; ++j) {
+                        const int px = bt + 64 * j;
+                        if (px < 130)
+                            *reinterpret_cast<uint4*>(dst + px * 16) = make_uint4(w0[j] | (w1[j] << 16), w2[j], 0u, 0u);
                     }
-                }
-                // ring slot of row u + 3 held row u - 1, which every producer finished reading before
-                // this row's barrier; row u + 3 becomes visible at the next row's barrier
-                put_in(u + 3, nxt);
-                wait_bar(&a_empty[slot], ((q / kSRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                uint8_t* dst = smem + oSRing + slot * kSRow;
+                    ptx::fence_proxy_async_smem();
+                    if (!p.fault_stall) ptx::mbar_arrive(&a1_full[slot]);
+                    // rows u+1 .. u+3 become the window; the loads of row u + 3 + kLd take row u+3's place
 #pragma unroll
-                for (int i = 0; i < kSTasks; ++i) {
-                    const int e = pt + kSProdThreads * i;
-                    if (e < 260) *reinterpret_cast<uint4*>(dst + ((e & 1) * kSP + (e >> 1)) * 16) = v[i];
+                    for (int j = 0; j < 3; ++j) {
+                        w0[j] = w1[j];
+                        w1[j] = w2[j];
+                        w2[j] = pend[t][j];
+                    }
+                    load_row(u + 3 + kLd, pend[t]);
                 }
-                ptx::fence_proxy_async_smem();
-                if (!p.fault_stall) ptx::mbar_arrive(&a_full[slot]);
             }
-            a_seq += it.rows + 2;
+            rq += (uint32_t)n_rows;
         }
-    } else {
-        // ================= epilogue ===================================================================
-        const int px = tid - 128;  // TMEM lane = pixel of the strip
+    } else if (warp >= 4 && warp < 8) {
+        // ================= layer-1 epilogue: x 1/255, bias, ReLU, BF16 -> staged feature ring =======
+        const int px = tid - 128;
         const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
-        uint32_t acc_seq = 0;
+        const float inv = cst[kCInv];
+        uint32_t rq = 0;
+        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+            const StItem it = st_item(p, k);
+            if (it.rows == 0) continue;
+            const int n_rows = it.rows + 2;
+            for (int u = 0; u < n_rows; ++u) {
+                const uint32_t q = rq + (uint32_t)u, sl = q % kKL;
+                wait_bar(&l1_full[sl], (q / kKL) & 1, abort_flag, p.err, p.wait_ns);
+                ptx::tc_fence_after();
+                float d[16];
+                ptx::tmem_ld16(tbase + lanes + kL1Col + 16u * sl, d);
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&l1_free[sl]);
+                uint32_t wd[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    wd[c] = pack_bf16x2(fmaxf(fmaf(d[2 * c], inv, cst[kCB1 + 2 * c]), 0.f),
+                                        fmaxf(fmaf(d[2 * c + 1], inv, cst[kCB1 + 2 * c + 1]), 0.f));
+                const uint32_t ss = q % kNS;
+                wait_bar(&s_empty[ss], ((q / kNS) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                uint8_t* dst = smem + oSS + ss * kSRowB;
+                *reinterpret_cast<uint4*>(dst + px * 16) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                *reinterpret_cast<uint4*>(dst + (kSPitch + px) * 16) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+                ptx::fence_proxy_async_smem();
+                ptx::mbar_arrive(&s_full[ss]);
+            }
+            rq += (uint32_t)n_rows;
+        }
+    } else if (warp >= 8) {
+        // ================= layer-2 epilogue: bias, ReLU, head, sigmoid, store ========================
+        const int px = tid - 256;  // TMEM lane = output pixel of the strip
+        const uint32_t lanes = (uint32_t)(32 * (warp - 8)) << 16;
+        uint32_t aq = 0;
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const StItem it = st_item(p, k);
             for (int j = 0; j < it.rows; ++j) {
-                const uint32_t qa = acc_seq + j, s = qa % kSAcc;
-                wait_bar(&acc_full[s], (qa / kSAcc) & 1, abort_flag, p.err, p.wait_ns);
+                const uint32_t qa = aq + (uint32_t)j, sl = qa % kKA;
+                wait_bar(&l2_full[sl], (qa / kKA) & 1, abort_flag, p.err, p.wait_ns);
                 ptx::tc_fence_after();
                 float d[16];
-                ptx::tmem_ld16(tbase + lanes + 16u * s, d);
+                const uint32_t ta = tbase + lanes + 16u * sl;
+                ptx::tmem_ld16(ta, d);
+                ptx::tmem_st16_zero(ta);
                 ptx::tc_fence_before();
-                ptx::mbar_arrive(&acc_free[s]);
-                float z = cst[kSConst - 1];
+                ptx::mbar_arrive(&l2_free[sl]);
+                float z = cst[kCBH];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) z = fmaf(cst[176 + c], fmaxf(d[c] + cst[160 + c], 0.f), z);
+                for (int c = 0; c < 16; ++c) z = fmaf(cst[kCWH + c], fmaxf(d[c] + cst[kCB2 + c], 0.f), z);
                 const float prob = 1.0f / (1.0f + expf(-z));
                 if (px < it.ncol && !*abort_flag) {
                     const int64_t idx = (int64_t)it.z * p.out_slice + (int64_t)(it.m0 + j) * p.out_pitch + it.s0 + px;
@@ -360,7 +423,7 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                         static_cast<float*>(p.out)[idx] = prob;
                 }
             }
-            acc_seq += it.rows;
+            aq += (uint32_t)it.rows;
         }
     }
 
@@ -370,17 +433,33 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
     if (warp == 0) ptx::tmem_dealloc(tbase, kSTmem);
 }
 
-// B tiles (BF16) and FP32 constants from the forward-layout parameters (W1t[tap][co], b1,
-// W2t[ci][tap][co], b2, wh, bh): tile tap = [ci / 8][co][ci % 8].
+// Operands and constants from the forward-layout parameters (W1t[tap][co], b1, W2t[ci][tap][co], b2,
+// wh, bh; tap = 3 ky + kx):
+//   B1, per column tap kx: [chunk][co][8] BF16 with element k = ky < 3 holding W1[co][ky][kx]
+//   B2, per column tap kx: [chunk][n][8] BF16, n = 16 i + co, element ci holding W2[co][ci][2 - i][kx]
+//   constants: b1, b2, head weights, head bias, 1/255
 __global__ void st_tc_pack(const float* fwd, uint8_t* wpack) {
-    __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(wpack);
-    float* c = reinterpret_cast<float*>(wpack + kSB);
-    for (int i = threadIdx.x; i < 9 * 16 * 16; i += blockDim.x) {
-        const int tap = i / 256, co = (i / 16) % 16, ci = i % 16;
-        b[tap * 256 + ((ci / 8) * 16 + co) * 8 + (ci % 8)] = __float2bfloat16_rn(fwd[kFW2 + (ci * 9 + tap) * 16 + co]);
+    __nv_bfloat16* b1 = reinterpret_cast<__nv_bfloat16*>(wpack);
+    for (int i = threadIdx.x; i < kB1 / 2; i += blockDim.x) {
+        const int kx = i / 256, rem = i % 256, kk = (rem / 128) * 8 + rem % 8, co = (rem / 8) % 16;
+        b1[i] = __float2bfloat16_rn(kk < 3 ? fwd[kFW1 + (kk * 3 + kx) * 16 + co] : 0.f);
     }
-    for (int i = threadIdx.x; i < 160; i += blockDim.x) c[i] = fwd[kFW1 + i];  // W1t and b1
-    for (int i = threadIdx.x; i < 33; i += blockDim.x) c[160 + i] = fwd[kFB2 + i];  // b2, wh, bh
+    __nv_bfloat16* b2 = reinterpret_cast<__nv_bfloat16*>(wpack + kB1);
+    for (int i = threadIdx.x; i < kB2 / 2; i += blockDim.x) {
+        const int kx = i / 768, rem = i % 768, ci = (rem / 384) * 8 + rem % 8, n = (rem / 8) % 48;
+        const int ky = 2 - n / 16, co = n % 16;
+        b2[i] = __float2bfloat16_rn(fwd[kFW2 + (ci * 9 + ky * 3 + kx) * 16 + co]);
+    }
+    float* c = reinterpret_cast<float*>(wpack + kB1 + kB2);
+    for (int i = threadIdx.x; i < kSConst; i += blockDim.x) {
+        float v = 0.f;
+        if (i < 16) v = fwd[kFB1 + i];
+        else if (i < 32) v = fwd[kFB2 + (i - 16)];
+        else if (i < 48) v = fwd[kFWH + (i - 32)];
+        else if (i == kCBH) v = fwd[kFBH];
+        else if (i == kCInv) v = 1.0f / 255.0f;
+        c[i] = v;
+    }
 }
 
 struct StTcState {
@@ -414,7 +493,7 @@ mb_status st_tc_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int
         }
         net->st_state = S;
     }
-    if (!S->d_wpack) MB_TRY(dev_alloc((void**)&S->d_wpack, kSB + 208 * 4));
+    if (!S->d_wpack) MB_TRY(dev_alloc((void**)&S->d_wpack, kWpack));
     if (!S->h_err) {
         if (fault_oom()) {
             set_error("pinned allocation failed (MB_FAULT_OOM injected)");
@@ -435,7 +514,7 @@ mb_status st_tc_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int
         MB_CUDA(cudaDeviceGetAttribute(&S->n_sms, cudaDevAttrMultiProcessorCount, dev));
         MB_CUDA(cudaFuncSetAttribute(st_tc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem));
     }
-    // the forward copy changes while the student trains: pack it on every call (2,497 values)
+    // the forward copy changes while the student trains: pack it on every call
     st_tc_pack<<<1, 256, 0, st>>>(net->d_simt, S->d_wpack);
     count_launch();
     MB_CUDA(cudaGetLastError());
@@ -455,8 +534,9 @@ mb_status st_tc_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int
     p.rows = (int)rows;
     p.cols = (int)cols;
     p.out_u8 = ot == MB_OUT_U8 ? 1 : 0;
-    p.n_strips = (int)((cols + 127) / 128);
-    // rows per item: at least two items per CTA slot when the region is large, 64 at most
+    p.n_strips = (int)((cols + kSW - 1) / kSW);
+    // rows per item: at least two items per CTA slot when the region is large, 64 at most (each item
+    // computes two extra layer-1 rows)
     const int64_t slots = (int64_t)S->n_sms * 2;
     int rpi = 64;
     while (rpi > 8 && z * p.n_strips * ((rows + rpi - 1) / rpi) < 2 * slots) rpi /= 2;
