@@ -195,16 +195,31 @@ mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t 
                                    mb_out_type out_type, void* stream);
 
 /*
- * Autotuner of the persistent tensor-core kernel: times each candidate number of output rows
- * per work item (64 .. 1024) on a synthetic h x w x z workload on `stream`, keeps the fastest in
- * the net, and records it in the JSON cache at cache_path (HOST string, may be NULL) keyed on
- * GPU name, precision and shape. A cached entry is reused without timing. choice_out (HOST, may
- * be NULL) receives {rows_per_item, stages (the activation-ring depth, fixed), from_cache}. FP8
- * nets split a launch's rows evenly over the CTAs instead (measured faster for FP8, slower for
- * BF16): for them nothing is timed and rows_per_item is reported as 0. Synchronous.
+ * Autotuner of the persistent tensor-core teacher kernel (BF16/FP8 teacher nets). Its knobs:
+ *  - stages: the depth of the kernel's two A-operand rings (staged layer-2 and layer-3 input rows)
+ *    and so how far the layer-1 producers and the layer-2 epilogue may run ahead of the MMAs;
+ *    compiled depths BF16 4, 5, 6 and FP8 4, 6, 8 (FP8 rows take half the bytes);
+ *  - rows_per_item (BF16 only): output rows per work item, 64 .. 1024 (each item restarts the row
+ *    pipeline: 9 extra rows); FP8 launches split their rows evenly over the CTAs instead (measured
+ *    faster for FP8, slower for BF16), so for them it is reported as 0.
+ * The strip width (118 output columns per 128-pixel MMA) is not a knob: a narrower strip costs the
+ * same MMAs for fewer columns. Every candidate gives bitwise the same maps.
+ * Times every candidate on a synthetic h x w x z workload on `stream` (median of 4 launches after
+ * one), keeps the fastest in the net and records it in the JSON cache at cache_path (HOST string,
+ * may be NULL) keyed on GPU name, precision and shape; a cached entry is reused without timing.
+ * choice_out (HOST, may be NULL) receives {rows_per_item, stages, from_cache}. Synchronous.
  */
 mb_status mb_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path,
                       int32_t* choice_out, void* stream);
+
+/*
+ * Apply a known tuning choice (for example one recorded by mb_autotune on the same GPU) without
+ * timing: rows_per_item 64, 128, 256, 512 or 1024 for BF16 (0 for FP8) and stages among the
+ * compiled depths of the net's precision (BF16 4, 5, 6; FP8 4, 6, 8). Other values return
+ * MB_ERR_INVALID_ARG; nets without the tensor-core teacher kernel MB_ERR_UNSUPPORTED. Drops the
+ * net's captured batch graphs (they hold the previous choice).
+ */
+mb_status mb_set_tuning(mb_net* net, int32_t rows_per_item, int32_t stages);
 
 /*
  * Student loss and gradient on n slices (device, in[n][h][w] uint8; target[n][h][w] float32):

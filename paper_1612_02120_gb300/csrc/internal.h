@@ -86,7 +86,7 @@ struct mb_net {
     cudaEvent_t slab_events[6] = {};                              // per buffer: in, comp, out
     // persistent kernel tuning
     int rows_per_item = 64;
-    int stages = 2;
+    int stages = 6;  // teacher A-ring depth (a compiled candidate; set by the autotuner or mb_set_tuning)
     bool tuned = false;
     // batch graph cache
     std::vector<mb::GraphCacheEntry*> graphs;

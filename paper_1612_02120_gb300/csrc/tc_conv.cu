@@ -45,7 +45,7 @@ constexpr int kPitch = 136;          // pixels per ring row (128 used + dx overr
 constexpr int kStrip = 118;          // valid output columns per 128-pixel strip
 constexpr int kInCols = 132;         // input columns read per row
 constexpr int kInRing = 8;           // input row ring
-constexpr int kRing = 6;             // mf1 / mf2 ring slots
+constexpr int kRingDefault = 6;      // mf1 / mf2 ring slots (the A operands of layers 2 and 3) until tuned
 constexpr int kMaxBlocks = 64;       // blocks per launch (kernel-parameter table)
 constexpr int kWpackConstOff = 2 * 10 * 5120;  // constants follow the largest packed B (BF16)
 constexpr uint64_t kWaitNs = 4000000000ull;
@@ -76,8 +76,11 @@ struct TcParams {
     TcBlockDesc blk[kMaxBlocks];
 };
 
-template <bool FP8>
+// RING: depth of the two A-operand rings (staged rows of the layer-2 and layer-3 inputs), a tuning
+// parameter chosen at run time among compiled depths (BF16 4, 5, 6; FP8 4, 6, 8).
+template <bool FP8, int RING = kRingDefault>
 struct Cfg {
+    static constexpr int kRing = RING;
     static constexpr int kChunks = FP8 ? 2 : 4;                 // 16-byte channel chunks per pixel
     static constexpr int kSlotBytes = kChunks * kPitch * 16;
     static constexpr int kGroups = FP8 ? 5 : 10;                // MMAs per (layer, input row, run)
@@ -360,9 +363,10 @@ __device__ __forceinline__ void issue_row(uint32_t tcol0, uint32_t acc_base_seq,
     }
 }
 
-template <bool FP8>
+template <bool FP8, int RING>
 __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_constant__ TcParams p) {
-    using C = Cfg<FP8>;
+    using C = Cfg<FP8, RING>;
+    constexpr int kRing = C::kRing;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* barmem = reinterpret_cast<uint64_t*>(smem + C::oBar);
     Bars B;
@@ -937,6 +941,29 @@ void tc_release(mb_net* net) {
 
 static int g_num_sms = 0;
 
+// A-ring depths compiled per precision; the tuned depth picks the instantiation.
+constexpr int kBf16Rings[] = {4, 5, 6};
+constexpr int kFp8Rings[] = {4, 6, 8};
+
+static bool ring_supported(bool fp8, int ring) {
+    for (int r : fp8 ? kFp8Rings : kBf16Rings)
+        if (r == ring) return true;
+    return false;
+}
+
+template <bool FP8, int RING>
+static mb_status launch_ring(TcParams& prm, int grid, cudaStream_t st) {
+    using C = Cfg<FP8, RING>;
+    static bool attr = false;  // per instantiation
+    if (!attr) {
+        MB_CUDA(cudaFuncSetAttribute(tc_fused_teacher<FP8, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     C::kSmem));
+        attr = true;
+    }
+    tc_fused_teacher<FP8, RING><<<grid, kThreads, C::kSmem, st>>>(prm);
+    return MB_OK;
+}
+
 static mb_status launch_tc(mb_net* net, TcParams& prm, cudaStream_t st) {
     const bool fp8 = net->prec == MB_PREC_FP8;
     if (g_num_sms == 0) {
@@ -944,25 +971,25 @@ static mb_status launch_tc(mb_net* net, TcParams& prm, cudaStream_t st) {
         MB_CUDA(cudaGetDevice(&dev));
         MB_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    const int smem = fp8 ? Cfg<true>::kSmem : Cfg<false>::kSmem;
     // FP8 (even split of the rows): one CTA per SM, or fewer when a CTA would get under 64 rows
     const int grid = fp8 ? (int)std::max<int64_t>(1, std::min<int64_t>(g_num_sms, (prm.total_rows + 63) / 64))
                          : std::max(1, std::min(prm.n_items, g_num_sms));
+    const int ring = ring_supported(fp8, net->stages) ? net->stages : kRingDefault;
+    mb_status s = MB_OK;
     if (fp8) {
-        static bool attr = false;
-        if (!attr) {
-            MB_CUDA(cudaFuncSetAttribute(tc_fused_teacher<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr = true;
+        switch (ring) {
+            case 4: s = launch_ring<true, 4>(prm, grid, st); break;
+            case 8: s = launch_ring<true, 8>(prm, grid, st); break;
+            default: s = launch_ring<true, 6>(prm, grid, st); break;
         }
-        tc_fused_teacher<true><<<grid, kThreads, smem, st>>>(prm);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            MB_CUDA(cudaFuncSetAttribute(tc_fused_teacher<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-            attr = true;
+        switch (ring) {
+            case 4: s = launch_ring<false, 4>(prm, grid, st); break;
+            case 5: s = launch_ring<false, 5>(prm, grid, st); break;
+            default: s = launch_ring<false, 6>(prm, grid, st); break;
         }
-        tc_fused_teacher<false><<<grid, kThreads, smem, st>>>(prm);
     }
+    MB_TRY(s);
     count_launch();
     MB_CUDA(cudaGetLastError());
     return MB_OK;
@@ -1188,7 +1215,7 @@ static bool cache_lookup(const char* path, const std::string& key, int* rows, in
         if (r && s) {
             *rows = atoi(r + 17);
             *stages = atoi(s + 10);
-            found = *rows > 0 && *stages > 0;
+            found = *rows >= 0 && *stages > 0;
         }
     }
     fclose(f);
@@ -1206,25 +1233,18 @@ static void cache_store(const char* path, const std::string& key, int rows, int 
 
 mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path, int32_t* choice,
                       cudaStream_t st) {
-    if (net->prec == MB_PREC_FP8) {
-        // FP8 launches split their rows evenly over the CTAs: there is no item length to tune
-        if (choice) {
-            choice[0] = 0;
-            choice[1] = net->stages;
-            choice[2] = 0;
-        }
-        return MB_OK;
-    }
+    // FP8 launches split their rows evenly over the CTAs, so their only knob is the ring depth.
+    const bool fp8 = net->prec == MB_PREC_FP8;
     int dev = 0;
     MB_CUDA(cudaGetDevice(&dev));
     const std::string key = tune_key(dev, net->prec, z, h, w);
     int rows = 0, stages = 0;
-    if (cache_lookup(cache_path, key, &rows, &stages)) {
-        net->rows_per_item = rows;
+    if (cache_lookup(cache_path, key, &rows, &stages) && ring_supported(fp8, stages) && (fp8 || rows > 0)) {
+        if (!fp8) net->rows_per_item = rows;
         net->stages = stages;
         net->tuned = true;
         if (choice) {
-            choice[0] = rows;
+            choice[0] = fp8 ? 0 : rows;
             choice[1] = stages;
             choice[2] = 1;
         }
@@ -1246,7 +1266,8 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
     if (rc == MB_OK) {
         fill_bytes<<<1024, 256, 0, st>>>(in, z * h * w, 12345u);
         count_launch();
-        const int cand_rows[] = {64, 128, 256, 512, 1024};
+        const int cand_rows_bf16[] = {64, 128, 256, 512, 1024};
+        const int cand_rows_fp8[] = {0};
         mb_block b;
         b.in = in;
         b.z = z;
@@ -1258,11 +1279,15 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
         b.out_pitch = w;
         b.out_slice_pitch = h * w;
         const int64_t y0 = 0, x0 = 0;
-        for (int R : cand_rows) {
-            if (R > 2 * h && R != cand_rows[0]) continue;
-            {
-                const int S = kRing;  // A-ring depth: fixed at compile time, reported
-                net->rows_per_item = R;
+        const int* cand_rows = fp8 ? cand_rows_fp8 : cand_rows_bf16;
+        const int n_rows = fp8 ? 1 : 5;
+        const int* cand_rings = fp8 ? kFp8Rings : kBf16Rings;
+        for (int ir = 0; ir < n_rows && rc == MB_OK; ++ir) {
+            const int R = cand_rows[ir];
+            if (!fp8 && R > 2 * h && R != cand_rows[0]) continue;
+            for (int is = 0; is < 3 && rc == MB_OK; ++is) {
+                const int S = cand_rings[is];
+                net->rows_per_item = fp8 ? saved_rows : R;
                 net->stages = S;
                 float ms_rep[5] = {};
                 for (int rep = 0; rep < 5 && rc == MB_OK; ++rep) {
@@ -1283,7 +1308,7 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
                 const float med = 0.5f * (ms_rep[2] + ms_rep[3]);
                 if (med < best) {
                     best = med;
-                    best_r = R;
+                    best_r = fp8 ? saved_rows : R;
                     best_s = S;
                 }
             }
@@ -1304,9 +1329,9 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
     net->stages = best_s;
     net->tuned = true;
     drop_graphs(net);
-    cache_store(cache_path, key, best_r, best_s, best);
+    cache_store(cache_path, key, fp8 ? 0 : best_r, best_s, best);
     if (choice) {
-        choice[0] = best_r;
+        choice[0] = fp8 ? 0 : best_r;
         choice[1] = best_s;
         choice[2] = 0;
     }
@@ -1314,6 +1339,32 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
 }
 
 }  // namespace mb
+
+extern "C" mb_status mb_set_tuning(mb_net* net, int32_t rows_per_item, int32_t stages) {
+    mb::clear_error();
+    if (!net) {
+        mb::set_error("mb_set_tuning: net is NULL");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (net->family != mb::FAMILY_TEACHER || net->prec == MB_PREC_FP32) {
+        mb::set_error("mb_set_tuning: only the tensor-core teacher (BF16/FP8) has tunables");
+        return MB_ERR_UNSUPPORTED;
+    }
+    const bool fp8 = net->prec == MB_PREC_FP8;
+    const bool rows_ok = fp8 ? rows_per_item == 0
+                             : (rows_per_item == 64 || rows_per_item == 128 || rows_per_item == 256 ||
+                                rows_per_item == 512 || rows_per_item == 1024);
+    if (!rows_ok || !mb::ring_supported(fp8, stages)) {
+        mb::set_error("mb_set_tuning: (%d rows per item, %d stages) is not a candidate for %s", (int)rows_per_item,
+                      (int)stages, fp8 ? "FP8 (rows 0; stages 4, 6, 8)" : "BF16 (rows 64..1024; stages 4, 5, 6)");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (!fp8) net->rows_per_item = rows_per_item;
+    net->stages = stages;
+    net->tuned = true;
+    mb::drop_graphs(net);
+    return MB_OK;
+}
 
 extern "C" mb_status mb_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path,
                                  int32_t* choice_out, void* stream) {

@@ -81,7 +81,7 @@ def test_autotune_choice_and_cache(bf16, tmp_path):
     before = infer(bf16, v)
     cache = str(tmp_path / "tune.json")
     c1 = m.mb_autotune(bf16.handle, 2, 300, 260, cache)
-    assert not c1["from_cache"] and c1["rows_per_item"] in (64, 128, 256, 512, 1024) and c1["stages"] >= 2
+    assert not c1["from_cache"] and c1["rows_per_item"] in (64, 128, 256, 512, 1024) and c1["stages"] in (4, 5, 6)
     c2 = m.mb_autotune(bf16.handle, 2, 300, 260, cache)
     assert c2["from_cache"] and c2["rows_per_item"] == c1["rows_per_item"] and c2["stages"] == c1["stages"]
     np.testing.assert_array_equal(infer(bf16, v), before)
@@ -98,3 +98,65 @@ def test_fp32_batch_uses_per_block_path():
     for v, o in zip(vols, outs):
         np.testing.assert_array_equal(o.cpu().numpy(), infer(net, v))
     net.close()
+
+
+def test_every_tuning_candidate_gives_the_same_maps(bf16):
+    """The autotuner's knobs (rows per work item, A-ring depth) change the schedule, never a value:
+    every BF16 candidate, applied with mb_set_tuning, maps a volume and an uneven batch bitwise as
+    the default does."""
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    v = synth.em_volume(4010, 3, 300, 260)
+    shapes = [(2, 37, 300), (1, 256, 129), (3, 64, 64)]
+    vols, _, outs, blocks = make_blocks(shapes, 4011)
+    m.mb_set_tuning(bf16.handle, 1024, 6)
+    ref = infer(bf16, v)
+    m.mb_infer_batch(bf16.handle, blocks)
+    torch.cuda.synchronize()
+    ref_b = [o.clone() for o in outs]
+    for rows in (64, 128, 256, 512, 1024):
+        for stages in (4, 5, 6):
+            m.mb_set_tuning(bf16.handle, rows, stages)
+            np.testing.assert_array_equal(infer(bf16, v), ref, err_msg=f"rows {rows} stages {stages}")
+            for o in outs:
+                o.fill_(-1.0)
+            m.mb_infer_batch(bf16.handle, blocks)
+            torch.cuda.synchronize()
+            for a, b in zip(outs, ref_b):
+                assert torch.equal(a, b), (rows, stages)
+    m.mb_set_tuning(bf16.handle, 1024, 6)
+
+
+def test_fp8_tuning_candidates_and_cache(tmp_path):
+    """FP8 nets tune the ring depth only (rows per item reported as 0); every depth gives the same
+    maps; the choice is cached; invalid choices are rejected."""
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    net = make_net(T, m.MB_PREC_FP8, teacher_params())
+    cal = torch.from_numpy(synth.em_volume(synth.BASE_SEED + 3, 4, 256, 256)).cuda()
+    m.mb_calibrate_fp8(net.handle, cal, 4, 256, 256)
+    v = synth.em_volume(4012, 3, 200, 300)
+    ref = infer(net, v)
+    for stages in (4, 6, 8):
+        m.mb_set_tuning(net.handle, 0, stages)
+        np.testing.assert_array_equal(infer(net, v), ref, err_msg=f"stages {stages}")
+    cache = str(tmp_path / "tune.json")
+    c1 = m.mb_autotune(net.handle, 2, 300, 260, cache)
+    assert not c1["from_cache"] and c1["rows_per_item"] == 0 and c1["stages"] in (4, 6, 8)
+    c2 = m.mb_autotune(net.handle, 2, 300, 260, cache)
+    assert c2["from_cache"] and c2["stages"] == c1["stages"]
+    lib = m.load()
+    assert lib.mb_set_tuning(net.handle, 0, 5) == m.MB_ERR_INVALID_ARG      # not a compiled FP8 depth
+    assert lib.mb_set_tuning(net.handle, 64, 6) == m.MB_ERR_INVALID_ARG     # FP8 has no item length
+    net.close()
+
+
+def test_set_tuning_rejects_what_it_cannot_apply(bf16):
+    from paper_1612_02120_gb300 import membrane as m
+    lib = m.load()
+    assert lib.mb_set_tuning(bf16.handle, 96, 6) == m.MB_ERR_INVALID_ARG
+    assert lib.mb_set_tuning(bf16.handle, 256, 8) == m.MB_ERR_INVALID_ARG
+    assert lib.mb_set_tuning(None, 256, 6) == m.MB_ERR_INVALID_ARG
+    fp32 = make_net(T, m.MB_PREC_FP32, teacher_params())
+    assert lib.mb_set_tuning(fp32.handle, 256, 6) == m.MB_ERR_UNSUPPORTED
+    fp32.close()
