@@ -117,12 +117,11 @@ __device__ __forceinline__ uint64_t gtime() {
 
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                          uint64_t limit_ns) {
+    if (ptx::mbar_test(bar, parity)) return true;  // a completed phase costs one poll
     if (*abort_flag) return false;
-    if (ptx::mbar_test(bar, parity)) return true;
     const uint64_t t0 = gtime();
     uint32_t n = 0;
     while (!ptx::mbar_test(bar, parity)) {
-        __nanosleep(32);
         if ((++n & 255u) == 0) {
             if (*abort_flag) return false;
             if (gtime() - t0 > limit_ns) {

@@ -132,12 +132,11 @@ __device__ __forceinline__ uint64_t gtime() {
 // complete within kWaitNs, or immediately once the CTA is aborting.
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                            int* err, uint64_t limit_ns = kWaitNs) {
+    if (ptx::mbar_test(bar, parity)) return true;  // a completed phase costs one poll
     if (*abort_flag) return false;
-    if (ptx::mbar_test(bar, parity)) return true;
     const uint64_t t0 = gtime();
     uint32_t n = 0;
     while (!ptx::mbar_test(bar, parity)) {
-        __nanosleep(32);  // polls share the shared-memory pipe with the MMA operand reads
         if ((++n & 255u) == 0) {
             if (*abort_flag) return false;
             if (gtime() - t0 > limit_ns) {
