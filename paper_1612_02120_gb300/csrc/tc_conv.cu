@@ -584,7 +584,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(&B.a2_free[s]);
 #pragma unroll
-                for (int ch = 0; ch < 32; ++ch) v[ch] = fmaxf(fmaf(v[ch], cst[kCE2S + ch], cst[kCE2B + ch]), 0.f);
+                for (int ch = 0; ch < 32; ++ch)  // BF16: the scales are 1 and are not read
+                    v[ch] = fmaxf(FP8 ? fmaf(v[ch], cst[kCE2S + ch], cst[kCE2B + ch]) : v[ch] + cst[kCE2B + ch], 0.f);
                 if (j > 0) {
                     float (&m)[32] = prev;  // vertical max in place; prev is reloaded from v below
 #pragma unroll
@@ -638,7 +639,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                 float z = p.hb;
 #pragma unroll
                 for (int ch = 0; ch < 32; ++ch)
-                    z = fmaf(cst[kCHW + ch], fmaxf(fmaf(v[ch], cst[kCE3S + ch], cst[kCE3B + ch]), 0.f), z);
+                    z = fmaf(cst[kCHW + ch],
+                             fmaxf(FP8 ? fmaf(v[ch], cst[kCE3S + ch], cst[kCE3B + ch]) : v[ch] + cst[kCE3B + ch], 0.f), z);
                 const float prob = 1.0f / (1.0f + expf(-z));
                 if (col_ok && !*abort_flag) {
                     const int64_t idx = (int64_t)it.zi * d.out_slice + (int64_t)(it.y0 + y) * d.out_pitch + it.x0 + c;
