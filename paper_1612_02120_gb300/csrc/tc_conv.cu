@@ -433,9 +433,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
     const uint32_t tbase = *tmem_slot;
     const uint32_t smem_base = ptx::smem_u32(smem);
     // Register budget per warpgroup (launched with 128 per thread = the whole register file):
-    // MMA issuers + loader 64, layer-2 epilogue 112, layer-3 epilogue 80, layer-1 producers 232.
-    // Sum 488 <= 512 per thread-slot, so the producers' increase is always satisfiable.
-    static_assert(64 + 112 + 80 + 232 <= 4 * 128, "register budget exceeds the launch allocation");
+    // MMA issuers + loader 64, layer-2 epilogue 128, layer-3 epilogue 112 (both keep their
+    // per-channel constants in registers), layer-1 producers 200. Sum 504 <= 512 per thread-slot,
+    // so the producers' increase is always satisfiable.
+    static_assert(64 + 128 + 112 + 200 <= 4 * 128, "register budget exceeds the launch allocation");
     if (warp >= 4 && warp < 12) {
         // every accumulator starts at zero (the MMAs only accumulate)
         const uint32_t col0 = warp < 8 ? 0u : 256u;
@@ -561,13 +562,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         }
         // warp 3 has no role
     } else if (warp < 8) {
-        ptx::setmaxnreg_dec<112>();
+        // 128 = the launch allocation: no change
         // ================= layer-2 epilogue: bias, ReLU, max-filter -> A ring of layer 3 =======
         const int c = tid - 128;
         const int pw = warp - 4;
         float* stage = reinterpret_cast<float*>(smem + C::oSt2);
         uint32_t a2_seq = 0, m2_seq = 0;
         float prev[32];
+        // per-channel constants in registers (the waits are compiler barriers, so reads from shared
+        // memory would repeat every row, beside the MMA operand traffic)
+        // (FP8 reads its scales from shared memory: registers would not hold them as well)
+        float b2[32];
+#pragma unroll
+        for (int ch = 0; ch < 32; ++ch) b2[ch] = cst[kCE2B + ch];
         RangeIter range = range_begin(p);
         ItemInfo it;
         for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
@@ -584,8 +591,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(&B.a2_free[s]);
 #pragma unroll
-                for (int ch = 0; ch < 32; ++ch)  // BF16: the scales are 1 and are not read
-                    v[ch] = fmaxf(FP8 ? fmaf(v[ch], cst[kCE2S + ch], cst[kCE2B + ch]) : v[ch] + cst[kCE2B + ch], 0.f);
+                for (int ch = 0; ch < 32; ++ch)  // BF16: the scales are 1
+                    v[ch] = fmaxf(FP8 ? fmaf(v[ch], cst[kCE2S + ch], b2[ch]) : v[ch] + b2[ch], 0.f);
                 if (j > 0) {
                     float (&m)[32] = prev;  // vertical max in place; prev is reloaded from v below
 #pragma unroll
@@ -614,11 +621,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             m2_seq += N2 - 1;
         }
     } else if (warp < 12) {
-        ptx::setmaxnreg_dec<80>();
+        ptx::setmaxnreg_dec<112>();
         // ================= layer-3 epilogue: bias, ReLU, head, sigmoid, store ==================
         const int c = tid - 256;
         const int pw = warp - 8;
         uint32_t a3_seq = 0;
+        float b3[32], hw[32];  // per-channel constants in registers (FP8 scales stay in shared memory)
+#pragma unroll
+        for (int ch = 0; ch < 32; ++ch) {
+            b3[ch] = cst[kCE3B + ch];
+            hw[ch] = cst[kCHW + ch];
+        }
         RangeIter range = range_begin(p);
         ItemInfo it;
         for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
@@ -639,8 +652,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
                 float z = p.hb;
 #pragma unroll
                 for (int ch = 0; ch < 32; ++ch)
-                    z = fmaf(cst[kCHW + ch],
-                             fmaxf(FP8 ? fmaf(v[ch], cst[kCE3S + ch], cst[kCE3B + ch]) : v[ch] + cst[kCE3B + ch], 0.f), z);
+                    z = fmaf(hw[ch], fmaxf(FP8 ? fmaf(v[ch], cst[kCE3S + ch], b3[ch]) : v[ch] + b3[ch], 0.f), z);
                 const float prob = 1.0f / (1.0f + expf(-z));
                 if (col_ok && !*abort_flag) {
                     const int64_t idx = (int64_t)it.zi * d.out_slice + (int64_t)(it.y0 + y) * d.out_pitch + it.x0 + c;
@@ -653,7 +665,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             a3_seq += NR;
         }
     } else {
-        ptx::setmaxnreg_inc<232>();
+        ptx::setmaxnreg_inc<200>();
         // ================= layer 1 + max-filter producer ======================================
         // Thread = (channel group h = warp - 12, column quad): columns c0 = 4 lane .. c0 + 3,
         // channels 8h .. 8h+7. Every weight load is a warp-wide broadcast feeding four columns, and
