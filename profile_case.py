@@ -2,7 +2,7 @@
 captures of one kernel). `reps` launches of one path on a z x h x w synthetic volume (the
 generator of `synth`), so a capture of one kernel stays a few hundred MB on the device.
 
-    python profile_case.py --prec bf16 --z 4 --h 1024 --w 1024 --reps 3
+    python profile_case.py --prec bf16 --z 4 --h 1024 --w 1024 --reps 3 [--rows 1024 --stages 6]
     python profile_case.py --net fastmemb --prec bf16 --z 4 --reps 3
     python profile_case.py --net maskextend --prec fp16 --z 4 --h 512 --w 512
       (MaskExtend: `z` transfer steps on an h x w window per rep)
@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--h", type=int, default=1024)
     ap.add_argument("--w", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--rows", type=int, default=0, help="teacher: rows per work item (mb_set_tuning); 0 keeps the default")
+    ap.add_argument("--stages", type=int, default=0, help="teacher: A-ring depth (mb_set_tuning); 0 keeps the default")
     a = ap.parse_args()
     import torch
 
@@ -70,6 +72,8 @@ def main():
         net = m.Net(synth.TEACHER, prec, 0, synth.init_params(synth.TEACHER, synth.TEACHER_WEIGHT_SEED))
         if prec == m.MB_PREC_FP8:
             m.mb_calibrate_fp8(net.handle, x[: min(4, a.z)], min(4, a.z), a.h, a.w)
+        if a.stages and prec != m.MB_PREC_FP32:
+            m.mb_set_tuning(net.handle, a.rows if prec == m.MB_PREC_BF16 else 0, a.stages)
     for _ in range(a.reps):
         m.mb_infer_volume(net.handle, x, a.z, a.h, a.w, out)
     torch.cuda.synchronize()
