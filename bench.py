@@ -411,6 +411,13 @@ def main():
         refs = [oracle.forward_region(synth.TEACHER, params, vol[z]) for z in zs]
         p = {"bf16": {"mvox_s": value, "ms": ms_per_step,
                       "error": err_metrics([bf16_map[z] for z in zs], refs, TOL["bf16"])}}
+        # uint8 output (q = round(255 p)): 1 B/vox stored instead of 4, through the same kernel
+        out_u8 = torch.empty((Z, H, W), dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            ms = time_device(lambda: m.mb_infer_volume(net.handle, x, Z, H, W, out_u8, m.MB_OUT_U8, stream),
+                             args.steps, 3, stream, flush)
+        p["bf16_u8_out"] = {"mvox_s": vox / (statistics.mean(ms) / 1e3) / 1e6, "ms": statistics.mean(ms)}
+        del out_u8
         fp32 = m.Net(synth.TEACHER, m.MB_PREC_FP32, local, params)
         with torch.cuda.stream(stream):
             ms = time_device(lambda: m.mb_infer_volume(fp32.handle, x, Z, H, W, out, m.MB_OUT_F32, stream),
