@@ -214,73 +214,117 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
     if (warp == 0 || warp == 3) {
         // ================= MMA issuers: warp 0 lane 0 layer 1, warp 3 lane 0 layer 2 ================
         // Each issues, commits and finally drains only its own MMAs; they meet only through the
-        // layer-1 epilogue (layer 1 runs ahead as far as its 4 accumulators allow).
+        // layer-1 epilogue (layer 1 runs ahead as far as its 4 accumulators allow). A single thread's
+        // per-row instruction chain is what bounds the issue rate of MMAs this small, so ring
+        // positions are running slot/phase counters (no division per row), and a full layer-2 window
+        // is issued from one of three branches with compile-time instruction descriptors: it starts
+        // below slot 6 (one N = 48 MMA per column tap) or in slot 6 or 7 (split where it wraps).
         if (lane == 0) {
-            const bool l1 = warp == 0;
-            const uint64_t a1d = ptx::smem_desc(sbase + oSA1, kSPitch * 16, 128);
-            const uint64_t sd = ptx::smem_desc(sbase + oSS, kSPitch * 16, 128);
-            const uint64_t b1d = ptx::smem_desc(sbase + oSB1, 16 * 16, 128);
-            const uint64_t b2d = ptx::smem_desc(sbase + oSB2, 48 * 16, 128);
             constexpr uint32_t id16 = ptx::idesc_f32acc(ptx::kFmtBF16, 128, 16);
-            uint32_t rq = 0, aq = 0;  // operand / staged rows and layer-2 accumulator rows so far
+            constexpr uint32_t id32 = ptx::idesc_f32acc(ptx::kFmtBF16, 128, 32);
+            constexpr uint32_t id48 = ptx::idesc_f32acc(ptx::kFmtBF16, 128, 48);
             bool ok = true;
-            auto layer1 = [&](uint32_t q) {
-                const uint32_t sa = q % kNA1, sl = q % kKL;
-                ok = ok && wait_bar(&a1_full[sa], (q / kNA1) & 1, abort_flag, p.err, p.wait_ns);
-                ok = ok && wait_bar(&l1_free[sl], ((q / kKL) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                ptx::tc_fence_after();
-                if (ok) {
-                    const uint64_t arow = a1d + (uint64_t)((sa * kSRowB) >> 4);
+            if (warp == 0) {
+                static_assert(kNA1 == kKL, "one counter serves both layer-1 rings");
+                const uint64_t a1d = ptx::smem_desc(sbase + oSA1, kSPitch * 16, 128);
+                const uint64_t b1d = ptx::smem_desc(sbase + oSB1, 16 * 16, 128);
+                uint32_t s1 = 0, ph1 = 0;  // operand slot = layer-1 accumulator slot, and its phase
+                for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+                    const StItem it = st_item(p, k);
+                    if (it.rows == 0) continue;
+                    const int n_rows = it.rows + 2;
+                    for (int u = 0; u < n_rows; ++u) {
+                        ok = ok && wait_bar(&a1_full[s1], ph1, abort_flag, p.err, p.wait_ns);
+                        ok = ok && wait_bar(&l1_free[s1], ph1 ^ 1, abort_flag, p.err, p.wait_ns);
+                        ptx::tc_fence_after();
+                        if (ok) {
+                            const uint64_t arow = a1d + (uint64_t)((s1 * kSRowB) >> 4);
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx)
-                        ptx::mma_bf16(tbase + kL1Col + 16u * sl, arow + (uint64_t)kx,
-                                      b1d + (uint64_t)((kx * 512) >> 4), id16, kx ? 1u : 0u);
-                }
-                ptx::mma_commit(&a1_empty[sa]);
-                ptx::mma_commit(&l1_full[sl]);
-            };
-            // staged row u (sequence q) feeds output rows u-2+i, i = 0..2, with row tap 2-i
-            auto layer2 = [&](uint32_t q, int u, int R) {
-                const uint32_t ss = q % kNS;
-                ok = ok && wait_bar(&s_full[ss], (q / kNS) & 1, abort_flag, p.err, p.wait_ns);
-                if (u < R) {  // output row u starts here: its accumulator must have been drained
-                    const uint32_t qa = aq + (uint32_t)u;
-                    ok = ok && wait_bar(&l2_free[qa % kKA], ((qa / kKA) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
-                }
-                ptx::tc_fence_after();
-                const int ilo = max(0, 2 - u), ihi = min(2, R + 1 - u);
-                if (ok && ilo <= ihi) {
-                    const int s_lo = (int)((aq + (uint32_t)(u - 2 + ilo)) % kKA);
-                    const int iw = ilo + (kKA - s_lo);  // first block whose slot wraps to 0
-                    const int hi0 = iw <= ihi ? iw - 1 : ihi;
-                    const uint64_t arow = sd + (uint64_t)((ss * kSRowB) >> 4);
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) {
-                        const uint64_t bg = b2d + (uint64_t)((kx * kB2Group) >> 4);
-                        ptx::mma_bf16(tbase + 16u * s_lo, arow + (uint64_t)kx, bg + (uint64_t)(16 * ilo),
-                                      ptx::idesc_f32acc(ptx::kFmtBF16, 128, (uint32_t)(16 * (hi0 - ilo + 1))), 1u);
-                        if (iw <= ihi)
-                            ptx::mma_bf16(tbase, arow + (uint64_t)kx, bg + (uint64_t)(16 * iw),
-                                          ptx::idesc_f32acc(ptx::kFmtBF16, 128, (uint32_t)(16 * (ihi - iw + 1))), 1u);
+                            for (int kx = 0; kx < 3; ++kx)
+                                ptx::mma_bf16(tbase + kL1Col + 16u * s1, arow + (uint64_t)kx,
+                                              b1d + (uint64_t)((kx * 512) >> 4), id16, kx ? 1u : 0u);
+                        }
+                        ptx::mma_commit(&a1_empty[s1]);
+                        ptx::mma_commit(&l1_full[s1]);
+                        if (++s1 == kKL) {
+                            s1 = 0;
+                            ph1 ^= 1;
+                        }
                     }
                 }
-                ptx::mma_commit(&s_empty[ss]);
-                if (u >= 2 && u - 2 < R) ptx::mma_commit(&l2_full[(aq + (uint32_t)(u - 2)) % kKA]);
-            };
-            for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-                const StItem it = st_item(p, k);
-                if (it.rows == 0) continue;
-                const int R = it.rows, n_rows = R + 2;
-                for (int u = 0; u < n_rows; ++u) {
-                    if (l1)
-                        layer1(rq + (uint32_t)u);
-                    else
-                        layer2(rq + (uint32_t)u, u, R);
+            } else {
+                // staged row u of an item feeds output rows u-2+i, i = 0..2, with row tap 2-i; output
+                // row o of the item accumulates in slot (aq + o) mod kKA, aq = output rows before it
+                const uint64_t sd = ptx::smem_desc(sbase + oSS, kSPitch * 16, 128);
+                const uint64_t b2d = ptx::smem_desc(sbase + oSB2, 48 * 16, 128);
+                uint32_t ss = 0, sph = 0;  // staged slot and phase
+                uint32_t as = 0, aph = 0;  // slot and phase of the next output row to start
+                uint32_t ws = kKA - 2;     // slot of output row u - 2 (may be a row of no item)
+                for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
+                    const StItem it = st_item(p, k);
+                    if (it.rows == 0) continue;
+                    const int R = it.rows, n_rows = R + 2;
+                    for (int u = 0; u < n_rows; ++u) {
+                        ok = ok && wait_bar(&s_full[ss], sph, abort_flag, p.err, p.wait_ns);
+                        if (u < R)  // output row u starts here: its accumulator must have been drained
+                            ok = ok && wait_bar(&l2_free[as], aph ^ 1, abort_flag, p.err, p.wait_ns);
+                        ptx::tc_fence_after();
+                        const uint64_t arow = sd + (uint64_t)((ss * kSRowB) >> 4);
+                        if (ok && u >= 2 && u < R) {
+                            if (ws < kKA - 2) {
+#pragma unroll
+                                for (int kx = 0; kx < 3; ++kx)
+                                    ptx::mma_bf16(tbase + 16u * ws, arow + (uint64_t)kx,
+                                                  b2d + (uint64_t)((kx * kB2Group) >> 4), id48, 1u);
+                            } else if (ws == kKA - 2) {  // blocks 0-1 in slots 6-7, block 2 in slot 0
+#pragma unroll
+                                for (int kx = 0; kx < 3; ++kx) {
+                                    const uint64_t bg = b2d + (uint64_t)((kx * kB2Group) >> 4);
+                                    ptx::mma_bf16(tbase + 16u * (kKA - 2), arow + (uint64_t)kx, bg, id32, 1u);
+                                    ptx::mma_bf16(tbase, arow + (uint64_t)kx, bg + 32u, id16, 1u);
+                                }
+                            } else {  // block 0 in slot 7, blocks 1-2 in slots 0-1
+#pragma unroll
+                                for (int kx = 0; kx < 3; ++kx) {
+                                    const uint64_t bg = b2d + (uint64_t)((kx * kB2Group) >> 4);
+                                    ptx::mma_bf16(tbase + 16u * (kKA - 1), arow + (uint64_t)kx, bg, id16, 1u);
+                                    ptx::mma_bf16(tbase, arow + (uint64_t)kx, bg + 16u, id32, 1u);
+                                }
+                            }
+                        } else if (ok) {  // the first and last two staged rows: part of the window
+                            const int ilo = max(0, 2 - u), ihi = min(2, R + 1 - u);
+                            if (ilo <= ihi) {
+                                const int s_lo = (int)((ws + (uint32_t)ilo) % kKA);
+                                const int iw = ilo + (kKA - s_lo);  // first block whose slot wraps to 0
+                                const int hi0 = iw <= ihi ? iw - 1 : ihi;
+#pragma unroll
+                                for (int kx = 0; kx < 3; ++kx) {
+                                    const uint64_t bg = b2d + (uint64_t)((kx * kB2Group) >> 4);
+                                    ptx::mma_bf16(tbase + 16u * s_lo, arow + (uint64_t)kx, bg + (uint64_t)(16 * ilo),
+                                                  ptx::idesc_f32acc(ptx::kFmtBF16, 128, (uint32_t)(16 * (hi0 - ilo + 1))), 1u);
+                                    if (iw <= ihi)
+                                        ptx::mma_bf16(tbase, arow + (uint64_t)kx, bg + (uint64_t)(16 * iw),
+                                                      ptx::idesc_f32acc(ptx::kFmtBF16, 128, (uint32_t)(16 * (ihi - iw + 1))), 1u);
+                                }
+                            }
+                        }
+                        ptx::mma_commit(&s_empty[ss]);
+                        if (u >= 2) ptx::mma_commit(&l2_full[ws]);  // output row u - 2 is complete
+                        if (++ss == kNS) {
+                            ss = 0;
+                            sph ^= 1;
+                        }
+                        if (u < R && ++as == kKA) {
+                            as = 0;
+                            aph ^= 1;
+                        }
+                        if (++ws == kKA) ws = 0;
+                    }
+                    // the next item's first window starts two rows before its output row 0
+                    ws = (ws + kKA - 2) % kKA;
                 }
-                rq += (uint32_t)n_rows;
-                aq += (uint32_t)R;
             }
-            uint64_t* f = fin + (l1 ? 0 : 1);
+            uint64_t* f = fin + (warp == 0 ? 0 : 1);
             ptx::mma_commit(f);
             const uint64_t t0 = gtime();
             while (!ptx::mbar_test(f, 0)) {
@@ -299,7 +343,7 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
         // keeps its three rows in registers and has the loads of the kLd rows after them in flight
         // (one thread also bulk-prefetches rows into L2).
         const int bt = tid - 32;
-        uint32_t rq = 0;
+        uint32_t slot = 0, sph = 0;  // operand slot and its phase
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const StItem it = st_item(p, k);
             if (it.rows == 0) continue;
@@ -338,8 +382,7 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                     const int u = u0 + t;
                     if (u >= n_rows) break;
                     prefetch_row(u + 3 + kPf);
-                    const uint32_t q = rq + (uint32_t)u, slot = q % kNA1;
-                    wait_bar(&a1_empty[slot], ((q / kNA1) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                    wait_bar(&a1_empty[slot], sph ^ 1, abort_flag, p.err, p.wait_ns);
                     uint8_t* dst = smem + oSA1 + slot * kSRowB;
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
@@ -349,6 +392,10 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                     }
                     ptx::fence_proxy_async_smem();
                     if (!p.fault_stall) ptx::mbar_arrive(&a1_full[slot]);
+                    if (++slot == kNA1) {
+                        slot = 0;
+                        sph ^= 1;
+                    }
                     // rows u+1 .. u+3 become the window; the loads of row u + 3 + kLd take row u+3's place
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
@@ -359,51 +406,57 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                     load_row(u + 3 + kLd, pend[t]);
                 }
             }
-            rq += (uint32_t)n_rows;
         }
     } else if (warp >= 4 && warp < 8) {
         // ================= layer-1 epilogue: x 1/255, bias, ReLU, BF16 -> staged feature ring =======
         const int px = tid - 128;
         const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
         const float inv = cst[kCInv];
-        uint32_t rq = 0;
+        uint32_t sl = 0, lph = 0, ss = 0, sph = 0;  // accumulator and staged slots, their phases
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const StItem it = st_item(p, k);
             if (it.rows == 0) continue;
             const int n_rows = it.rows + 2;
             for (int u = 0; u < n_rows; ++u) {
-                const uint32_t q = rq + (uint32_t)u, sl = q % kKL;
-                wait_bar(&l1_full[sl], (q / kKL) & 1, abort_flag, p.err, p.wait_ns);
+                wait_bar(&l1_full[sl], lph, abort_flag, p.err, p.wait_ns);
                 ptx::tc_fence_after();
                 float d[16];
                 ptx::tmem_ld16(tbase + lanes + kL1Col + 16u * sl, d);
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(&l1_free[sl]);
+                if (++sl == kKL) {
+                    sl = 0;
+                    lph ^= 1;
+                }
                 uint32_t wd[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
                     wd[c] = pack_bf16x2(fmaxf(fmaf(d[2 * c], inv, cst[kCB1 + 2 * c]), 0.f),
                                         fmaxf(fmaf(d[2 * c + 1], inv, cst[kCB1 + 2 * c + 1]), 0.f));
-                const uint32_t ss = q % kNS;
-                wait_bar(&s_empty[ss], ((q / kNS) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
+                wait_bar(&s_empty[ss], sph ^ 1, abort_flag, p.err, p.wait_ns);
                 uint8_t* dst = smem + oSS + ss * kSRowB;
                 *reinterpret_cast<uint4*>(dst + px * 16) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
                 *reinterpret_cast<uint4*>(dst + (kSPitch + px) * 16) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
                 ptx::fence_proxy_async_smem();
                 ptx::mbar_arrive(&s_full[ss]);
+                if (++ss == kNS) {
+                    ss = 0;
+                    sph ^= 1;
+                }
             }
-            rq += (uint32_t)n_rows;
         }
     } else if (warp >= 8) {
         // ================= layer-2 epilogue: bias, ReLU, head, sigmoid, store ========================
         const int px = tid - 256;  // TMEM lane = output pixel of the strip
         const uint32_t lanes = (uint32_t)(32 * (warp - 8)) << 16;
-        uint32_t aq = 0;
+        uint32_t sl = 0, aph = 0;  // accumulator slot and its phase
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
             const StItem it = st_item(p, k);
-            for (int j = 0; j < it.rows; ++j) {
-                const uint32_t qa = aq + (uint32_t)j, sl = qa % kKA;
-                wait_bar(&l2_full[sl], (qa / kKA) & 1, abort_flag, p.err, p.wait_ns);
+            const bool col = px < it.ncol;
+            int64_t idx = (int64_t)it.z * p.out_slice + (int64_t)it.m0 * p.out_pitch + it.s0 + px;
+            for (int j = 0; j < it.rows; ++j, idx += p.out_pitch) {
+                wait_bar(&l2_full[sl], aph, abort_flag, p.err, p.wait_ns);
+                const bool live = !*abort_flag;  // read early: its latency overlaps the drain
                 ptx::tc_fence_after();
                 float d[16];
                 const uint32_t ta = tbase + lanes + 16u * sl;
@@ -411,19 +464,22 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                 ptx::tmem_st16_zero(ta);
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(&l2_free[sl]);
+                if (++sl == kKA) {
+                    sl = 0;
+                    aph ^= 1;
+                }
                 float z = cst[kCBH];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) z = fmaf(cst[kCWH + c], fmaxf(d[c] + cst[kCB2 + c], 0.f), z);
-                const float prob = 1.0f / (1.0f + expf(-z));
-                if (px < it.ncol && !*abort_flag) {
-                    const int64_t idx = (int64_t)it.z * p.out_slice + (int64_t)(it.m0 + j) * p.out_pitch + it.s0 + px;
+                // the correctly rounded reciprocal is the correctly rounded quotient 1 / x
+                const float prob = __frcp_rn(1.0f + expf(-z));
+                if (col && live) {
                     if (p.out_u8)
                         static_cast<uint8_t*>(p.out)[idx] = (uint8_t)fminf(floorf(255.0f * prob + 0.5f), 255.0f);
                     else
                         static_cast<float*>(p.out)[idx] = prob;
                 }
             }
-            aq += (uint32_t)it.rows;
         }
     }
 
