@@ -341,7 +341,8 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
         // bytes of rows r - 1 .. r + 1 (elements 0..2 of K chunk 0) at column x0 + s0 - 2 + q, both
         // mirror-padded at the slice borders. Builder thread b (warps 1-2) owns pixels b + 64 k; it
         // keeps its three rows in registers and has the loads of the kLd rows after them in flight
-        // (one thread also bulk-prefetches rows into L2).
+        // (one thread also bulk-prefetches rows into L2). A loaded byte is converted only when its
+        // row enters the window: converting it at the load would stall the thread on the load.
         const int bt = tid - 32;
         uint32_t slot = 0, sph = 0;  // operand slot and its phase
         for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
@@ -355,10 +356,14 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
             int col[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) col[i] = bt + 64 * i < nin ? refl(c0 + bt + 64 * i, p.w) : -1;
-            auto load_row = [&](int i, uint32_t (&v)[3]) {
+            auto load_row = [&](int i, uint32_t (&v)[3]) {  // raw bytes (columns past the strip read column 0)
                 const uint8_t* row = src + (int64_t)refl(rbase + min(i, last), p.h) * p.in_pitch;
 #pragma unroll
-                for (int j = 0; j < 3; ++j) v[j] = col[j] >= 0 ? bf16_of_byte((uint32_t)__ldg(row + col[j])) : 0u;
+                for (int j = 0; j < 3; ++j) v[j] = (uint32_t)__ldg(row + max(col[j], 0));
+            };
+            auto bf16_row = [&](uint32_t (&v)[3]) {  // raw bytes -> BF16 bits, zero past the strip
+#pragma unroll
+                for (int j = 0; j < 3; ++j) v[j] = col[j] >= 0 ? bf16_of_byte(v[j]) : 0u;
             };
             constexpr int kPf = 8;
             auto prefetch_row = [&](int i) {
@@ -374,6 +379,9 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
             load_row(0, w0);
             load_row(1, w1);
             load_row(2, w2);
+            bf16_row(w0);
+            bf16_row(w1);
+            bf16_row(w2);
 #pragma unroll
             for (int t = 0; t < kLd; ++t) load_row(3 + t, pend[t]);  // rows past the last are clamped to it
             for (int u0 = 0; u0 < n_rows; u0 += kLd) {
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                     for (int j = 0; j < 3; ++j) {
                         w0[j] = w1[j];
                         w1[j] = w2[j];
-                        w2[j] = pend[t][j];
+                        w2[j] = col[j] >= 0 ? bf16_of_byte(pend[t][j]) : 0u;
                     }
                     load_row(u + 3 + kLd, pend[t]);
                 }
