@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                 if (hi > lo) ptx::prefetch_l2_bulk((const void*)lo, (uint32_t)(hi - lo));
             };
             for (int i = 3; i < 3 + kPf; ++i) prefetch_row(i);
-            constexpr int kLd = 4;  // input rows whose loads are in flight
+            constexpr int kLd = 3;  // input rows whose loads are in flight
             uint32_t w0[3], w1[3], w2[3], pend[kLd][3];
             load_row(0, w0);
             load_row(1, w1);
