@@ -1,7 +1,8 @@
 """BF16 student inference on the tensor cores (the fused kernel of student_tc.cu) through the C ABI:
 parity with the FP64 oracle (BF16-rounded weights) at the BF16 bar over slice shapes that span
 strips, ragged edges and the minimum size; regions with their true context; uint8 output; host
-buffers; batches; a sampled check at a large size; a timed-out device wait."""
+buffers; batches; a volume against its slices one by one; a sampled check at a large size; a
+timed-out device wait."""
 import numpy as np
 import pytest
 
@@ -75,6 +76,16 @@ def test_u8_host_and_batch_paths(net):
     torch.cuda.synchronize()
     for i in range(3):
         np.testing.assert_array_equal(outs[i].cpu().numpy()[0], pf[i])
+
+
+def test_volume_equals_slice_by_slice(net):
+    """A many-slice launch walks every CTA's rings (operand, accumulator and staged-row slots and
+    their phases) through many wraps and item boundaries at other offsets than one-slice launches
+    do; the maps must not depend on where a row falls in them."""
+    v = synth.em_volume(7350, 7, 333, 517)
+    full = infer(net, v)
+    for zi in range(7):
+        np.testing.assert_array_equal(infer(net, v[zi:zi + 1])[0], full[zi])
 
 
 def test_sampled_crops_at_a_large_size(net):
