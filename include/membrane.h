@@ -199,9 +199,10 @@ mb_status mb_infer_batch_per_block(mb_net* net, const mb_block* blocks, int32_t 
  *  - stages: the depth of the kernel's two A-operand rings (staged layer-2 and layer-3 input rows)
  *    and so how far the layer-1 producers and the layer-2 epilogue may run ahead of the MMAs;
  *    compiled depths BF16 4, 5, 6 and FP8 4, 6, 8 (FP8 rows take half the bytes);
- *  - rows_per_item (BF16 only): output rows per work item, 64 .. 1024 (each item restarts the row
- *    pipeline: 9 extra rows); FP8 launches split their rows evenly over the CTAs instead (measured
- *    faster for FP8, slower for BF16), so for them it is reported as 0.
+ *  - rows_per_item (BF16): output rows per work item taken round-robin by the CTAs, 64 .. 1024
+ *    (each item restarts the row pipeline: 9 extra rows), or 0: the launch's strip-rows split into
+ *    one equal contiguous range per CTA (no tail wave; items are the runs of a range within one
+ *    strip). FP8 launches always split evenly (measured faster for FP8), reported as 0.
  * The strip width (118 output columns per 128-pixel MMA) is not a knob: a narrower strip costs the
  * same MMAs for fewer columns. Every candidate gives bitwise the same maps.
  * Times every candidate on a synthetic h x w x z workload on `stream` (median of 4 launches after
@@ -213,8 +214,20 @@ mb_status mb_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
                       int32_t* choice_out, void* stream);
 
 /*
+ * The same autotuner timed on the caller's own batch (configs of uneven blocks whose best schedule
+ * a single-volume shape does not predict): every candidate runs the whole batch as mb_infer_batch
+ * would (without its captured graph), so the blocks' outputs are written with valid maps; inputs are
+ * only read. blocks, n_blocks and out_type as for mb_infer_batch (same checks and errors). The cache
+ * key holds the GPU name, precision, output type and a hash of the blocks' shapes (z, h, w), not
+ * their addresses. A batch with no voxels returns MB_ERR_INVALID_ARG; nets without the tensor-core
+ * teacher kernel MB_ERR_UNSUPPORTED. choice_out as for mb_autotune. Synchronous.
+ */
+mb_status mb_autotune_batch(mb_net* net, const mb_block* blocks, int32_t n_blocks, mb_out_type out_type,
+                            const char* cache_path, int32_t* choice_out, void* stream);
+
+/*
  * Apply a known tuning choice (for example one recorded by mb_autotune on the same GPU) without
- * timing: rows_per_item 64, 128, 256, 512 or 1024 for BF16 (0 for FP8) and stages among the
+ * timing: rows_per_item 0, 64, 128, 256, 512 or 1024 for BF16 (0 for FP8) and stages among the
  * compiled depths of the net's precision (BF16 4, 5, 6; FP8 4, 6, 8). Other values return
  * MB_ERR_INVALID_ARG; nets without the tensor-core teacher kernel MB_ERR_UNSUPPORTED. Drops the
  * net's captured batch graphs (they hold the previous choice).

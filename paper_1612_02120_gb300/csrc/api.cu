@@ -772,6 +772,25 @@ mb_status mb_infer_batch(mb_net* net, const mb_block* blocks, int32_t n_blocks, 
                            (cudaStream_t)stream, true);
 }
 
+mb_status mb_autotune_batch(mb_net* net, const mb_block* blocks, int32_t n_blocks, mb_out_type out_type,
+                            const char* cache_path, int32_t* choice_out, void* stream) {
+    API_BEGIN
+    MB_TRY(check_ready(net));
+    MB_TRY(check_blocks(net, blocks, n_blocks, out_type));
+    if (net->family != FAMILY_TEACHER || net->prec == MB_PREC_FP32) {
+        set_error("mb_autotune_batch: only the tensor-core teacher (BF16/FP8) has tunables");
+        return MB_ERR_UNSUPPORTED;
+    }
+    int64_t vox = 0;
+    for (int i = 0; i < n_blocks; ++i) vox += blocks[i].z * blocks[i].h * blocks[i].w;
+    if (vox == 0) {
+        set_error("mb_autotune_batch: the batch has no voxels to time");
+        return MB_ERR_INVALID_ARG;
+    }
+    API_GUARD(net)
+    return tc_autotune_batch(net, blocks, n_blocks, out_type, cache_path, choice_out, (cudaStream_t)stream);
+}
+
 mb_status mb_student_loss_grad(mb_net* student, const uint8_t* in, const float* target, int64_t n, int64_t h,
                                int64_t w, double* loss, float* grad, void* stream) {
     API_BEGIN

@@ -164,6 +164,9 @@ struct TcItem;                       // work item (device layout in tc_conv.cu)
 mb_status tc_infer_blocks(mb_net* net, const mb_block* blocks, int n_blocks, const int64_t* y0,
                           const int64_t* x0, const int64_t* rows, const int64_t* cols, mb_out_type ot,
                           cudaStream_t st, bool use_graph);
+// Autotuner timed on the caller's own batch (its outputs are written by every candidate).
+mb_status tc_autotune_batch(mb_net* net, const mb_block* blocks, int n_blocks, mb_out_type ot, const char* cache_path,
+                            int32_t* choice, cudaStream_t st);
 
 // Student training and cascade.
 mb_status student_loss_grad(mb_net* s, const uint8_t* in, const float* tgt, int64_t n, int64_t h, int64_t w,

@@ -177,11 +177,12 @@ __device__ __forceinline__ ItemInfo decode_item(const TcParams& p, int k) {
     return it;
 }
 
-// Work split of the FP8 kernel: the launch's strip-rows, in (block, slice, strip, row) order, are
-// cut into one equal contiguous range per CTA, so every CTA computes the same number of rows and
-// no tail wave remains; a CTA's items are the parts of its range in one (block, slice, strip)
-// column. (The BF16 kernel walks round-robin items instead: measured 4.9 % faster for FP8 and
-// 1.4 % slower for BF16 on 1024x1024x32.) Every role of a CTA walks the same sequence.
+// Even-range work split (always for FP8; for BF16 when tuned to rows per item 0): the launch's
+// strip-rows, in (block, slice, strip, row) order, are cut into one equal contiguous range per CTA,
+// so every CTA computes the same number of rows and no tail wave remains; a CTA's items are the
+// parts of its range in one (block, slice, strip) column. The other split walks round-robin items
+// of a tuned number of rows. Chosen at compile time (a run-time choice in one kernel cost BF16
+// 1.9 %). Every role of a CTA walks the same sequence.
 struct RangeIter {
     int64_t r, hi;  // next strip-row, end of this CTA's range
 };
@@ -362,7 +363,7 @@ __device__ __forceinline__ void issue_row(uint32_t tcol0, uint32_t acc_base_seq,
     }
 }
 
-template <bool FP8, int RING>
+template <bool FP8, int RING, bool RNG>
 __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_constant__ TcParams p) {
     using C = Cfg<FP8, RING>;
     constexpr int kRing = C::kRing;
@@ -480,8 +481,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
             };
             RangeIter range = range_begin(p);
             ItemInfo it;
-            for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
-                if constexpr (!FP8) it = decode_item(p, k);
+            for (int k = blockIdx.x; RNG ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+                if constexpr (!RNG) it = decode_item(p, k);
                 const int NR = it.rows;
                 const int n_in = l2 ? NR + 9 : NR + 4;   // input rows of this layer
                 const int n_out = l2 ? NR + 5 : NR;      // output rows of this layer
@@ -528,8 +529,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         uint32_t in_seq = 0;
         RangeIter range = range_begin(p);
         ItemInfo it;
-        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
-            if constexpr (!FP8) it = decode_item(p, k);
+        for (int k = blockIdx.x; RNG ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!RNG) it = decode_item(p, k);
             const TcBlockDesc& d = p.blk[it.b];
             const uint8_t* src = d.in + (int64_t)it.zi * d.in_slice;
             const int nrows = it.rows + 14;
@@ -577,8 +578,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         for (int ch = 0; ch < 32; ++ch) b2[ch] = cst[kCE2B + ch];
         RangeIter range = range_begin(p);
         ItemInfo it;
-        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
-            if constexpr (!FP8) it = decode_item(p, k);
+        for (int k = blockIdx.x; RNG ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!RNG) it = decode_item(p, k);
             const int N2 = it.rows + 5;
             for (int j = 0; j < N2; ++j) {
                 const uint32_t q = a2_seq + j, s = q % C::kAcc;
@@ -634,8 +635,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         }
         RangeIter range = range_begin(p);
         ItemInfo it;
-        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
-            if constexpr (!FP8) it = decode_item(p, k);
+        for (int k = blockIdx.x; RNG ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!RNG) it = decode_item(p, k);
             const TcBlockDesc& d = p.blk[it.b];
             const int NR = it.rows;
             const bool col_ok = c < kStrip && it.x0 + c < d.rw;
@@ -676,8 +677,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_fused_teacher(const __grid_con
         float prev[4][8], cur[4][8];
         RangeIter range = range_begin(p);
         ItemInfo it;
-        for (int k = blockIdx.x; FP8 ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
-            if constexpr (!FP8) it = decode_item(p, k);
+        for (int k = blockIdx.x; RNG ? range_next(p, range, it) : k < p.n_items; k += gridDim.x) {
+            if constexpr (!RNG) it = decode_item(p, k);
             const int NR = it.rows;
             const int M1 = NR + 9;
             for (int t = -1; t < M1; ++t) {
@@ -964,16 +965,16 @@ static bool ring_supported(bool fp8, int ring) {
     return false;
 }
 
-template <bool FP8, int RING>
+template <bool FP8, int RING, bool RNG>
 static mb_status launch_ring(TcParams& prm, int grid, cudaStream_t st) {
     using C = Cfg<FP8, RING>;
     static bool attr = false;  // per instantiation
     if (!attr) {
-        MB_CUDA(cudaFuncSetAttribute(tc_fused_teacher<FP8, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MB_CUDA(cudaFuncSetAttribute(tc_fused_teacher<FP8, RING, RNG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      C::kSmem));
         attr = true;
     }
-    tc_fused_teacher<FP8, RING><<<grid, kThreads, C::kSmem, st>>>(prm);
+    tc_fused_teacher<FP8, RING, RNG><<<grid, kThreads, C::kSmem, st>>>(prm);
     return MB_OK;
 }
 
@@ -984,22 +985,29 @@ static mb_status launch_tc(mb_net* net, TcParams& prm, cudaStream_t st) {
         MB_CUDA(cudaGetDevice(&dev));
         MB_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    // FP8 (even split of the rows): one CTA per SM, or fewer when a CTA would get under 64 rows
-    const int grid = fp8 ? (int)std::max<int64_t>(1, std::min<int64_t>(g_num_sms, (prm.total_rows + 63) / 64))
+    // even split of the rows: one CTA per SM, or fewer when a CTA would get under 64 rows
+    const bool rng = fp8 || net->rows_per_item == 0;
+    const int grid = rng ? (int)std::max<int64_t>(1, std::min<int64_t>(g_num_sms, (prm.total_rows + 63) / 64))
                          : std::max(1, std::min(prm.n_items, g_num_sms));
     const int ring = ring_supported(fp8, net->stages) ? net->stages : kRingDefault;
     mb_status s = MB_OK;
     if (fp8) {
         switch (ring) {
-            case 4: s = launch_ring<true, 4>(prm, grid, st); break;
-            case 8: s = launch_ring<true, 8>(prm, grid, st); break;
-            default: s = launch_ring<true, 6>(prm, grid, st); break;
+            case 4: s = launch_ring<true, 4, true>(prm, grid, st); break;
+            case 8: s = launch_ring<true, 8, true>(prm, grid, st); break;
+            default: s = launch_ring<true, 6, true>(prm, grid, st); break;
+        }
+    } else if (rng) {
+        switch (ring) {
+            case 4: s = launch_ring<false, 4, true>(prm, grid, st); break;
+            case 5: s = launch_ring<false, 5, true>(prm, grid, st); break;
+            default: s = launch_ring<false, 6, true>(prm, grid, st); break;
         }
     } else {
         switch (ring) {
-            case 4: s = launch_ring<false, 4>(prm, grid, st); break;
-            case 5: s = launch_ring<false, 5>(prm, grid, st); break;
-            default: s = launch_ring<false, 6>(prm, grid, st); break;
+            case 4: s = launch_ring<false, 4, false>(prm, grid, st); break;
+            case 5: s = launch_ring<false, 5, false>(prm, grid, st); break;
+            default: s = launch_ring<false, 6, false>(prm, grid, st); break;
         }
     }
     MB_TRY(s);
@@ -1017,9 +1025,11 @@ static int fill_blocks(mb_net* net, TcParams& prm, const mb_block* blocks, int n
     // Rows per work item: the tuned value, unless the launch would not fill one wave of CTAs (a
     // streamed slab, a few small blocks). Then the candidates R, R/2, .. 64 are compared by the
     // predicted time, waves x (rows + 9) (each item restarts the layer-2 row pipeline, 9 extra
-    // rows), ties to the larger R. The choice never changes a result.
-    int R = std::max(8, net->rows_per_item);
-    {
+    // rows), ties to the larger R. The choice never changes a result. (The even-range split, rows
+    // per item 0, takes its items from the ranges; R then only sizes the unused item table.)
+    const bool even_split = net->prec == MB_PREC_FP8 || net->rows_per_item == 0;
+    int R = even_split ? 1024 : std::max(8, net->rows_per_item);
+    if (!even_split) {
         if (g_num_sms == 0) {
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1244,18 +1254,20 @@ static void cache_store(const char* path, const std::string& key, int rows, int 
     fclose(f);
 }
 
-mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path, int32_t* choice,
-                      cudaStream_t st) {
-    // FP8 launches split their rows evenly over the CTAs, so their only knob is the ring depth.
+// Times every candidate on one workload (`run` launches it once on `st`; median of 4 launches
+// after one), keeps the fastest in the net and records it under `key` in the cache. A cached entry
+// is applied without timing. Candidates whose rows per item exceed twice the workload's tallest
+// block are skipped (they equal the largest useful one), except the smallest and the even split.
+template <class Run>
+static mb_status tune_candidates(mb_net* net, const std::string& key, const char* cache_path, int32_t* choice,
+                                 cudaStream_t st, int64_t max_rows, Run run) {
     const bool fp8 = net->prec == MB_PREC_FP8;
-    int dev = 0;
-    MB_CUDA(cudaGetDevice(&dev));
-    const std::string key = tune_key(dev, net->prec, z, h, w);
     int rows = 0, stages = 0;
-    if (cache_lookup(cache_path, key, &rows, &stages) && ring_supported(fp8, stages) && (fp8 || rows > 0)) {
+    if (cache_lookup(cache_path, key, &rows, &stages) && ring_supported(fp8, stages) && (fp8 || rows >= 0)) {
         if (!fp8) net->rows_per_item = rows;
         net->stages = stages;
         net->tuned = true;
+        drop_graphs(net);
         if (choice) {
             choice[0] = fp8 ? 0 : rows;
             choice[1] = stages;
@@ -1263,12 +1275,9 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
         }
         return MB_OK;
     }
-    uint8_t* in = nullptr;
-    float* out = nullptr;
-    MB_TRY(dev_alloc((void**)&in, (size_t)(z * h * w)));
-    mb_status rc = dev_alloc((void**)&out, (size_t)(z * h * w) * 4);
+    mb_status rc = MB_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (rc == MB_OK) {
+    {
         cudaError_t e = cudaEventCreate(&e0);
         if (e == cudaSuccess) e = cudaEventCreate(&e1);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__);
@@ -1277,27 +1286,14 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
     int best_r = saved_rows, best_s = saved_stages;
     float best = 1e30f;
     if (rc == MB_OK) {
-        fill_bytes<<<1024, 256, 0, st>>>(in, z * h * w, 12345u);
-        count_launch();
-        const int cand_rows_bf16[] = {64, 128, 256, 512, 1024};
+        const int cand_rows_bf16[] = {64, 128, 256, 512, 1024, 0};  // 0: the even-range split
         const int cand_rows_fp8[] = {0};
-        mb_block b;
-        b.in = in;
-        b.z = z;
-        b.h = h;
-        b.w = w;
-        b.in_pitch = w;
-        b.in_slice_pitch = h * w;
-        b.out = out;
-        b.out_pitch = w;
-        b.out_slice_pitch = h * w;
-        const int64_t y0 = 0, x0 = 0;
         const int* cand_rows = fp8 ? cand_rows_fp8 : cand_rows_bf16;
-        const int n_rows = fp8 ? 1 : 5;
+        const int n_rows = fp8 ? 1 : 6;
         const int* cand_rings = fp8 ? kFp8Rings : kBf16Rings;
         for (int ir = 0; ir < n_rows && rc == MB_OK; ++ir) {
             const int R = cand_rows[ir];
-            if (!fp8 && R > 2 * h && R != cand_rows[0]) continue;
+            if (!fp8 && R > 2 * max_rows && R != cand_rows[0] && R != 0) continue;
             for (int is = 0; is < 3 && rc == MB_OK; ++is) {
                 const int S = cand_rings[is];
                 net->rows_per_item = fp8 ? saved_rows : R;
@@ -1306,7 +1302,7 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
                 for (int rep = 0; rep < 5 && rc == MB_OK; ++rep) {
                     cudaError_t e = cudaEventRecord(e0, st);
                     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__); break; }
-                    rc = tc_infer_blocks(net, &b, 1, &y0, &x0, &h, &w, MB_OUT_F32, st, false);
+                    rc = run();
                     if (rc != MB_OK) break;
                     e = cudaEventRecord(e1, st);
                     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1325,13 +1321,10 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
                     best_s = S;
                 }
             }
-            if (rc != MB_OK) break;
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    dev_free(in);
-    dev_free(out);
     if (rc == MB_OK) rc = check_err(net);
     if (rc != MB_OK) {
         net->rows_per_item = saved_rows;
@@ -1351,6 +1344,71 @@ mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* 
     return MB_OK;
 }
 
+mb_status tc_autotune(mb_net* net, int64_t z, int64_t h, int64_t w, const char* cache_path, int32_t* choice,
+                      cudaStream_t st) {
+    int dev = 0;
+    MB_CUDA(cudaGetDevice(&dev));
+    const std::string key = tune_key(dev, net->prec, z, h, w);
+    uint8_t* in = nullptr;
+    float* out = nullptr;
+    MB_TRY(dev_alloc((void**)&in, (size_t)(z * h * w)));
+    mb_status rc = dev_alloc((void**)&out, (size_t)(z * h * w) * 4);
+    if (rc == MB_OK) {
+        fill_bytes<<<1024, 256, 0, st>>>(in, z * h * w, 12345u);
+        count_launch();
+        mb_block b;
+        b.in = in;
+        b.z = z;
+        b.h = h;
+        b.w = w;
+        b.in_pitch = w;
+        b.in_slice_pitch = h * w;
+        b.out = out;
+        b.out_pitch = w;
+        b.out_slice_pitch = h * w;
+        const int64_t y0 = 0, x0 = 0;
+        rc = tune_candidates(net, key, cache_path, choice, st, h,
+                             [&] { return tc_infer_blocks(net, &b, 1, &y0, &x0, &h, &w, MB_OUT_F32, st, false); });
+    }
+    dev_free(in);
+    dev_free(out);
+    return rc;
+}
+
+mb_status tc_autotune_batch(mb_net* net, const mb_block* blocks, int n_blocks, mb_out_type ot, const char* cache_path,
+                            int32_t* choice, cudaStream_t st) {
+    int dev = 0;
+    MB_CUDA(cudaGetDevice(&dev));
+    // key: GPU, precision, output type and the blocks' shapes (FNV-1a over z, h, w of each block)
+    uint64_t hsh = 1469598103934665603ull;
+    int64_t max_h = 8, vox = 0;
+    std::vector<int64_t> y0(n_blocks, 0), x0(n_blocks, 0), rows(n_blocks), cols(n_blocks);
+    for (int i = 0; i < n_blocks; ++i) {
+        const int64_t v3[3] = {blocks[i].z, blocks[i].h, blocks[i].w};
+        for (int64_t v : v3)
+            for (int byte = 0; byte < 8; ++byte) {
+                hsh ^= (uint64_t)((v >> (8 * byte)) & 0xff);
+                hsh *= 1099511628211ull;
+            }
+        rows[i] = blocks[i].h;
+        cols[i] = blocks[i].w;
+        max_h = std::max<int64_t>(max_h, blocks[i].h);
+        vox += blocks[i].z * blocks[i].h * blocks[i].w;
+    }
+    cudaDeviceProp pr;
+    const char* name = cudaGetDeviceProperties(&pr, dev) == cudaSuccess ? pr.name : "unknown";
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s|%s|batch|%s|%d blocks|%lld vox|%016llx", name,
+             net->prec == MB_PREC_FP8 ? "fp8" : "bf16", ot == MB_OUT_U8 ? "u8" : "f32", n_blocks, (long long)vox,
+             (unsigned long long)hsh);
+    std::string key = buf;
+    for (char& c : key)
+        if (c == '"' || c == '\\') c = '_';
+    return tune_candidates(net, key, cache_path, choice, st, max_h, [&] {
+        return tc_infer_blocks(net, blocks, n_blocks, y0.data(), x0.data(), rows.data(), cols.data(), ot, st, false);
+    });
+}
+
 }  // namespace mb
 
 extern "C" mb_status mb_set_tuning(mb_net* net, int32_t rows_per_item, int32_t stages) {
@@ -1365,11 +1423,11 @@ extern "C" mb_status mb_set_tuning(mb_net* net, int32_t rows_per_item, int32_t s
     }
     const bool fp8 = net->prec == MB_PREC_FP8;
     const bool rows_ok = fp8 ? rows_per_item == 0
-                             : (rows_per_item == 64 || rows_per_item == 128 || rows_per_item == 256 ||
-                                rows_per_item == 512 || rows_per_item == 1024);
+                             : (rows_per_item == 0 || rows_per_item == 64 || rows_per_item == 128 ||
+                                rows_per_item == 256 || rows_per_item == 512 || rows_per_item == 1024);
     if (!rows_ok || !mb::ring_supported(fp8, stages)) {
         mb::set_error("mb_set_tuning: (%d rows per item, %d stages) is not a candidate for %s", (int)rows_per_item,
-                      (int)stages, fp8 ? "FP8 (rows 0; stages 4, 6, 8)" : "BF16 (rows 64..1024; stages 4, 5, 6)");
+                      (int)stages, fp8 ? "FP8 (rows 0; stages 4, 6, 8)" : "BF16 (rows 0 or 64..1024; stages 4, 5, 6)");
         return MB_ERR_INVALID_ARG;
     }
     if (!fp8) net->rows_per_item = rows_per_item;

@@ -23,7 +23,7 @@ EXPORTED = (
     "mb_calibrate_fp8", "mb_infer_volume", "mb_infer_region", "mb_infer_batch", "mb_infer_batch_per_block",
     "mb_autotune", "mb_student_loss_grad", "mb_student_train", "mb_infer_cascade", "mb_status_string",
     "mb_last_error", "mb_launch_count", "mb_infer_volume_noalloc", "mb_infer_volume_subsampled", "mb_mask_extend",
-    "mb_mask_extend_dir", "mb_set_tuning",
+    "mb_mask_extend_dir", "mb_set_tuning", "mb_autotune_batch",
 )
 
 
@@ -76,6 +76,7 @@ def load() -> ctypes.CDLL:
         "mb_infer_batch_per_block": ([p, p, i32, i32, p], st),
         "mb_autotune": ([p, i64, i64, i64, ctypes.c_char_p, p, p], st),
         "mb_set_tuning": ([p, i32, i32], st),
+        "mb_autotune_batch": ([p, p, i32, i32, ctypes.c_char_p, p, p], st),
         "mb_student_loss_grad": ([p, p, p, i64, i64, i64, p, p, p], st),
         "mb_student_train": ([p, p, p, i64, i64, i64, p, ctypes.c_char_p, p, p], st),
         "mb_infer_cascade": ([p, p, p, i64, i64, i64, p, i32, f32, f32, f32, p, p, p], st),
@@ -240,6 +241,14 @@ def mb_autotune(net, z, h, w, cache_path=None, stream=None):
     choice = (ctypes.c_int32 * 3)()
     check(load().mb_autotune(net, z, h, w, cache_path.encode() if cache_path else None, choice,
                              stream_handle(stream)), "mb_autotune")
+    return {"rows_per_item": choice[0], "stages": choice[1], "from_cache": bool(choice[2])}
+
+
+def mb_autotune_batch(net, blocks, out_type=MB_OUT_F32, cache_path=None, stream=None):
+    arr = block_array(blocks)
+    choice = (ctypes.c_int32 * 3)()
+    check(load().mb_autotune_batch(net, arr, len(blocks), out_type, cache_path.encode() if cache_path else None,
+                                   choice, stream_handle(stream)), "mb_autotune_batch")
     return {"rows_per_item": choice[0], "stages": choice[1], "from_cache": bool(choice[2])}
 
 

@@ -81,10 +81,42 @@ def test_autotune_choice_and_cache(bf16, tmp_path):
     before = infer(bf16, v)
     cache = str(tmp_path / "tune.json")
     c1 = m.mb_autotune(bf16.handle, 2, 300, 260, cache)
-    assert not c1["from_cache"] and c1["rows_per_item"] in (64, 128, 256, 512, 1024) and c1["stages"] in (4, 5, 6)
+    assert not c1["from_cache"] and c1["rows_per_item"] in (0, 64, 128, 256, 512, 1024) and c1["stages"] in (4, 5, 6)
     c2 = m.mb_autotune(bf16.handle, 2, 300, 260, cache)
     assert c2["from_cache"] and c2["rows_per_item"] == c1["rows_per_item"] and c2["stages"] == c1["stages"]
     np.testing.assert_array_equal(infer(bf16, v), before)
+
+
+def test_batch_autotune_on_the_batch_itself(bf16, tmp_path):
+    """The batch tuner times every candidate on the caller's blocks: its choice is a candidate, it is
+    cached under the blocks' shapes (other addresses, same shapes: a hit), the outputs it leaves are
+    the batch's maps, and the batch maps the same afterwards."""
+    import torch
+    from paper_1612_02120_gb300 import membrane as m
+    shapes = [(2, 37, 300), (1, 256, 129), (3, 64, 64)]
+    vols, _, outs, blocks = make_blocks(shapes, 4012)
+    m.mb_set_tuning(bf16.handle, 1024, 6)
+    m.mb_infer_batch(bf16.handle, blocks)
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(-1.0)
+    cache = str(tmp_path / "tune.json")
+    c1 = m.mb_autotune_batch(bf16.handle, blocks, m.MB_OUT_F32, cache)
+    assert not c1["from_cache"] and c1["rows_per_item"] in (0, 64, 128, 256, 512, 1024) and c1["stages"] in (4, 5, 6)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, ref):
+        assert torch.equal(a, b)
+    _, _, outs2, blocks2 = make_blocks(shapes, 4012)
+    c2 = m.mb_autotune_batch(bf16.handle, blocks2, m.MB_OUT_F32, cache)
+    assert c2["from_cache"] and (c2["rows_per_item"], c2["stages"]) == (c1["rows_per_item"], c1["stages"])
+    m.mb_infer_batch(bf16.handle, blocks2)
+    torch.cuda.synchronize()
+    for a, b in zip(outs2, ref):
+        assert torch.equal(a, b)
+    lib = m.load()
+    assert lib.mb_autotune_batch(bf16.handle, None, 0, 0, None, None, None) == m.MB_ERR_INVALID_ARG
+    m.mb_set_tuning(bf16.handle, 1024, 6)
 
 
 def test_fp32_batch_uses_per_block_path():
@@ -101,9 +133,9 @@ def test_fp32_batch_uses_per_block_path():
 
 
 def test_every_tuning_candidate_gives_the_same_maps(bf16):
-    """The autotuner's knobs (rows per work item, A-ring depth) change the schedule, never a value:
-    every BF16 candidate, applied with mb_set_tuning, maps a volume and an uneven batch bitwise as
-    the default does."""
+    """The autotuner's knobs (rows per work item or the even-range split, A-ring depth) change the
+    schedule, never a value: every BF16 candidate, applied with mb_set_tuning, maps a volume and an
+    uneven batch bitwise as the default does."""
     import torch
     from paper_1612_02120_gb300 import membrane as m
     v = synth.em_volume(4010, 3, 300, 260)
@@ -114,7 +146,7 @@ def test_every_tuning_candidate_gives_the_same_maps(bf16):
     m.mb_infer_batch(bf16.handle, blocks)
     torch.cuda.synchronize()
     ref_b = [o.clone() for o in outs]
-    for rows in (64, 128, 256, 512, 1024):
+    for rows in (64, 128, 256, 512, 1024, 0):
         for stages in (4, 5, 6):
             m.mb_set_tuning(bf16.handle, rows, stages)
             np.testing.assert_array_equal(infer(bf16, v), ref, err_msg=f"rows {rows} stages {stages}")
