@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 #include <string.h>
 
 #include <algorithm>
@@ -618,9 +619,29 @@ mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, 
     p.dm = dm;
     p.nz = nz;
     p.out_u8 = out_u8;
-    p.rows_per_item = 64;
     p.n_strips = (out_w + 127) / 128;
     const int hf = (out_h + d - 1) / d;
+    {
+        // rows per item: the candidate with the least predicted time, waves x (rows + 3) (an item
+        // stages 3 rows beyond its outputs), ties to the larger
+        static int n_sms = 0;
+        if (n_sms == 0) {
+            int dev = 0;
+            MB_CUDA(cudaGetDevice(&dev));
+            MB_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        int64_t best = INT64_MAX;
+        int best_r = 64;
+        for (int r = 32; r <= 512; r *= 2) {
+            const int64_t n = (int64_t)nz * d * p.n_strips * ((hf + r - 1) / r);
+            const int64_t cost = (n + n_sms - 1) / n_sms * (int64_t)(std::min(r, hf) + 3);
+            if (cost <= best) {
+                best = cost;
+                best_r = r;
+            }
+        }
+        p.rows_per_item = best_r;
+    }
     p.n_chunks = (hf + p.rows_per_item - 1) / p.rows_per_item;
     const int64_t items = (int64_t)nz * d * p.n_strips * p.n_chunks;
     if (items > 0x7fffffffLL) {

@@ -599,10 +599,10 @@ mb_status st_tc_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int
     p.cols = (int)cols;
     p.out_u8 = ot == MB_OUT_U8 ? 1 : 0;
     p.n_strips = (int)((cols + kSW - 1) / kSW);
-    // rows per item: at least two items per CTA slot when the region is large, 64 at most (each item
+    // rows per item: at least two items per CTA slot when the region is large, 256 at most (each item
     // computes two extra layer-1 rows)
     const int64_t slots = (int64_t)S->n_sms * 2;
-    int rpi = 64;
+    int rpi = 256;
     while (rpi > 8 && z * p.n_strips * ((rows + rpi - 1) / rpi) < 2 * slots) rpi /= 2;
     p.rows_per_item = rpi;
     p.n_chunks = (int)((rows + rpi - 1) / rpi);
