@@ -104,7 +104,8 @@ struct MeTcParams {
     int cs;                 // source channels (a multiple of 8, <= 16 KC)
     int in_rows, in_cols;   // conv input domain: input (r, c) = 2x2 max (dilation dm) at source (r, c)
     int out_h, out_w, dm;
-    int n_strips, n_chunks, rows_per_item, n_items;
+    int n_strips;
+    int total_rows;         // strip-rows of the launch: n_strips x out_h (< 2^31, checked)
     int fault_stall;        // test injection: producers withhold their arrivals
     uint64_t wait_ns;
 };
@@ -138,17 +139,39 @@ struct MeItem {
     int ry, x0, m0, rows;  // output rows y = ry + D (m0 + j), j < rows; rows may be 0
 };
 
+// Work split: the launch's strip-rows, in (residue class ry, strip, row) order, are cut into one
+// equal contiguous range per CTA (every CTA gets the same number of rows, no tail wave); a CTA's
+// items are the parts of its range in one (ry, strip) column. Residue class ry has
+// hr = ceil((out_h - ry) / D) rows per strip, i.e. base + 1 for ry < rem and base after
+// (out_h = D base + rem), so n_strips (ry base + min(ry, rem)) strip-rows precede it. Every role of
+// a CTA walks the same sequence.
+struct MeCursor {
+    int g, hi;  // next strip-row, end of this CTA's range
+};
+
+__device__ __forceinline__ MeCursor me_begin(const MeTcParams& p) {
+    MeCursor c;
+    c.g = (int)((int64_t)p.total_rows * blockIdx.x / gridDim.x);
+    c.hi = (int)((int64_t)p.total_rows * (blockIdx.x + 1) / gridDim.x);
+    return c;
+}
+
 template <int D>
-__device__ __forceinline__ MeItem me_item(const MeTcParams& p, int k) {
-    MeItem it;
-    const int chunk = k % p.n_chunks;
-    k /= p.n_chunks;
-    it.x0 = (k % p.n_strips) * 128;
-    it.ry = k / p.n_strips;
-    it.m0 = chunk * p.rows_per_item;
-    const int hr = (p.out_h - it.ry + D - 1) / D;  // rows of this residue class
-    it.rows = max(0, min(p.rows_per_item, hr - it.m0));
-    return it;
+__device__ __forceinline__ bool me_next(const MeTcParams& p, MeCursor& c, MeItem& it) {
+    if (c.g >= c.hi) return false;
+    const int base = p.out_h / D, rem = p.out_h % D;
+    auto before = [&](int ry) { return p.n_strips * (ry * base + min(ry, rem)); };
+    int ry = 0;
+    while (ry + 1 < D && before(ry + 1) <= c.g) ++ry;
+    const int hr = base + (ry < rem ? 1 : 0);  // > 0: before(ry) <= g < before(ry + 1)
+    const int off = c.g - before(ry);
+    const int strip = off / hr;
+    it.ry = ry;
+    it.x0 = strip * 128;
+    it.m0 = off - strip * hr;
+    it.rows = min(hr - it.m0, c.hi - c.g);
+    c.g += it.rows;
+    return true;
 }
 
 __device__ __forceinline__ uint4 hmax4(uint4 a, uint4 b) {
@@ -237,9 +260,9 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
             auto wait_unit = [&](uint32_t q) {
                 ok = ok && wait_bar(&b_full[q % kMBRing], (q / kMBRing) & 1, abort_flag, p.err, p.wait_ns);
             };
-            for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-                const MeItem it = me_item<D>(p, k);
-                if (it.rows == 0) continue;
+            MeCursor cur = me_begin(p);
+            MeItem it;
+            while (me_next<D>(p, cur, it)) {
                 const int groups = (it.rows + kR - 1) / kR;
                 int a_known = 0;  // staged rows [0, a_known) of the item are known full
                 int a_rel = 0;    // staged rows [0, a_rel) are released
@@ -334,8 +357,9 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
         const int px = tid - 128;  // TMEM lane = pixel of the strip
         const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
         uint32_t n_groups = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const MeItem it = me_item<D>(p, k);
+        MeCursor cur = me_begin(p);
+        MeItem it;
+        while (me_next<D>(p, cur, it)) {
             const int x = it.x0 + px;
             for (int j = 0; j < it.rows; ++j) {
                 if (j % C::kR == 0) {  // a new group: all its accumulators are complete together
@@ -419,9 +443,9 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
         if (lane == 0) {
             uint32_t issued = 0;
             bool go = true;
-            for (int k = blockIdx.x; go && k < p.n_items; k += gridDim.x) {
-                const MeItem it = me_item<D>(p, k);
-                if (it.rows == 0) continue;
+            MeCursor cur = me_begin(p);
+            MeItem it;
+            while (go && me_next<D>(p, cur, it)) {
                 const int groups = (it.rows + C::kR - 1) / C::kR;
                 for (int g = 0; go && g < groups; ++g)
                     for (int t0 = 0; go && t0 < 16; t0 += C::kBU) {
@@ -458,9 +482,9 @@ __global__ void __launch_bounds__(kMThreads, 1) me_tc_conv(const __grid_constant
         const int64_t dxo = (int64_t)p.dm * p.cs, dyo = (int64_t)p.dm * p.in_pitch * p.cs;
         const int src_chunks = p.cs / 8;
         uint32_t a_seq = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const MeItem it = me_item<D>(p, k);
-            if (it.rows == 0) continue;
+        MeCursor cur = me_begin(p);
+        MeItem it;
+        while (me_next<D>(p, cur, it)) {
             for (int u = grp; u < it.rows + 3; u += C::kGroups) {
                 const uint32_t q = a_seq + u, slot = q % C::kARing;
                 const int yin = it.ry + D * (it.m0 + u);
@@ -545,7 +569,8 @@ mb_status launch_me_tc(const MeTcParams& p, cudaStream_t st) {
                                      C::kSmem));
         attr = true;
     }
-    const int grid = std::max(1, std::min(p.n_items, n_sms));
+    // one range per SM, or fewer when a range would get under 8 rows
+    const int grid = std::max(1, std::min(n_sms, (p.total_rows + 7) / 8));
     me_tc_conv<KC, N, D, HEAD><<<grid, kMThreads, C::kSmem, st>>>(p);
     count_launch();
     MB_CUDA(cudaGetLastError());
@@ -626,19 +651,6 @@ mb_status me_tc_poll_error(mb_net* net) {
 
 // Rows per work item: the cost of a launch is taken as waves x (rows + 5) staged-row steps (3 rows
 // of context and ~2 of pipeline fill per item); the smallest cost wins, ties to more rows.
-static int me_rows_per_item(int d, int strips, int out_h, int n_sms) {
-    const int hr = (out_h + d - 1) / d;
-    int best = 4, best_cost = 0x7fffffff;
-    for (int r = 4; r < hr + 4; r += 4) {
-        const int64_t items = (int64_t)d * strips * ((hr + r - 1) / r);
-        const int64_t cost = ((items + n_sms - 1) / n_sms) * (r + 5);
-        if (cost <= best_cost) {
-            best_cost = (int)std::min<int64_t>(cost, 0x7fffffff);
-            best = r;
-        }
-    }
-    return best;
-}
 
 mb_status me_tc_layer(mb_net* net, int layer, const void* in, int64_t in_pitch, int cs, int in_rows, int in_cols,
                       int dm, void* out, int64_t out_pitch, int out_h, int out_w, float* probs, int64_t probs_plane,
@@ -670,15 +682,11 @@ mb_status me_tc_layer(mb_net* net, int layer, const void* in, int64_t in_pitch, 
     p.out_w = out_w;
     p.dm = dm;
     p.n_strips = (out_w + 127) / 128;
-    p.rows_per_item = me_rows_per_item(d, p.n_strips, out_h, S->n_sms);
-    const int hr = (out_h + d - 1) / d;
-    p.n_chunks = (hr + p.rows_per_item - 1) / p.rows_per_item;
-    const int64_t items = (int64_t)d * p.n_strips * p.n_chunks;
-    if (items > 0x7fffffffLL) {
-        set_error("MaskExtend: too many work items for one launch");
+    if ((int64_t)p.n_strips * out_h > 0x7fffffffLL) {
+        set_error("MaskExtend: too many strip-rows for one launch");
         return MB_ERR_SHAPE;
     }
-    p.n_items = (int)items;
+    p.total_rows = p.n_strips * out_h;
     const char* stall = getenv("MB_FAULT_STALL");
     p.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
     p.wait_ns = p.fault_stall ? 200000000ull : kMWaitNs;
