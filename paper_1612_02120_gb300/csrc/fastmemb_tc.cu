@@ -89,7 +89,8 @@ struct FmTcParams {
     int64_t src_cols;          // source pixels per row that may be read (prefetch bound)
     int out_h, out_w;
     int d, dm;                 // conv dilation, max-filter dilation
-    int nz, n_strips, n_chunks, rows_per_item, n_items;
+    int nz, n_strips;
+    int64_t total_rows;        // strip-rows of the launch: nz x n_strips x out_h
     int out_u8;                // head: uint8 output round(255 p)
     int fault_stall;           // test injection: producers withhold their arrivals
     uint64_t wait_ns;
@@ -124,19 +125,40 @@ struct FmItem {
     int z, ry, x0, m0, rows;  // output rows y = ry + d (m0 + j), j < rows; rows may be 0
 };
 
-__device__ __forceinline__ FmItem fm_item(const FmTcParams& p, int k) {
-    FmItem it;
-    const int chunk = k % p.n_chunks;
-    k /= p.n_chunks;
-    const int strip = k % p.n_strips;
-    k /= p.n_strips;
-    it.ry = k % p.d;
-    it.z = k / p.d;
+// Work split: the launch's strip-rows, in (slice z, residue class ry, strip, row) order, are cut
+// into one equal contiguous range per CTA (no tail wave); a CTA's items are the parts of its range
+// in one (z, ry, strip) column. Residue class ry has hr = ceil((out_h - ry) / d) rows per strip:
+// base + 1 for ry < rem and base after (out_h = d base + rem), so n_strips (ry base + min(ry, rem))
+// strip-rows of a slice precede it. Every role of a CTA walks the same sequence.
+struct FmCursor {
+    int64_t g, hi;  // next strip-row, end of this CTA's range
+};
+
+__device__ __forceinline__ FmCursor fm_begin(const FmTcParams& p) {
+    FmCursor c;
+    c.g = p.total_rows * (int64_t)blockIdx.x / gridDim.x;
+    c.hi = p.total_rows * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    return c;
+}
+
+__device__ __forceinline__ bool fm_next(const FmTcParams& p, FmCursor& c, FmItem& it) {
+    if (c.g >= c.hi) return false;
+    const int64_t per_slice = (int64_t)p.n_strips * p.out_h;
+    it.z = (int)(c.g / per_slice);
+    const int r = (int)(c.g - (int64_t)it.z * per_slice);  // strip-row within the slice
+    const int base = p.out_h / p.d, rem = p.out_h % p.d;
+    auto before = [&](int ry) { return p.n_strips * (ry * base + min(ry, rem)); };
+    int ry = 0;
+    while (ry + 1 < p.d && before(ry + 1) <= r) ++ry;
+    const int hr = base + (ry < rem ? 1 : 0);  // > 0: before(ry) <= r < before(ry + 1)
+    const int off = r - before(ry);
+    const int strip = off / hr;
+    it.ry = ry;
     it.x0 = strip * 128;
-    it.m0 = chunk * p.rows_per_item;
-    const int hr = (p.out_h - it.ry + p.d - 1) / p.d;  // rows of this residue class
-    it.rows = max(0, min(p.rows_per_item, hr - it.m0));
-    return it;
+    it.m0 = off - strip * hr;
+    it.rows = (int)min((int64_t)(hr - it.m0), c.hi - c.g);
+    c.g += it.rows;
+    return true;
 }
 
 __device__ __forceinline__ uint4 bmax(uint4 a, uint4 b) {
@@ -256,9 +278,9 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                                          ptx::idesc_f32acc(ptx::kFmtBF16, 128, 32),
                                          ptx::idesc_f32acc(ptx::kFmtBF16, 128, 48),
                                          ptx::idesc_f32acc(ptx::kFmtBF16, 128, 64)};
-                for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-                    const FmItem it = fm_item(p, k);
-                    if (it.rows == 0) continue;
+                FmCursor cur = fm_begin(p);
+                FmItem it;
+                while (fm_next(p, cur, it)) {
                     const int nst = it.rows + 3;
                     for (int u = 0; u < nst; ++u) {
                         const int blo = max(0, u - it.rows + 1), bhi = min(3, u);
@@ -294,10 +316,10 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                     row_seq += nst;
                     acc_seq += it.rows;
                 }
-            } else
-            for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-                const FmItem it = fm_item(p, k);
-                if (it.rows == 0) continue;
+            } else {
+            FmCursor cur = fm_begin(p);
+            FmItem it;
+            while (fm_next(p, cur, it)) {
                 for (int u = 0; u < 4; ++u) wait_row(row_seq + u);
                 wait_acc(acc_seq);
                 ptx::tc_fence_after();
@@ -318,6 +340,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                 row_seq += it.rows + 3;
                 acc_seq += it.rows;
             }
+            }
             ptx::mma_commit(fin);
             const uint64_t t0 = gtime();
             while (!ptx::mbar_test(fin, 0)) {
@@ -333,8 +356,9 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
         const int px = tid - 128;  // TMEM lane = pixel of the strip
         const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
         uint32_t acc_seq = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const FmItem it = fm_item(p, k);
+        FmCursor cur = fm_begin(p);
+        FmItem it;
+        while (fm_next(p, cur, it)) {
             const int x = it.x0 + px;
             for (int j = 0; j < it.rows; ++j) {
                 const uint32_t qa = acc_seq + j;
@@ -403,9 +427,9 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
         const int ntask = 4 * (128 + 3 * d);
         const int64_t dxo = (int64_t)p.dm * 32, dyo = (int64_t)p.dm * p.in_pitch * 32;
         uint32_t row_seq = 0;
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const FmItem it = fm_item(p, k);
-            if (it.rows == 0) continue;
+        FmCursor cur = fm_begin(p);
+        FmItem it;
+        while (fm_next(p, cur, it)) {
             const __nv_bfloat16* src = p.in + (int64_t)it.z * p.in_slice;
             // source pixels one staged row reads: stride (npix - 1) + dm + 1 from stride x0, clipped
             const int sx0 = p.stride * it.x0;
@@ -516,7 +540,8 @@ mb_status launch_fm_tc(const FmTcParams& p, cudaStream_t st) {
         MB_CUDA(cudaFuncSetAttribute(fm_tc_conv<HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
         attr = true;
     }
-    const int grid = std::max(1, std::min(p.n_items, n_sms));
+    // one range per SM, or fewer when a range would get under 8 rows
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_sms, (p.total_rows + 7) / 8));
     fm_tc_conv<HEAD><<<grid, kFThreads, C::kSmem, st>>>(p);
     count_launch();
     MB_CUDA(cudaGetLastError());
@@ -620,35 +645,7 @@ mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, 
     p.nz = nz;
     p.out_u8 = out_u8;
     p.n_strips = (out_w + 127) / 128;
-    const int hf = (out_h + d - 1) / d;
-    {
-        // rows per item: the candidate with the least predicted time, waves x (rows + 3) (an item
-        // stages 3 rows beyond its outputs), ties to the larger
-        static int n_sms = 0;
-        if (n_sms == 0) {
-            int dev = 0;
-            MB_CUDA(cudaGetDevice(&dev));
-            MB_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
-        }
-        int64_t best = INT64_MAX;
-        int best_r = 64;
-        for (int r = 32; r <= 512; r *= 2) {
-            const int64_t n = (int64_t)nz * d * p.n_strips * ((hf + r - 1) / r);
-            const int64_t cost = (n + n_sms - 1) / n_sms * (int64_t)(std::min(r, hf) + 3);
-            if (cost <= best) {
-                best = cost;
-                best_r = r;
-            }
-        }
-        p.rows_per_item = best_r;
-    }
-    p.n_chunks = (hf + p.rows_per_item - 1) / p.rows_per_item;
-    const int64_t items = (int64_t)nz * d * p.n_strips * p.n_chunks;
-    if (items > 0x7fffffffLL) {
-        set_error("FastMemb: too many work items for one launch");
-        return MB_ERR_SHAPE;
-    }
-    p.n_items = (int)items;
+    p.total_rows = (int64_t)nz * p.n_strips * out_h;
     const char* stall = getenv("MB_FAULT_STALL");
     p.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
     p.wait_ns = p.fault_stall ? 200000000ull : kFWaitNs;
