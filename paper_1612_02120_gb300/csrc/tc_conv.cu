@@ -9,7 +9,9 @@
 //   layer 3   conv5x5 32->32                  tcgen05.mma
 //   + bias + ReLU + head 1x1 + sigmoid        fused into the layer-3 epilogue, stored to HBM
 //
-// Work item: one slice, a strip of 118 output columns, a chunk of output rows. Each CTA walks
+// Work item: one slice, a strip of 118 output columns, a run of output rows: either chunks of a
+// tuned length taken round-robin, or the parts of one equal contiguous range of strip-rows per CTA
+// (a compile-time choice, tuned per workload for BF16; always the ranges for FP8). Each CTA walks
 // its items row by row. The layer-2/3 implicit GEMM per input row r:
 //   M = 128 pixels of the row, K = 32 channels (x 5 column taps dx), N = 5 row taps x 32 outputs.
 // The five row taps dy are stacked along N, so one input row is multiplied once and its five
