@@ -11,12 +11,12 @@
 //            into a ring of staged feature rows.
 //   layer 2  each staged row r is multiplied once per column tap kx with the three row taps stacked
 //            along N (N = 48: blocks for output rows r-2, r-1, r with row taps 2, 1, 0), accumulating
-//            into a ring of 8 row accumulators (windows that wrap the ring are split in two MMAs).
+//            into a ring of 12 row accumulators (windows that wrap the ring are split in two MMAs).
 //            The epilogue adds the bias, applies ReLU, the head and the sigmoid in FP32 and stores.
 // A strip covers 126 output columns (128 layer-1 pixels, the last two only feed the column taps).
 //
 // Warp roles (384 threads, two CTAs per SM, persistent over work items):
-//   warp 0      TMEM owner (256 columns: layer-2 ring 0..127, layer-1 ring 128..191); lane 0
+//   warp 0      TMEM owner (256 columns: layer-2 ring 0..191, layer-1 ring 192..255); lane 0
 //               issues the layer-1 MMAs
 //   warp 3      lane 0 issues the layer-2 MMAs (a thread stalls ~200 cycles on each commit; with
 //               two issuing threads the tensor core keeps working meanwhile)
@@ -46,9 +46,9 @@ constexpr int kSRowB = 2 * kSPitch * 16;  // bytes per operand row: 2 chunks (K 
 constexpr int kNA1 = 4;                   // layer-1 operand rows in flight
 constexpr int kNS = 6;                    // staged layer-1 feature rows
 constexpr int kKL = 4;                    // layer-1 accumulators, 16 TMEM columns each
-constexpr int kKA = 8;                    // layer-2 row accumulators, 16 TMEM columns each
+constexpr int kKA = 12;                   // layer-2 row accumulators, 16 TMEM columns each
 constexpr int kSTmem = 256;
-constexpr int kL1Col = 128;               // first TMEM column of the layer-1 ring
+constexpr int kL1Col = 16 * kKA;          // first TMEM column of the layer-1 ring
 constexpr int kB1 = 3 * 2 * 16 * 16;      // per column tap: [2 chunks][16 co][16 B]
 constexpr int kB2Group = 2 * 48 * 16;     // per column tap: [2 chunks][48 rows][16 B]
 constexpr int kB2 = 3 * kB2Group;
@@ -72,7 +72,7 @@ constexpr uint64_t kSWaitNs = 4000000000ull;
 constexpr int kFW1 = 0, kFB1 = 144, kFW2 = 160, kFB2 = 2464, kFWH = 2480, kFBH = 2496;
 static_assert(kSUsed <= kSSmem && 3 * kSSmem > 227 * 1024, "shared memory");
 static_assert(oSA1 % 16 == 0 && oSS % 16 == 0 && oSBar % 8 == 0, "alignment");
-static_assert(2 * kSTmem <= 512, "TMEM of two CTAs");
+static_assert(2 * kSTmem <= 512 && kL1Col + 16 * kKL <= kSTmem, "TMEM of two CTAs");
 
 struct StTcParams {
     const uint8_t* in;        // slice z at in + z in_slice; row pitch in_pitch
@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
         // per-row instruction chain is what bounds the issue rate of MMAs this small, so ring
         // positions are running slot/phase counters (no division per row), and a full layer-2 window
         // is issued from one of three branches with compile-time instruction descriptors: it starts
-        // below slot 6 (one N = 48 MMA per column tap) or in slot 6 or 7 (split where it wraps).
+        // at most two slots before the ring's end (one N = 48 MMA per column tap) or in one of the last
+        // two slots (split where it wraps).
         if (lane == 0) {
             constexpr uint32_t id16 = ptx::idesc_f32acc(ptx::kFmtBF16, 128, 16);
             constexpr uint32_t id32 = ptx::idesc_f32acc(ptx::kFmtBF16, 128, 32);
@@ -276,14 +277,14 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                                 for (int kx = 0; kx < 3; ++kx)
                                     ptx::mma_bf16(tbase + 16u * ws, arow + (uint64_t)kx,
                                                   b2d + (uint64_t)((kx * kB2Group) >> 4), id48, 1u);
-                            } else if (ws == kKA - 2) {  // blocks 0-1 in slots 6-7, block 2 in slot 0
+                            } else if (ws == kKA - 2) {  // blocks 0-1 in the last two slots, block 2 in slot 0
 #pragma unroll
                                 for (int kx = 0; kx < 3; ++kx) {
                                     const uint64_t bg = b2d + (uint64_t)((kx * kB2Group) >> 4);
                                     ptx::mma_bf16(tbase + 16u * (kKA - 2), arow + (uint64_t)kx, bg, id32, 1u);
                                     ptx::mma_bf16(tbase, arow + (uint64_t)kx, bg + 32u, id16, 1u);
                                 }
-                            } else {  // block 0 in slot 7, blocks 1-2 in slots 0-1
+                            } else {  // block 0 in the last slot, blocks 1-2 in slots 0-1
 #pragma unroll
                                 for (int kx = 0; kx < 3; ++kx) {
                                     const uint64_t bg = b2d + (uint64_t)((kx * kB2Group) >> 4);
