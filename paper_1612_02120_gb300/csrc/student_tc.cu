@@ -82,7 +82,8 @@ struct StTcParams {
     int64_t in_slice, in_pitch, out_slice, out_pitch;
     int h, w;                 // slice
     int y0, x0, rows, cols;   // region
-    int n_strips, n_chunks, rows_per_item, n_items;
+    int n_strips;
+    int64_t total_rows;       // strip-rows of the launch: z x n_strips x rows
     int out_u8;
     int fault_stall;
     uint64_t wait_ns;
@@ -121,17 +122,32 @@ struct StItem {
     int z, m0, rows, s0, ncol;  // region rows m0 .. m0 + rows - 1, region columns s0 .. s0 + ncol - 1
 };
 
-__device__ __forceinline__ StItem st_item(const StTcParams& p, int k) {
-    StItem it;
-    const int chunk = k % p.n_chunks;
-    k /= p.n_chunks;
-    const int strip = k % p.n_strips;
-    it.z = k / p.n_strips;
-    it.m0 = chunk * p.rows_per_item;
-    it.rows = max(0, min(p.rows_per_item, p.rows - it.m0));
+// Work split: the launch's strip-rows, in (slice, strip, row) order, are cut into one equal
+// contiguous range per CTA (every CTA gets the same number of rows, no tail wave); a CTA's items
+// are the parts of its range in one (slice, strip) column. Every role of a CTA walks the same
+// sequence.
+struct StCursor {
+    int64_t g, hi;  // next strip-row, end of this CTA's range
+};
+
+__device__ __forceinline__ StCursor st_begin(const StTcParams& p) {
+    StCursor c;
+    c.g = p.total_rows * (int64_t)blockIdx.x / gridDim.x;
+    c.hi = p.total_rows * (int64_t)(blockIdx.x + 1) / gridDim.x;
+    return c;
+}
+
+__device__ __forceinline__ bool st_next(const StTcParams& p, StCursor& c, StItem& it) {
+    if (c.g >= c.hi) return false;
+    const int64_t col = c.g / p.rows;  // (slice, strip) column
+    it.z = (int)(col / p.n_strips);
+    const int strip = (int)(col - (int64_t)it.z * p.n_strips);
+    it.m0 = (int)(c.g - col * p.rows);
+    it.rows = (int)min((int64_t)(p.rows - it.m0), c.hi - c.g);
     it.s0 = strip * kSW;
     it.ncol = min(kSW, p.cols - it.s0);
-    return it;
+    c.g += it.rows;
+    return true;
 }
 
 // BF16 bits of a byte value (exact: every integer up to 256 has at most 8 significant bits).
@@ -230,9 +246,9 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                 const uint64_t a1d = ptx::smem_desc(sbase + oSA1, kSPitch * 16, 128);
                 const uint64_t b1d = ptx::smem_desc(sbase + oSB1, 16 * 16, 128);
                 uint32_t s1 = 0, ph1 = 0;  // operand slot = layer-1 accumulator slot, and its phase
-                for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-                    const StItem it = st_item(p, k);
-                    if (it.rows == 0) continue;
+                StCursor cur = st_begin(p);
+                StItem it;
+                while (st_next(p, cur, it)) {
                     const int n_rows = it.rows + 2;
                     for (int u = 0; u < n_rows; ++u) {
                         ok = ok && wait_bar(&a1_full[s1], ph1, abort_flag, p.err, p.wait_ns);
@@ -261,9 +277,9 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                 uint32_t ss = 0, sph = 0;  // staged slot and phase
                 uint32_t as = 0, aph = 0;  // slot and phase of the next output row to start
                 uint32_t ws = kKA - 2;     // slot of output row u - 2 (may be a row of no item)
-                for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-                    const StItem it = st_item(p, k);
-                    if (it.rows == 0) continue;
+                StCursor cur = st_begin(p);
+                StItem it;
+                while (st_next(p, cur, it)) {
                     const int R = it.rows, n_rows = R + 2;
                     for (int u = 0; u < n_rows; ++u) {
                         ok = ok && wait_bar(&s_full[ss], sph, abort_flag, p.err, p.wait_ns);
@@ -346,9 +362,9 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
         // row enters the window: converting it at the load would stall the thread on the load.
         const int bt = tid - 32;
         uint32_t slot = 0, sph = 0;  // operand slot and its phase
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const StItem it = st_item(p, k);
-            if (it.rows == 0) continue;
+        StCursor cur = st_begin(p);
+        StItem it;
+        while (st_next(p, cur, it)) {
             const int R = it.rows, n_rows = R + 2, last = R + 3;  // input rows 0 .. R + 3 of the item
             const uint8_t* src = p.in + (int64_t)it.z * p.in_slice;
             const int c0 = p.x0 + it.s0 - 2;
@@ -422,9 +438,9 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
         const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
         const float inv = cst[kCInv];
         uint32_t sl = 0, lph = 0, ss = 0, sph = 0;  // accumulator and staged slots, their phases
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const StItem it = st_item(p, k);
-            if (it.rows == 0) continue;
+        StCursor cur = st_begin(p);
+        StItem it;
+        while (st_next(p, cur, it)) {
             const int n_rows = it.rows + 2;
             for (int u = 0; u < n_rows; ++u) {
                 wait_bar(&l1_full[sl], lph, abort_flag, p.err, p.wait_ns);
@@ -459,8 +475,9 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
         const int px = tid - 256;  // TMEM lane = output pixel of the strip
         const uint32_t lanes = (uint32_t)(32 * (warp - 8)) << 16;
         uint32_t sl = 0, aph = 0;  // accumulator slot and its phase
-        for (int k = blockIdx.x; k < p.n_items; k += gridDim.x) {
-            const StItem it = st_item(p, k);
+        StCursor cur = st_begin(p);
+        StItem it;
+        while (st_next(p, cur, it)) {
             const bool col = px < it.ncol;
             int64_t idx = (int64_t)it.z * p.out_slice + (int64_t)it.m0 * p.out_pitch + it.s0 + px;
             for (int j = 0; j < it.rows; ++j, idx += p.out_pitch) {
@@ -600,23 +617,13 @@ mb_status st_tc_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int
     p.cols = (int)cols;
     p.out_u8 = ot == MB_OUT_U8 ? 1 : 0;
     p.n_strips = (int)((cols + kSW - 1) / kSW);
-    // rows per item: at least two items per CTA slot when the region is large, 256 at most (each item
-    // computes two extra layer-1 rows)
     const int64_t slots = (int64_t)S->n_sms * 2;
-    int rpi = 256;
-    while (rpi > 8 && z * p.n_strips * ((rows + rpi - 1) / rpi) < 2 * slots) rpi /= 2;
-    p.rows_per_item = rpi;
-    p.n_chunks = (int)((rows + rpi - 1) / rpi);
-    const int64_t items = z * p.n_strips * p.n_chunks;
-    if (items > 0x7fffffffLL) {
-        set_error("student: too many work items for one launch");
-        return MB_ERR_SHAPE;
-    }
-    p.n_items = (int)items;
+    p.total_rows = z * p.n_strips * rows;
     const char* stall = getenv("MB_FAULT_STALL");
     p.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
     p.wait_ns = p.fault_stall ? 200000000ull : kSWaitNs;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, slots));
+    // one range per CTA slot, or fewer when a range would get under 8 rows
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(slots, (p.total_rows + 7) / 8));
     st_tc_infer<<<grid, kSThreads, kSSmem, st>>>(p);
     count_launch();
     MB_CUDA(cudaGetLastError());
