@@ -475,6 +475,15 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
         const int px = tid - 256;  // TMEM lane = output pixel of the strip
         const uint32_t lanes = (uint32_t)(32 * (warp - 8)) << 16;
         uint32_t sl = 0, aph = 0;  // accumulator slot and its phase
+        // the head's constants in registers (shared-memory reads would repeat every row: the waits
+        // are compiler barriers)
+        float b2r[16], whr[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            b2r[c] = cst[kCB2 + c];
+            whr[c] = cst[kCWH + c];
+        }
+        const float bhr = cst[kCBH];
         StCursor cur = st_begin(p);
         StItem it;
         while (st_next(p, cur, it)) {
@@ -494,9 +503,9 @@ __global__ void __launch_bounds__(kSThreads, 2) st_tc_infer(const __grid_constan
                     sl = 0;
                     aph ^= 1;
                 }
-                float z = cst[kCBH];
+                float z = bhr;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) z = fmaf(cst[kCWH + c], fmaxf(d[c] + cst[kCB2 + c], 0.f), z);
+                for (int c = 0; c < 16; ++c) z = fmaf(whr[c], fmaxf(d[c] + b2r[c], 0.f), z);
                 // the correctly rounded reciprocal is the correctly rounded quotient 1 / x
                 const float prob = __frcp_rn(1.0f + expf(-z));
                 if (col && live) {
