@@ -134,16 +134,16 @@ def test_fp8_uncalibrated_is_not_ready():
     n.close()
 
 
-def test_host_streaming_over_several_slabs_equals_device_path():
-    """1024x1024x30 from pinned host buffers streams as slabs of 4, 8, 8, 6 and 4 slices (half-size
-    first and last slabs, a ragged one before the last; slabs alternate between two buffers and,
-    for this tensor-core net, two compute streams); the maps equal the device-resident call
-    bitwise."""
+@pytest.mark.parametrize("z", [30, 23, 15])
+def test_host_streaming_over_several_slabs_equals_device_path(z):
+    """1024x1024xz from pinned host buffers streams in slabs of at most 8 slices: for 30 slices
+    4, 8, 8, 6, 4 (half-size first and last slabs, a ragged one before the last), for 23 4, 8, 7, 4,
+    for 15 8, 7 (too short to halve the ends); slabs alternate between two buffers and, for this
+    tensor-core net, two compute streams. The maps equal the device-resident call bitwise."""
     import torch
     from paper_1612_02120_gb300 import build, membrane as m
     build.build()
     net = make_net(T, m.MB_PREC_BF16, teacher_params())
-    z = 30
     v = synth.em_volume(5100, z, 1024, 1024)
     dev = infer(net, v)
     pin_in = torch.from_numpy(v).pin_memory()
