@@ -298,10 +298,10 @@ __device__ __forceinline__ void store_eighth(uint8_t* slot, int c, int h, const 
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int ch = 4 * j;
-            __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(m[ch] * q[ch], m[ch + 1] * q[ch + 1]),
-                                                               __NV_SATFINITE, __NV_E4M3);
-            __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
-                make_float2(m[ch + 2] * q[ch + 2], m[ch + 3] * q[ch + 3]), __NV_SATFINITE, __NV_E4M3);
+            // (layer 1 arrives already scaled: the scale is folded into its weights and bias)
+            __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(m[ch], m[ch + 1]), __NV_SATFINITE, __NV_E4M3);
+            __nv_fp8x2_storage_t hi =
+                __nv_cvt_float2_to_fp8x2(make_float2(m[ch + 2], m[ch + 3]), __NV_SATFINITE, __NV_E4M3);
             w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
         }
         *reinterpret_cast<uint2*>(slot + ((h >> 1) * kPitch + c) * 16 + (h & 1) * 8) = make_uint2(w[0], w[1]);
@@ -900,6 +900,12 @@ mb_status tc_prepare(mb_net* net) {
                 const float a = net->fp8_amax[l][ci];
                 sa[ci] = a > 0.f ? a / 448.f : 1.f;
                 cs[(l == 0 ? kCQ1 : kCQ2) + ci] = 1.f / sa[ci];
+                if (l == 0) {
+                    // layer 1's quantisation scale (> 0) commutes with ReLU and the max-filter: it
+                    // is folded into layer 1's weights and bias, so the producers store as they go
+                    for (int k = 0; k < 25; ++k) cs[kCW1 + k * 32 + ci] /= sa[ci];
+                    cs[kCB1 + ci] /= sa[ci];
+                }
             }
             std::vector<float> Wp(25600);
             float inv[32];
