@@ -64,6 +64,7 @@ struct TcBlockDesc {
 
 // Per-channel constants, staged into shared memory at kernel start (floats):
 //   w1[25 taps][32 ch] | b1 | ep2 scale | ep2 bias | ep3 scale | ep3 bias | q1 | q2 | head w
+// (FP8 folds q1 into w1 and b1 on the host; the slot is kept so that the layout is one for both)
 constexpr int kCW1 = 0, kCB1 = 800, kCE2S = 832, kCE2B = 864, kCE3S = 896, kCE3B = 928, kCQ1 = 960,
               kCQ2 = 992, kCHW = 1024, kConsts = 1056;
 
