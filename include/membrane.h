@@ -52,6 +52,8 @@ typedef enum {
 
 typedef enum { MB_PREC_FP32 = 0, MB_PREC_BF16 = 1, MB_PREC_FP8 = 2, MB_PREC_FP16 = 3 } mb_precision;
 typedef enum { MB_OUT_F32 = 0, MB_OUT_U8 = 1 } mb_out_type;
+/* How mb_infer_volume moves a volume whose buffers are both in host memory (mb_set_host_io). */
+typedef enum { MB_HOST_IO_AUTO = 0, MB_HOST_IO_SLABS = 1 } mb_host_io;
 typedef enum {
     MB_CONV = 0,
     MB_MAXFILTER = 1,
@@ -151,9 +153,16 @@ mb_status mb_calibrate_fp8(mb_net* net, const uint8_t* slices, int64_t n, int64_
 /*
  * Probability maps of a contiguous volume in[z][h][w] (uint8) into out[z][h][w] (float32 or
  * uint8 q = min(255, floor(255 p + 0.5))). Device pointers: asynchronous on `stream`.
- * Pinned or pageable HOST pointers (both in and out on the host): the volume is streamed
- * through the device in z-slabs with copies overlapped with compute; synchronous.
- * Mixed host/device pointers: MB_ERR_INVALID_ARG.
+ * HOST pointers (both in and out on the host; synchronous, `stream` unused):
+ *   - both page-locked and mapped (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory), on
+ *     a GPU that reads host memory through the host's page tables (a coherent CPU-GPU link such
+ *     as NVLink-C2C; cudaDevAttrPageableMemoryAccessUsesHostPageTables), and the net's host I/O
+ *     mode MB_HOST_IO_AUTO (the default): the kernels read the input from and write the maps to
+ *     the host buffers themselves, in the same launches as for device buffers; no device buffer
+ *     and no copy;
+ *   - otherwise (pageable memory, another link, or MB_HOST_IO_SLABS): the volume is streamed
+ *     through device buffers in z-slabs, copies overlapped with compute.
+ * Both give the device path's maps bitwise. Mixed host/device pointers: MB_ERR_INVALID_ARG.
  */
 mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,
                           mb_out_type out_type, void* stream);
@@ -233,6 +242,13 @@ mb_status mb_autotune_batch(mb_net* net, const mb_block* blocks, int32_t n_block
  * net's captured batch graphs (they hold the previous choice).
  */
 mb_status mb_set_tuning(mb_net* net, int32_t rows_per_item, int32_t stages);
+
+/*
+ * Host I/O mode of mb_infer_volume for host buffers: MB_HOST_IO_AUTO (default: direct access
+ * where the buffers and the link allow it, else slabs) or MB_HOST_IO_SLABS (always slabs through
+ * device buffers). Other values: MB_ERR_INVALID_ARG. Results do not depend on the mode.
+ */
+mb_status mb_set_host_io(mb_net* net, int32_t mode);
 
 /*
  * Student loss and gradient on n slices (device, in[n][h][w] uint8; target[n][h][w] float32):

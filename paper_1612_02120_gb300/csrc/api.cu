@@ -152,6 +152,32 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked, mapped host memory at p (cudaHostAlloc / cudaHostRegister), or
+// nullptr for any other memory.
+static void* mapped_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    // the attributes describe the queried address; the offset term only matters if they name
+    // the allocation's start instead
+    const char* hp = a.hostPointer ? static_cast<const char*>(a.hostPointer) : static_cast<const char*>(p);
+    return static_cast<char*>(a.devicePointer) + (static_cast<const char*>(p) - hp);
+}
+
+// Whether the device reads host memory through the host's own page tables: a coherent CPU-GPU
+// link (NVLink-C2C), over which kernels stream host buffers at the rate this path needs.
+static bool coherent_host_link(int device) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return v != 0;
+}
+
 static mb_status check_ready(const mb_net* net) {
     if (!net) {
         set_error("net is NULL");
@@ -266,13 +292,28 @@ static mb_status net_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h
     return student_region(net, in, z, h, w, w, h * w, y0, x0, rows, cols, out, cols, rows * cols, ot, st);
 }
 
-// Host-memory volumes: z-slabs through double-buffered device slabs, H2D / compute / D2H on their
+// Host-memory volumes. Mapped page-locked buffers on a coherent link: the kernels access them
+// directly. Otherwise z-slabs through double-buffered device slabs, H2D / compute / D2H on their
 // own streams so copies overlap compute (the tensor-core teacher computes on two alternating
 // streams, so one slab's launch tail overlaps the next launch).
 static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,
                                    mb_out_type ot) {
     const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
     const size_t in_slice = (size_t)h * w, out_slice = (size_t)h * w * osz;
+    cudaStream_t* s = net->slab_streams;
+    if (net->host_io == MB_HOST_IO_AUTO && coherent_host_link(net->device)) {
+        // Direct: the kernels load the input bytes from and store the maps to the host buffers
+        // over the link, in the launches of the device path. A step then moves exactly the input
+        // and output bytes across the link, with no device buffer and no exposed copy at either end.
+        const void* mi = mapped_host_ptr(in);
+        void* mo = mi ? mapped_host_ptr(out) : nullptr;
+        if (mi && mo) {
+            if (!s[1]) MB_CUDA(cudaStreamCreateWithFlags(&s[1], cudaStreamNonBlocking));
+            MB_TRY(net_region(net, static_cast<const uint8_t*>(mi), z, h, w, 0, 0, h, w, mo, ot, s[1]));
+            MB_CUDA(cudaStreamSynchronize(s[1]));
+            return MB_OK;
+        }
+    }
     // Slabs of about 8 Mvox: large enough that one launch fills every SM, small enough that the
     // copies of neighbouring slabs overlap the compute (a 1024x1024x32 volume becomes 4 slabs);
     // at most 256 MB of device buffers per slab.
@@ -284,7 +325,6 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
     // device slabs, streams and events live with the net and are reused by later calls
     const size_t slab_bytes = (in_slice + out_slice) * (size_t)slab;
     MB_TRY(net->slab_ws.ensure(NB * slab_bytes));
-    cudaStream_t* s = net->slab_streams;
     for (int i = 0; i < 4; ++i)
         if (!s[i]) MB_CUDA(cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking));
     // The fused tensor-core teacher keeps no device state between launches, so consecutive slabs
@@ -635,6 +675,20 @@ mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, 
     }
     if (!din) return infer_host_volume(net, in, z, h, w, out, out_type);
     return net_region(net, in, z, h, w, 0, 0, h, w, out, out_type, (cudaStream_t)stream);
+}
+
+mb_status mb_set_host_io(mb_net* net, int32_t mode) {
+    API_BEGIN
+    if (!net) {
+        set_error("mb_set_host_io: net is NULL");
+        return MB_ERR_INVALID_ARG;
+    }
+    if (mode != MB_HOST_IO_AUTO && mode != MB_HOST_IO_SLABS) {
+        set_error("mb_set_host_io: unknown mode %d", (int)mode);
+        return MB_ERR_INVALID_ARG;
+    }
+    net->host_io = mode;
+    return MB_OK;
 }
 
 mb_status mb_infer_volume_subsampled(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int32_t factor,

@@ -83,6 +83,7 @@ struct mb_net {
     mb::Workspace ws2;           // student training / cascade scratch
     mb::Workspace slab_ws;       // host-buffer streaming: double-buffered device slabs
     cudaStream_t slab_streams[4] = {};  // H2D, compute, D2H, second compute stream (overlapping slabs)
+    int host_io = 0;             // mb_host_io: 0 direct host access where possible, 1 always slabs
     cudaEvent_t slab_events[6] = {};                              // per buffer: in, comp, out
     // persistent kernel tuning
     int rows_per_item = 64;

@@ -16,6 +16,7 @@ MB_OK, MB_ERR_INVALID_ARG, MB_ERR_SHAPE, MB_ERR_OOM, MB_ERR_CUDA, MB_ERR_TIMEOUT
     MB_ERR_UNSUPPORTED = range(8)
 MB_PREC_FP32, MB_PREC_BF16, MB_PREC_FP8, MB_PREC_FP16 = 0, 1, 2, 3
 MB_OUT_F32, MB_OUT_U8 = 0, 1
+MB_HOST_IO_AUTO, MB_HOST_IO_SLABS = 0, 1
 MB_CONV, MB_MAXFILTER, MB_HEAD_SIGMOID, MB_HEAD_SOFTMAX2, MB_HEAD_SOFTMAX = 0, 1, 2, 3, 4
 
 EXPORTED = (
@@ -23,7 +24,7 @@ EXPORTED = (
     "mb_calibrate_fp8", "mb_infer_volume", "mb_infer_region", "mb_infer_batch", "mb_infer_batch_per_block",
     "mb_autotune", "mb_student_loss_grad", "mb_student_train", "mb_infer_cascade", "mb_status_string",
     "mb_last_error", "mb_launch_count", "mb_infer_volume_noalloc", "mb_infer_volume_subsampled", "mb_mask_extend",
-    "mb_mask_extend_dir", "mb_set_tuning", "mb_autotune_batch",
+    "mb_mask_extend_dir", "mb_set_tuning", "mb_autotune_batch", "mb_set_host_io",
 )
 
 
@@ -76,6 +77,7 @@ def load() -> ctypes.CDLL:
         "mb_infer_batch_per_block": ([p, p, i32, i32, p], st),
         "mb_autotune": ([p, i64, i64, i64, ctypes.c_char_p, p, p], st),
         "mb_set_tuning": ([p, i32, i32], st),
+        "mb_set_host_io": ([p, i32], st),
         "mb_autotune_batch": ([p, p, i32, i32, ctypes.c_char_p, p, p], st),
         "mb_student_loss_grad": ([p, p, p, i64, i64, i64, p, p, p], st),
         "mb_student_train": ([p, p, p, i64, i64, i64, p, ctypes.c_char_p, p, p], st),
@@ -254,6 +256,10 @@ def mb_autotune_batch(net, blocks, out_type=MB_OUT_F32, cache_path=None, stream=
 
 def mb_set_tuning(net, rows_per_item, stages) -> None:
     check(load().mb_set_tuning(net, rows_per_item, stages), "mb_set_tuning")
+
+
+def mb_set_host_io(net, mode) -> None:
+    check(load().mb_set_host_io(net, mode), "mb_set_host_io")
 
 
 def mb_student_loss_grad(net, inp, target, n, h, w, grad, stream=None) -> float:

@@ -77,8 +77,11 @@ def test_host_pointers_stream_in_slabs_and_match_device_path(net):
     dev = infer(net, v)
     pin_in = torch.from_numpy(v).pin_memory()
     pin_out = torch.empty((5, 64, 72), dtype=torch.float32).pin_memory()
-    m.mb_infer_volume(net.handle, pin_in, 5, 64, 72, pin_out)
-    np.testing.assert_array_equal(pin_out.numpy(), dev)
+    for mode in (m.MB_HOST_IO_SLABS, m.MB_HOST_IO_AUTO):
+        m.mb_set_host_io(net.handle, mode)
+        pin_out.fill_(-1.0)
+        m.mb_infer_volume(net.handle, pin_in, 5, 64, 72, pin_out)
+        np.testing.assert_array_equal(pin_out.numpy(), dev)
     pageable_out = np.empty((5, 64, 72), dtype=np.float32)
     m.mb_infer_volume(net.handle, np.ascontiguousarray(v), 5, 64, 72, pageable_out)
     np.testing.assert_array_equal(pageable_out, dev)

@@ -144,8 +144,8 @@ def test_fp8_batch_equals_per_block_and_volume(fp8):
 
 
 def test_fp8_host_streaming_equals_device_path():
-    """1024x1024x30 from pinned host buffers (slabs of 4, 8, 8, 6, 4 slices on two compute streams)
-    equals the device-resident FP8 call bitwise."""
+    """1024x1024x30 from pinned host buffers, in slabs (4, 8, 8, 6, 4 slices on two compute
+    streams) and accessed directly by the kernel, equals the device-resident FP8 call bitwise."""
     import torch
     from paper_1612_02120_gb300 import membrane as m
     z = 30
@@ -154,7 +154,8 @@ def test_fp8_host_streaming_equals_device_path():
     dev = infer(net, v)
     pin_in = torch.from_numpy(v).pin_memory()
     pin_out = torch.empty((z, 1024, 1024), dtype=torch.float32).pin_memory()
-    for _ in range(2):
+    for mode in (m.MB_HOST_IO_SLABS, m.MB_HOST_IO_SLABS, m.MB_HOST_IO_AUTO):
+        m.mb_set_host_io(net.handle, mode)
         pin_out.fill_(-1.0)
         m.mb_infer_volume(net.handle, pin_in, z, 1024, 1024, pin_out)
         np.testing.assert_array_equal(pin_out.numpy(), dev)

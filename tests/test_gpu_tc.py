@@ -148,8 +148,13 @@ def test_host_streaming_over_several_slabs_equals_device_path(z):
     dev = infer(net, v)
     pin_in = torch.from_numpy(v).pin_memory()
     pin_out = torch.empty((z, 1024, 1024), dtype=torch.float32).pin_memory()
+    m.mb_set_host_io(net.handle, m.MB_HOST_IO_SLABS)  # pinned buffers would otherwise be accessed directly
     for _ in range(2):  # the second call reuses the net's slab buffers, streams and events
         pin_out.fill_(-1.0)
         m.mb_infer_volume(net.handle, pin_in, z, 1024, 1024, pin_out)
         np.testing.assert_array_equal(pin_out.numpy(), dev)
+    m.mb_set_host_io(net.handle, m.MB_HOST_IO_AUTO)
+    pin_out.fill_(-1.0)
+    m.mb_infer_volume(net.handle, pin_in, z, 1024, 1024, pin_out)
+    np.testing.assert_array_equal(pin_out.numpy(), dev)
     net.close()
