@@ -156,12 +156,13 @@ mb_status mb_calibrate_fp8(mb_net* net, const uint8_t* slices, int64_t n, int64_
  * HOST pointers (both in and out on the host; synchronous, `stream` unused):
  *   - both page-locked and mapped (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory), on
  *     a GPU that reads host memory through the host's page tables (a coherent CPU-GPU link such
- *     as NVLink-C2C; cudaDevAttrPageableMemoryAccessUsesHostPageTables), and the net's host I/O
- *     mode MB_HOST_IO_AUTO (the default): the kernels read the input from and write the maps to
- *     the host buffers themselves, in the same launches as for device buffers; no device buffer
- *     and no copy;
- *   - otherwise (pageable memory, another link, or MB_HOST_IO_SLABS): the volume is streamed
- *     through device buffers in z-slabs, copies overlapped with compute.
+ *     as NVLink-C2C; cudaDevAttrPageableMemoryAccessUsesHostPageTables), the net's host I/O
+ *     mode MB_HOST_IO_AUTO (the default) and a teacher or FastMemb net: the kernels read the
+ *     input from and write the maps to the host buffers themselves, in the same launches as for
+ *     device buffers; no device buffer and no copy;
+ *   - otherwise (pageable memory, another link, MB_HOST_IO_SLABS, or a student net, whose kernel
+ *     outruns direct host access): the volume is streamed through device buffers in z-slabs,
+ *     copies overlapped with compute.
  * Both give the device path's maps bitwise. Mixed host/device pointers: MB_ERR_INVALID_ARG.
  */
 mb_status mb_infer_volume(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, void* out,

@@ -301,10 +301,12 @@ static mb_status infer_host_volume(mb_net* net, const uint8_t* in, int64_t z, in
     const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
     const size_t in_slice = (size_t)h * w, out_slice = (size_t)h * w * osz;
     cudaStream_t* s = net->slab_streams;
-    if (net->host_io == MB_HOST_IO_AUTO && coherent_host_link(net->device)) {
-        // Direct: the kernels load the input bytes from and store the maps to the host buffers
-        // over the link, in the launches of the device path. A step then moves exactly the input
-        // and output bytes across the link, with no device buffer and no exposed copy at either end.
+    // Direct: the kernels load the input bytes from and store the maps to the host buffers over
+    // the link, in the launches of the device path. A call then moves exactly the input and
+    // output bytes across the link, with no device buffer and no exposed copy at either end. The
+    // student's kernel (tens of Gvox/s) outruns what it gets from host memory this way (measured
+    // 28.6 against 37.1 Gvox/s in slabs on 1024x1024x32), so student nets always stream slabs.
+    if (net->host_io == MB_HOST_IO_AUTO && net->family != FAMILY_STUDENT && coherent_host_link(net->device)) {
         const void* mi = mapped_host_ptr(in);
         void* mo = mi ? mapped_host_ptr(out) : nullptr;
         if (mi && mo) {

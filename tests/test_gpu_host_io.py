@@ -49,7 +49,8 @@ def _launches(fn):
 @pytest.mark.parametrize("out_type", [0, 1])
 def test_direct_and_slab_host_io_equal_device_path(kind, out_type):
     """4 x 192 x 200 (a ragged strip and row tail for every kernel) from pinned buffers, in both
-    host I/O modes; the direct mode makes exactly the device path's launches."""
+    host I/O modes; the default mode (direct access; slabs for student nets) makes exactly the
+    device path's launches (one slab here)."""
     import torch
     from paper_1612_02120_gb300 import membrane as m
     net = _net(kind)
