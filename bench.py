@@ -18,11 +18,11 @@ timed beside it). L2 is flushed
   cfg8  the second teacher workload: the stand-in with its head fitted to the generator's membrane
         truth (a map that straddles 0.5): FP32/BF16/FP8 errors and accuracy against the truth, a
         student distilled from it, and the cascade under the stated rule on the cfg3 volume;
-  cfg6  FastMemb_3nm (one more stage, 109 field of view) on 2048x2048x8 (3 nm images), FP32 and
-        BF16, dense and sub-sampled by 2 (a 6 nm output map), errors on 2 seeded 256x256 crops;
+  cfg6  FastMemb_3nm (one more stage, 109 field of view) on 2048x2048x8 (3 nm images), FP32,
+        BF16 and FP16, dense and sub-sampled by 2 (a 6 nm output map), errors on 2 seeded 256x256 crops;
   cfg7  MaskExtend (Sec. 3.2): the +z transfer recursion on a 512x512 window for 16 sections
         (FP32), errors of one step's 3 class maps against the oracle on a 128x128 crop;
-  cfg5  FastMemb in dense form (Sec. 2.2) on the cfg1 volume, FP32 and BF16, dense and sub-sampled
+  cfg5  FastMemb in dense form (Sec. 2.2) on the cfg1 volume, FP32, BF16 and FP16, dense and sub-sampled
         by 2 (the pruned fragment tree), with errors against the oracle on 3 seeded 384x384 crops
         (true context; even crop origins, so the sub-sampled crops are the dense crops' even pixels).
 The reference arm (--impl reference) is the FP64 CPU oracle on bounded samples.
@@ -688,7 +688,8 @@ def main():
                   2 * int(rng.integers(0, (W - 384) // 2))) for _ in range(3)]
         refs = [oracle.forward_region(synth.FASTMEMB, fm_params, vol[z], y, x0, 384, 384) for z, y, x0 in crops]
         p = {"crops_384": crops}
-        for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16)):
+        for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16), ("fp16", m.MB_PREC_FP16)):
+            tol = TOL["bf16" if name == "fp16" else name]  # FP16 is held to the 16-bit (BF16) bar
             fm = m.Net(synth.FASTMEMB, prec, local, fm_params)
             with torch.cuda.stream(stream):
                 ms = time_device(lambda: m.mb_infer_volume(fm.handle, x, Z, H, W, out, m.MB_OUT_F32, stream),
@@ -697,7 +698,7 @@ def main():
             mv = vox / (statistics.mean(ms) / 1e3) / 1e6
             p[name] = {"mvox_s": mv, "ms": statistics.mean(ms),
                        "tflops": FASTMEMB_FLOP_PER_PX * mv * 1e6 / 1e12,
-                       "error": err_metrics(got, refs, TOL[name])}
+                       "error": err_metrics(got, refs, tol)}
             # sub-sampled output (factor 2, the pruned fragment tree): every slice's map at even
             # rows and columns; throughput counted in input voxels (and output voxels)
             osub = torch.empty((Z, H // 2, W // 2), dtype=torch.float32, device="cuda")
@@ -709,10 +710,11 @@ def main():
             p[name + "_subsampled2"] = {
                 "input_mvox_s": vox / (statistics.mean(ms) / 1e3) / 1e6,
                 "output_mvox_s": vox / 4 / (statistics.mean(ms) / 1e3) / 1e6, "ms": statistics.mean(ms),
-                "error": err_metrics(got, [r[::2, ::2] for r in refs], TOL[name])}
+                "error": err_metrics(got, [r[::2, ::2] for r in refs], tol)}
             del osub
             fm.close()
         p["bf16"]["speedup_vs_fp32"] = p["bf16"]["mvox_s"] / p["fp32"]["mvox_s"]
+        p["fp16"]["speedup_vs_bf16"] = p["fp16"]["mvox_s"] / p["bf16"]["mvox_s"]
         paths["cfg5_fastmemb_1024x1024x32"] = p
     # ---- cfg6: FastMemb_3nm on 2048x2048x8 ----------------------------------------------------------
     if "6" in configs:
@@ -729,7 +731,8 @@ def main():
                   2 * int(rng.integers(0, (W6 - 256) // 2))) for _ in range(2)]
         refs = [oracle.forward_region(f3, f3_params, vol6[z], y, x0, 256, 256) for z, y, x0 in crops]
         p = {"crops_256": crops, "flop_per_px": FASTMEMB3_FLOP_PER_PX}
-        for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16)):
+        for name, prec in (("fp32", m.MB_PREC_FP32), ("bf16", m.MB_PREC_BF16), ("fp16", m.MB_PREC_FP16)):
+            tol = TOL["bf16" if name == "fp16" else name]
             fm = m.Net(f3, prec, local, f3_params)
             k, w0 = (2, 1) if name == "fp32" else (args.steps, 3)
             with torch.cuda.stream(stream):
@@ -740,12 +743,12 @@ def main():
             mv = v6 / (statistics.mean(ms) / 1e3) / 1e6
             p[name] = {"mvox_s": mv, "ms": statistics.mean(ms), "tflops": FASTMEMB3_FLOP_PER_PX * mv * 1e6 / 1e12,
                        "error": err_metrics([o6[z, y:y + 256, x0:x0 + 256].cpu().numpy() for z, y, x0 in crops],
-                                            refs, TOL[name])}
+                                            refs, tol)}
             p[name + "_subsampled2"] = {
                 "input_mvox_s": v6 / (statistics.mean(ms_s) / 1e3) / 1e6,
                 "output_mvox_s": v6 / 4 / (statistics.mean(ms_s) / 1e3) / 1e6, "ms": statistics.mean(ms_s),
                 "error": err_metrics([s6[z, y // 2:(y + 256) // 2, x0 // 2:(x0 + 256) // 2].cpu().numpy()
-                                      for z, y, x0 in crops], [r[::2, ::2] for r in refs], TOL[name])}
+                                      for z, y, x0 in crops], [r[::2, ::2] for r in refs], tol)}
             fm.close()
         paths["cfg6_fastmemb3nm_2048x2048x8"] = p
         del x6, o6, s6

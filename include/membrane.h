@@ -86,12 +86,15 @@ typedef enum {
  * conv4x4 32->32 G=2 d=4, maxfilter d=4, softmax head conv4x4 32->2 d=8; no ReLU; radius 26,
  * so its slices need h, w >= 27) and FastMemb_3nm (Sec. 2.2, "A subsampling CNN for 3 nm data":
  * one more stage, conv4x4 32->32 G=2 d=8 and maxfilter d=8, then the head at d=16; radius 54,
- * slices h, w >= 55), both in FP32 and BF16; and MaskExtend (Sec. 3.2: conv4x4 12->32 G=2 d=1,
+ * slices h, w >= 55), both in FP32, BF16 and FP16 (the 16-bit nets: layer 1 on CUDA cores in
+ * FP32 stored as 16-bit, the later convs and the head on the tensor cores with FP32 accumulation;
+ * BF16 weights are split into two BF16 parts, FP16 weights are one FP16 value except the head's;
+ * FP16 activations are finite below 65504); and MaskExtend (Sec. 3.2: conv4x4 12->32 G=2 d=1,
  * maxfilter d=1, conv4x4 32->40 G=2 d=2, maxfilter d=2, conv4x4 40->48 G=2 d=4, maxfilter d=4,
  * conv4x4 48->56 G=2 d=8, maxfilter d=8, conv4x4 56->64 G=2 d=16, head 1x1 64->3 softmax; radius
- * 54) in FP32 (CUDA cores) and FP16 (tensor cores: FP16 operands, FP32 accumulation; MB_PREC_FP16
- * is accepted for MaskExtend nets only), run only through mb_mask_extend (the map calls return
- * MB_ERR_UNSUPPORTED).
+ * 54) in FP32 (CUDA cores) and FP16 (tensor cores: FP16 operands, FP32 accumulation), run only
+ * through mb_mask_extend (the map calls return MB_ERR_UNSUPPORTED). MB_PREC_FP16 is accepted for
+ * FastMemb and MaskExtend nets only.
  */
 typedef struct {
     int32_t kind, ksize, dilation, cin, cout, relu, maxout_groups;

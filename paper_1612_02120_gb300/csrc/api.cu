@@ -275,9 +275,9 @@ mb_status student_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, i
 static mb_status fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
                                  int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
                                  int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub = 1) {
-    if (net->prec == MB_PREC_BF16)
-        return bf16_fastmemb_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch,
-                                    out_slice, ot, st, sub);
+    if (net->prec == MB_PREC_BF16 || net->prec == MB_PREC_FP16)
+        return tc_fastmemb_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch,
+                                  out_slice, ot, st, sub);
     return simt_fastmemb_region(net, in, z, h, w, in_pitch, in_slice, y0, x0, rows, cols, out, out_pitch, out_slice,
                                 ot, st, sub);
 }
@@ -470,12 +470,12 @@ mb_status mb_net_create(const mb_layer_desc* layers, int32_t n_layers, mb_precis
         set_error("mb_net_create: MaskExtend runs in FP32 or FP16");
         return MB_ERR_UNSUPPORTED;
     }
-    if (fam != FAMILY_MASKEXTEND && prec == MB_PREC_FP16) {
-        set_error("mb_net_create: FP16 is MaskExtend's tensor-core precision only");
+    if (fam != FAMILY_MASKEXTEND && !is_fastmemb(fam) && prec == MB_PREC_FP16) {
+        set_error("mb_net_create: FP16 is a precision of the MaskExtend and FastMemb nets only");
         return MB_ERR_UNSUPPORTED;
     }
     if (is_fastmemb(fam) && prec == MB_PREC_FP8) {
-        set_error("mb_net_create: FastMemb runs in FP32 or BF16");
+        set_error("mb_net_create: FastMemb runs in FP32, BF16 or FP16");
         return MB_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -587,7 +587,8 @@ mb_status mb_load_weights(mb_net* net, const float* params, int64_t n_params) {
     net->calibrated = false;
     net->loaded = true;
     if (net->family == FAMILY_TEACHER && net->prec == MB_PREC_BF16) MB_TRY(tc_prepare(net));
-    if (is_fastmemb(net->family) && net->prec == MB_PREC_BF16) MB_TRY(fm_tc_prepare(net));
+    if (is_fastmemb(net->family) && (net->prec == MB_PREC_BF16 || net->prec == MB_PREC_FP16))
+        MB_TRY(fm_tc_prepare(net));
     if (net->family == FAMILY_MASKEXTEND && net->prec == MB_PREC_FP16) MB_TRY(me_tc_prepare(net));
     return MB_OK;
 }

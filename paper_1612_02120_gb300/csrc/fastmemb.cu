@@ -158,9 +158,10 @@ mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
     return MB_OK;
 }
 
-// BF16 path: layer 1 on CUDA cores (FP32 arithmetic, BF16 out); the two 32->64 dilated convs and
-// the head on the tensor cores (fastmemb_tc.cu); activations between layers are BF16 [slice][y][x][32].
-mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
+// Tensor-core paths (BF16 or FP16): layer 1 on CUDA cores (FP32 arithmetic, 16-bit out); the two
+// 32->64 dilated convs and the head on the tensor cores (fastmemb_tc.cu); activations between
+// layers are 16-bit [slice][y][x][32] of the net's type.
+mb_status tc_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w, int64_t in_pitch,
                                int64_t in_slice, int64_t y0, int64_t x0, int64_t rows, int64_t cols, void* out,
                                int64_t out_pitch, int64_t out_slice, mb_out_type ot, cudaStream_t st, int sub) {
     if (z == 0 || rows == 0 || cols == 0) return MB_OK;
@@ -178,8 +179,8 @@ mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
     const size_t budget = (size_t)3 << 30;
     const int64_t zc = std::min<int64_t>(std::min<int64_t>(std::max<size_t>(1, budget / per), 65535), z);
     MB_TRY(net->ws.ensure(per * (size_t)zc));
-    __nv_bfloat16* act[kFmMaxConvs - 1];
-    act[0] = static_cast<__nv_bfloat16*>(net->ws.ptr);
+    uint16_t* act[kFmMaxConvs - 1];
+    act[0] = static_cast<uint16_t*>(net->ws.ptr);
     for (int k = 1; k < nc - 1; ++k) act[k] = act[k - 1] + (size_t)zc * n[k - 1];
     const size_t osz = ot == MB_OUT_F32 ? 4 : 1;
     for (int64_t z0 = 0; z0 < z; z0 += zc) {
@@ -201,7 +202,10 @@ mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
         a.out_slice = n[0];
         a.out_pitch = g.c[0];
         a.wt = fm_simt_w(net, 0, nc, &a.bias);
-        MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT_BF16>(a, nz, st)));
+        if (net->prec == MB_PREC_FP16)
+            MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT_F16>(a, nz, st)));
+        else
+            MB_TRY((launch_fm<1, 1, 64, 8, FM_IN_U8, FM_OUT_MAXOUT_BF16>(a, nz, st)));
         for (int k = 1; k < nc; ++k) {
             const bool head = k == nc - 1;
             void* o = head ? static_cast<void*>(static_cast<uint8_t*>(out) + z0 * out_slice * osz) : act[k];

@@ -11,10 +11,13 @@
 // Output rows are walked in steps of d (one residue class y mod d at a time, the max-pooling
 // fragments of Sec. 2.2), so each staged row serves 4 consecutive output rows and is loaded once.
 //
-// Weights are split W = W_hi + W_lo, both BF16 (W_lo = BF16(W - W_hi)), and stacked along N, so
-// each MMA applies both and the result carries BF16 activation rounding only:
-//   layers: N = 128, columns n (hi) and 64 + n (lo) of conv channel n
-//   head:   16 columns per row tap ky: 0, 1 (hi of classes 0, 1) and 2, 3 (lo); the rest zero.
+// Two operand types, one template: BF16 and FP16 (both kind::f16 MMAs, A and B of the same type).
+// BF16 weights are split W = W_hi + W_lo, both BF16 (W_lo = BF16(W - W_hi)), and stacked along N,
+// so each MMA applies both and the result carries BF16 activation rounding only; FP16's 11-bit
+// significand makes the split unnecessary for the layers (half the B rows, N = 64):
+//   layers: BF16 N = 128, columns n (hi) and 64 + n (lo) of conv channel n; FP16 N = 64, column n
+//   head:   16 columns per row tap ky: 0, 1 (hi of classes 0, 1) and 2, 3 (lo); the rest zero
+//           (both types keep the split here: the head's MMAs cost the same with it).
 //           The 4 row taps are stacked along N instead of issued per output row: staged row u is
 //           multiplied once per (kx, K-half) into the accumulators of output rows u .. u-3, a
 //           ring of 8 row accumulators (N = 16 x the taps that fall inside the item, split where
@@ -22,21 +25,23 @@
 //           used columns of a row's accumulator after draining it.
 //
 // Warp roles (512 threads, 1 CTA per SM, persistent over work items):
-//   warp 0      TMEM owner; lane 0 issues the MMAs (BF16 -> FP32 in TMEM)
-//   warps 4-7   epilogue: TMEM -> registers; layers: hi + lo + bias, max-out, BF16 store;
+//   warp 0      TMEM owner; lane 0 issues the MMAs (16-bit operands -> FP32 in TMEM)
+//   warps 4-7   epilogue: TMEM -> registers; layers: (hi + lo) + bias, max-out, 16-bit store;
 //               head: z_c = hi + lo + bias, p = 1 / (1 + exp(z0 - z1)), FP32 or uint8 store
-//   warps 8-15  producers, two groups of 4 warps taking alternate staged rows: max-filter 4 BF16
+//   warps 8-15  producers, two groups of 4 warps taking alternate staged rows: max-filter 4 16-bit
 //               pixels of the previous stage into the A rows; one thread of each group
 //               bulk-prefetches the source rows of its staged row 4 ahead into L2
 // Every mbarrier wait is bounded (a global-timer limit), after which the CTA records
 // MB_ERR_TIMEOUT in a mapped host word, stops issuing work and frees its TMEM.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <climits>
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -49,7 +54,7 @@ namespace {
 constexpr int kFThreads = 512;
 constexpr int kFP = 178;                 // pixels per staged row (>= 128 + 3*16); 178 mod 8 = 2 spreads
                                          // the 4 chunk planes of one pixel pair over distinct banks
-constexpr int kFSlot = 4 * kFP * 16;     // bytes per staged row (4 chunks of 8 BF16 channels)
+constexpr int kFSlot = 4 * kFP * 16;     // bytes per staged row (4 chunks of 8 16-bit channels)
 constexpr int kFRing = 8;                // staged rows in flight
 constexpr int kFAcc = 4;                 // TMEM accumulators of the 32->64 layers
 constexpr int kHAcc = 8;                 // head: ring of row accumulators (16 columns each)
@@ -57,17 +62,18 @@ constexpr int kFTasks = 6;               // producer tasks per thread and row: c
 constexpr int kFPrefetch = 4;            // staged rows between a row's L2 prefetch and its loads
 constexpr uint64_t kFWaitNs = 4000000000ull;
 
-template <bool HEAD>
+template <bool HEAD, bool F16>
 struct FCfg {
-    // Layers: N = 128 per output row, one B block per (tap, K-half): [2 chunks][128 rows][16 B].
-    // Head: the 4 row taps are stacked along N, 16 rows each (4 used), one B block per (column
-    // tap, K-half): [2 chunks][64 rows][16 B]; a staged row's MMA covers up to 4 output rows.
-    static constexpr int N = HEAD ? 16 : 128;          // accumulator width per output row
-    static constexpr int kBRows = HEAD ? 64 : 128;     // B rows per block
+    // Layers: N = 128 (BF16, hi + lo) or 64 (FP16) per output row, one B block per (tap, K-half):
+    // [2 chunks][N rows][16 B]. Head: the 4 row taps are stacked along N, 16 rows each (4 used),
+    // one B block per (column tap, K-half): [2 chunks][64 rows][16 B]; a staged row's MMA covers
+    // up to 4 output rows.
+    static constexpr int N = HEAD ? 16 : (F16 ? 64 : 128);  // accumulator width per output row
+    static constexpr int kBRows = HEAD ? 64 : N;            // B rows per block
     static constexpr int kBlock = 2 * kBRows * 16;
     static constexpr int kBBytes = (HEAD ? 8 : 32) * kBlock;
     static constexpr int kAcc = HEAD ? kHAcc : kFAcc;
-    static constexpr int kTmemCols = HEAD ? 128 : 512;
+    static constexpr int kTmemCols = HEAD ? 128 : kFAcc * N;
     static constexpr int oB = 0;
     static constexpr int oRing = oB + kBBytes;
     static constexpr int oBias = oRing + kFRing * kFSlot;
@@ -76,11 +82,12 @@ struct FCfg {
     static constexpr int oMisc = oBar + kBars * 8;
     static constexpr int kSmem = oMisc + 16;
     static_assert(kSmem <= 227 * 1024, "shared memory");
+    static_assert(kTmemCols == 128 || kTmemCols == 256 || kTmemCols == 512, "TMEM allocation");
 };
 
 struct FmTcParams {
-    const __nv_bfloat16* in;   // previous stage, [slice][y][x][32], before its max-filter
-    void* out;                 // layers: BF16 [slice][y][x][32]; head: FP32 or uint8 [slice][y][x]
+    const uint16_t* in;        // previous stage, [slice][y][x][32] BF16 or FP16, before its max-filter
+    void* out;                 // layers: [slice][y][x][32] of the same type; head: FP32 or uint8 [slice][y][x]
     const uint8_t* wpack;      // B operands then 64 FP32 biases
     int* err;
     int64_t in_slice, in_pitch, out_slice, out_pitch;  // elements / pixels
@@ -161,19 +168,23 @@ __device__ __forceinline__ bool fm_next(const FmTcParams& p, FmCursor& c, FmItem
     return true;
 }
 
+// element-wise max of 8 packed 16-bit values
+template <bool F16>
 __device__ __forceinline__ uint4 bmax(uint4 a, uint4 b) {
+    using T2 = typename std::conditional<F16, __half2, __nv_bfloat162>::type;
     uint4 r;
-    const __nv_bfloat162* x = reinterpret_cast<const __nv_bfloat162*>(&a);
-    const __nv_bfloat162* y = reinterpret_cast<const __nv_bfloat162*>(&b);
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(&r);
+    const T2* x = reinterpret_cast<const T2*>(&a);
+    const T2* y = reinterpret_cast<const T2*>(&b);
+    T2* o = reinterpret_cast<T2*>(&r);
 #pragma unroll
     for (int i = 0; i < 4; ++i) o[i] = __hmax2(x[i], y[i]);
     return r;
 }
 
-template <bool HEAD>
+template <bool HEAD, bool F16>
 __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant__ FmTcParams p) {
-    using C = FCfg<HEAD>;
+    using C = FCfg<HEAD, F16>;
+    constexpr uint32_t kFmt = F16 ? ptx::kFmtF16 : ptx::kFmtBF16;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* row_full = reinterpret_cast<uint64_t*>(smem + C::oBar);
     uint64_t* row_empty = row_full + kFRing;
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
         if (lane == 0) {
             const uint64_t adesc0 = ptx::smem_desc(sbase + C::oRing, kFP * 16, 128);
             const uint64_t bdesc0 = ptx::smem_desc(sbase + C::oB, C::kBRows * 16, 128);
-            constexpr uint32_t idesc = ptx::idesc_f32acc(ptx::kFmtBF16, 128, C::N);
+            constexpr uint32_t idesc = ptx::idesc_f32acc(kFmt, 128, C::N);
             uint32_t row_seq = 0, acc_seq = 0;
             bool ok = true;
             // The waits for output row j+1 (its one new staged row and its accumulator) are taken
@@ -274,10 +285,8 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                 auto slot_of = [](uint32_t q) { return (uint32_t)(K - 1) - q % (uint32_t)K; };
                 const uint64_t adesc = ptx::smem_desc(sbase + C::oRing, kFP * 16, 128);
                 const uint64_t bdesc = ptx::smem_desc(sbase + C::oB, C::kBRows * 16, 128);
-                const uint32_t idn[4] = {ptx::idesc_f32acc(ptx::kFmtBF16, 128, 16),
-                                         ptx::idesc_f32acc(ptx::kFmtBF16, 128, 32),
-                                         ptx::idesc_f32acc(ptx::kFmtBF16, 128, 48),
-                                         ptx::idesc_f32acc(ptx::kFmtBF16, 128, 64)};
+                const uint32_t idn[4] = {ptx::idesc_f32acc(kFmt, 128, 16), ptx::idesc_f32acc(kFmt, 128, 32),
+                                         ptx::idesc_f32acc(kFmt, 128, 48), ptx::idesc_f32acc(kFmt, 128, 64)};
                 FmCursor cur = fm_begin(p);
                 FmItem it;
                 while (fm_next(p, cur, it)) {
@@ -387,25 +396,37 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                     uint32_t w[16];
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
-                        // conv channels 32 half .. 32 half + 31: hi in columns n, lo in 64 + n
-                        float hi[32], lo[32];
+                        // conv channels 32 half .. 32 half + 31: column n (BF16: hi; lo in 64 + n)
+                        float hi[32];
                         ptx::tmem_ld32(ta + 32u * half, hi);
-                        ptx::tmem_ld32(ta + 64u + 32u * half, lo);
+                        if constexpr (F16) {
 #pragma unroll
-                        for (int c = 0; c < 16; c += 2) {
-                            const int n = 32 * half + 2 * c;
-                            const float a0 = fmaxf((hi[2 * c] + lo[2 * c]) + bias[n],
-                                                   (hi[2 * c + 1] + lo[2 * c + 1]) + bias[n + 1]);
-                            const float a1 = fmaxf((hi[2 * c + 2] + lo[2 * c + 2]) + bias[n + 2],
-                                                   (hi[2 * c + 3] + lo[2 * c + 3]) + bias[n + 3]);
-                            __nv_bfloat162 v = __floats2bfloat162_rn(a0, a1);
-                            w[8 * half + c / 2] = *reinterpret_cast<uint32_t*>(&v);
+                            for (int c = 0; c < 16; c += 2) {
+                                const int n = 32 * half + 2 * c;
+                                const float a0 = fmaxf(hi[2 * c] + bias[n], hi[2 * c + 1] + bias[n + 1]);
+                                const float a1 = fmaxf(hi[2 * c + 2] + bias[n + 2], hi[2 * c + 3] + bias[n + 3]);
+                                __half2 v = __floats2half2_rn(a0, a1);
+                                w[8 * half + c / 2] = *reinterpret_cast<uint32_t*>(&v);
+                            }
+                        } else {
+                            float lo[32];
+                            ptx::tmem_ld32(ta + 64u + 32u * half, lo);
+#pragma unroll
+                            for (int c = 0; c < 16; c += 2) {
+                                const int n = 32 * half + 2 * c;
+                                const float a0 = fmaxf((hi[2 * c] + lo[2 * c]) + bias[n],
+                                                       (hi[2 * c + 1] + lo[2 * c + 1]) + bias[n + 1]);
+                                const float a1 = fmaxf((hi[2 * c + 2] + lo[2 * c + 2]) + bias[n + 2],
+                                                       (hi[2 * c + 3] + lo[2 * c + 3]) + bias[n + 3]);
+                                __nv_bfloat162 v = __floats2bfloat162_rn(a0, a1);
+                                w[8 * half + c / 2] = *reinterpret_cast<uint32_t*>(&v);
+                            }
                         }
                     }
                     ptx::tc_fence_before();
                     ptx::mbar_arrive(&acc_free[s]);
                     if (store) {
-                        uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(p.out) +
+                        uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(p.out) +
                                                             (int64_t)it.z * p.out_slice +
                                                             ((int64_t)y * p.out_pitch + x) * 32);
                         o[0] = make_uint4(w[0], w[1], w[2], w[3]);
@@ -430,7 +451,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
         FmCursor cur = fm_begin(p);
         FmItem it;
         while (fm_next(p, cur, it)) {
-            const __nv_bfloat16* src = p.in + (int64_t)it.z * p.in_slice;
+            const uint16_t* src = p.in + (int64_t)it.z * p.in_slice;
             // source pixels one staged row reads: stride (npix - 1) + dm + 1 from stride x0, clipped
             const int sx0 = p.stride * it.x0;
             const int pf_cols = (int)min((int64_t)(p.stride * (127 + 3 * d) + p.dm + 1), p.src_cols - sx0);
@@ -441,7 +462,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                 if (pt == 0 && u + kFPrefetch < it.rows + 3) {
                     const int yp = it.ry + d * (it.m0 + u + kFPrefetch);
                     if (yp < p.in_rows && pf_cols > 0) {
-                        const __nv_bfloat16* r0 = src + ((int64_t)(p.stride * yp) * p.in_pitch + sx0) * 32;
+                        const uint16_t* r0 = src + ((int64_t)(p.stride * yp) * p.in_pitch + sx0) * 32;
                         ptx::prefetch_l2_bulk(r0, (uint32_t)pf_cols * 64u);
                         ptx::prefetch_l2_bulk(r0 + dyo, (uint32_t)pf_cols * 64u);
                     }
@@ -453,13 +474,13 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                     const int xin = it.x0 + (e >> 2);
                     v[i] = make_uint4(0, 0, 0, 0);
                     if (e < ntask && yin < p.in_rows && xin < p.in_cols) {
-                        const __nv_bfloat16* a =
+                        const uint16_t* a =
                             src + ((int64_t)(p.stride * yin) * p.in_pitch + p.stride * xin) * 32 + (e & 3) * 8;
                         const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(a));
                         const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(a + dxo));
                         const uint4 r2 = __ldg(reinterpret_cast<const uint4*>(a + dyo));
                         const uint4 r3 = __ldg(reinterpret_cast<const uint4*>(a + dyo + dxo));
-                        v[i] = bmax(bmax(r0, r1), bmax(r2, r3));
+                        v[i] = bmax<F16>(bmax<F16>(r0, r1), bmax<F16>(r2, r3));
                     }
                 }
                 wait_bar(&row_empty[slot], ((q / kFRing) & 1) ^ 1, abort_flag, p.err, p.wait_ns);
@@ -497,13 +518,28 @@ float bf16_value(uint16_t b) {
     return f;
 }
 
+uint16_t f16_bits_rn(float f) {
+    const __half h = __float2half_rn(f);
+    uint16_t u;
+    memcpy(&u, &h, 2);
+    return u;
+}
+
+float f16_value(uint16_t b) {
+    __half h;
+    memcpy(&h, &b, 2);
+    return __half2float(h);
+}
+
 // Pack a conv 4x4 32->C layer W[c][ci][ky][kx], b[c] as B operands: blocks of [chunk kc][row][8
-// BF16], ci = 16 h + 8 kc + e, per (tap t = 4 ky + kx, K-half h) for the layers and per (column tap
-// kx, K-half h) for the head, whose row taps are stacked along the rows. Part 0 of a weight is
-// BF16(W), part 1 BF16(W - BF16(W)). Then 64 FP32 biases.
-template <bool HEAD>
+// 16-bit], ci = 16 h + 8 kc + e, per (tap t = 4 ky + kx, K-half h) for the layers and per (column
+// tap kx, K-half h) for the head, whose row taps are stacked along the rows. Part 0 of a weight is
+// T(W), part 1 T(W - T(W)) for T = BF16 (layers and head) or FP16 (the head only: FP16 layers
+// carry part 0 alone). Then 64 FP32 biases.
+template <bool HEAD, bool F16>
 void fm_pack(const float* W, const float* b, int channels, std::vector<uint8_t>& out) {
-    using C = FCfg<HEAD>;
+    using C = FCfg<HEAD, F16>;
+    constexpr bool kLo = HEAD || !F16;
     out.assign(C::kBBytes + 64 * 4, 0);
     for (int c = 0; c < channels; ++c)
         for (int ci = 0; ci < 32; ++ci)
@@ -511,24 +547,25 @@ void fm_pack(const float* W, const float* b, int channels, std::vector<uint8_t>&
                 for (int kx = 0; kx < 4; ++kx) {
                     const int t = ky * 4 + kx, h = ci / 16, kc = (ci % 16) / 8, e = ci % 8;
                     const float w = W[((c * 32 + ci) * 4 + ky) * 4 + kx];
-                    const uint16_t whi = bf16_bits_rn(w);
-                    const uint16_t wlo = bf16_bits_rn(w - bf16_value(whi));
+                    const uint16_t whi = F16 ? f16_bits_rn(w) : bf16_bits_rn(w);
+                    const uint16_t wlo =
+                        F16 ? f16_bits_rn(w - f16_value(whi)) : bf16_bits_rn(w - bf16_value(whi));
                     // layers: block (tap, K-half), rows c (hi) and 64 + c (lo); head: block (column
                     // tap, K-half), rows 16 ky + c (hi) and 16 ky + 2 + c (lo)
                     const int rhi = HEAD ? 16 * ky + c : c, rlo = HEAD ? 16 * ky + 2 + c : 64 + c;
                     const int blk_i = HEAD ? kx * 2 + h : t * 2 + h;
                     uint8_t* blk = out.data() + blk_i * C::kBlock + kc * C::kBRows * 16;
                     memcpy(blk + rhi * 16 + e * 2, &whi, 2);
-                    memcpy(blk + rlo * 16 + e * 2, &wlo, 2);
+                    if (kLo) memcpy(blk + rlo * 16 + e * 2, &wlo, 2);
                 }
     std::vector<float> bias(64, 0.f);
     for (int c = 0; c < channels; ++c) bias[c] = b[c];
     memcpy(out.data() + C::kBBytes, bias.data(), 64 * 4);
 }
 
-template <bool HEAD>
+template <bool HEAD, bool F16>
 mb_status launch_fm_tc(const FmTcParams& p, cudaStream_t st) {
-    using C = FCfg<HEAD>;
+    using C = FCfg<HEAD, F16>;
     static int n_sms = 0;
     if (n_sms == 0) {
         int dev = 0;
@@ -537,12 +574,12 @@ mb_status launch_fm_tc(const FmTcParams& p, cudaStream_t st) {
     }
     static bool attr = false;
     if (!attr) {
-        MB_CUDA(cudaFuncSetAttribute(fm_tc_conv<HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
+        MB_CUDA(cudaFuncSetAttribute(fm_tc_conv<HEAD, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem));
         attr = true;
     }
     // one range per SM, or fewer when a range would get under 8 rows
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_sms, (p.total_rows + 7) / 8));
-    fm_tc_conv<HEAD><<<grid, kFThreads, C::kSmem, st>>>(p);
+    fm_tc_conv<HEAD, F16><<<grid, kFThreads, C::kSmem, st>>>(p);
     count_launch();
     MB_CUDA(cudaGetLastError());
     return MB_OK;
@@ -571,13 +608,14 @@ mb_status fm_tc_prepare(mb_net* net) {
     const int nc = fastmemb_convs(net->family);
     const float* P = net->host_params.data() + 64 * 16 + 64;
     std::vector<uint8_t> pk;
+    const bool f16 = net->prec == MB_PREC_FP16;
     for (int l = 0; l < nc - 1; ++l) {
         const bool head = l == nc - 2;
         const int co = head ? 2 : 64;
         if (!head)
-            fm_pack<false>(P, P + co * 32 * 16, co, pk);
+            f16 ? fm_pack<false, true>(P, P + co * 32 * 16, co, pk) : fm_pack<false, false>(P, P + co * 32 * 16, co, pk);
         else
-            fm_pack<true>(P, P + co * 32 * 16, co, pk);
+            f16 ? fm_pack<true, true>(P, P + co * 32 * 16, co, pk) : fm_pack<true, false>(P, P + co * 32 * 16, co, pk);
         P += co * 32 * 16 + co;
         if (!S->d_wpack[l]) MB_TRY(dev_alloc((void**)&S->d_wpack[l], pk.size()));
         MB_CUDA(cudaMemcpy(S->d_wpack[l], pk.data(), pk.size(), cudaMemcpyHostToDevice));
@@ -622,7 +660,7 @@ mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, 
         return MB_ERR_NOT_READY;
     }
     FmTcParams p{};
-    p.in = static_cast<const __nv_bfloat16*>(in);
+    p.in = static_cast<const uint16_t*>(in);
     p.out = out;
     p.wpack = S->d_wpack[layer];
     p.err = S->d_err;
@@ -649,7 +687,9 @@ mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, 
     const char* stall = getenv("MB_FAULT_STALL");
     p.fault_stall = (stall && stall[0] == '1') ? 1 : 0;
     p.wait_ns = p.fault_stall ? 200000000ull : kFWaitNs;
-    return layer == fastmemb_convs(net->family) - 2 ? launch_fm_tc<true>(p, st) : launch_fm_tc<false>(p, st);
+    const bool head = layer == fastmemb_convs(net->family) - 2;
+    if (net->prec == MB_PREC_FP16) return head ? launch_fm_tc<true, true>(p, st) : launch_fm_tc<false, true>(p, st);
+    return head ? launch_fm_tc<true, false>(p, st) : launch_fm_tc<false, false>(p, st);
 }
 
 }  // namespace mb

@@ -6,9 +6,10 @@
 // TH x 32 tile of one fragment: 4 consecutive fragment pixels x CPT conv channels per thread,
 // input channels staged CC at a time with the previous stage's dilated 2x2 max-filter (and an
 // optional source stride) applied while staging. Epilogues: max-out of adjacent channel pairs
-// (FP32 or BF16 out), or the 2-class softmax.
+// (FP32, BF16 or FP16 out), or the 2-class softmax.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -19,7 +20,7 @@ namespace mb {
 namespace {
 
 enum { FM_IN_U8 = 0, FM_IN_F32 = 1 };
-enum { FM_OUT_MAXOUT = 0, FM_OUT_SOFTMAX_F32 = 1, FM_OUT_SOFTMAX_U8 = 2, FM_OUT_MAXOUT_BF16 = 3 };
+enum { FM_OUT_MAXOUT = 0, FM_OUT_SOFTMAX_F32 = 1, FM_OUT_SOFTMAX_U8 = 2, FM_OUT_MAXOUT_BF16 = 3, FM_OUT_MAXOUT_F16 = 4 };
 
 struct FmArgs {
     const void* in;
@@ -159,9 +160,10 @@ __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
 
     const int oy = ry + d * (fy0 + ty);
     if (oy >= a.out_h) return;
-    if constexpr (OUT == FM_OUT_MAXOUT_BF16) {
+    if constexpr (OUT == FM_OUT_MAXOUT_BF16 || OUT == FM_OUT_MAXOUT_F16) {
+        // 16-bit activations (BF16 or FP16), the tensor-core layers' input
         static_assert(CPT >= 8, "max-out epilogue writes 4 channels per 8 conv channels");
-        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + (int64_t)zi * a.out_slice;
+        uint16_t* o = static_cast<uint16_t*>(a.out) + (int64_t)zi * a.out_slice;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int ox = rx + d * (fx0 + 4 * tx + j);
@@ -169,11 +171,18 @@ __global__ void __launch_bounds__(256) fm_conv(const FmArgs a) {
 #pragma unroll
                 for (int q = 0; q < CPT / 8; ++q) {
                     const float* v = acc[j] + 8 * q;
-                    __nv_bfloat162 lo = __floats2bfloat162_rn(fmaxf(v[0], v[1]), fmaxf(v[2], v[3]));
-                    __nv_bfloat162 hi = __floats2bfloat162_rn(fmaxf(v[4], v[5]), fmaxf(v[6], v[7]));
+                    const float2 l = make_float2(fmaxf(v[0], v[1]), fmaxf(v[2], v[3]));
+                    const float2 h = make_float2(fmaxf(v[4], v[5]), fmaxf(v[6], v[7]));
                     uint2 u;
-                    u.x = *reinterpret_cast<uint32_t*>(&lo);
-                    u.y = *reinterpret_cast<uint32_t*>(&hi);
+                    if constexpr (OUT == FM_OUT_MAXOUT_F16) {
+                        __half2 lo = __floats2half2_rn(l.x, l.y), hi = __floats2half2_rn(h.x, h.y);
+                        u.x = *reinterpret_cast<uint32_t*>(&lo);
+                        u.y = *reinterpret_cast<uint32_t*>(&hi);
+                    } else {
+                        __nv_bfloat162 lo = __floats2bfloat162_rn(l.x, l.y), hi = __floats2bfloat162_rn(h.x, h.y);
+                        u.x = *reinterpret_cast<uint32_t*>(&lo);
+                        u.y = *reinterpret_cast<uint32_t*>(&hi);
+                    }
                     *reinterpret_cast<uint2*>(o + ((int64_t)oy * a.out_pitch + ox) * (CO / 2) + (CPT / 2) * cg + 4 * q) =
                         u;
                 }

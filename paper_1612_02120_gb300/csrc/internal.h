@@ -111,19 +111,19 @@ mb_status simt_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_
                                int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
                                int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
                                mb_out_type ot, cudaStream_t st, int sub);
-mb_status bf16_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
-                               int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
-                               int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
-                               mb_out_type ot, cudaStream_t st, int sub);
-// FastMemb tensor-core layers (fastmemb_tc.cu): pack split BF16 B operands of the 32->64 convs and
-// the head, launch one (the head ends with the softmax, FP32 or uint8 out), poll the device-side
-// wait error word.
+mb_status tc_fastmemb_region(mb_net* net, const uint8_t* in, int64_t z, int64_t h, int64_t w,
+                             int64_t in_pitch, int64_t in_slice, int64_t y0, int64_t x0, int64_t rows,
+                             int64_t cols, void* out, int64_t out_pitch, int64_t out_slice,
+                             mb_out_type ot, cudaStream_t st, int sub);
+// FastMemb tensor-core layers (fastmemb_tc.cu): pack the B operands of the 32->64 convs and the
+// head (split BF16, or FP16 for FP16 nets), launch one (the head ends with the softmax, FP32 or
+// uint8 out), poll the device-side wait error word.
 mb_status fm_tc_prepare(mb_net* net);
 void fm_tc_release(mb_net* net);
 mb_status fm_tc_poll_error(mb_net* net);
-// in: [slice][src_rows][src_cols(pitch)][32] BF16; the conv reads input (r, c) = 2x2 max (dilation
-// dm) at source (stride r, stride c), for r < in_rows, c < in_cols. layer: 0-based index of the
-// conv after conv1; the last one is the head.
+// in: [slice][src_rows][src_cols(pitch)][32] BF16 or FP16 (the net's type); the conv reads input
+// (r, c) = 2x2 max (dilation dm) at source (stride r, stride c), for r < in_rows, c < in_cols.
+// layer: 0-based index of the conv after conv1; the last one is the head.
 mb_status fm_tc_layer(mb_net* net, int layer, const void* in, int64_t in_slice, int64_t in_pitch, int64_t src_rows,
                       int64_t src_cols, int in_rows, int in_cols, int dm, int stride, void* out, int64_t out_slice,
                       int64_t out_pitch, int out_h, int out_w, int d, int nz, int out_u8, cudaStream_t st);

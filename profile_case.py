@@ -63,7 +63,7 @@ def main():
     x = torch.from_numpy(v).cuda()
     out = torch.empty((a.z, a.h, a.w), dtype=torch.float32, device="cuda")
     if a.net == "fastmemb":
-        prec = {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16}[a.prec]
+        prec = {"fp32": m.MB_PREC_FP32, "bf16": m.MB_PREC_BF16, "fp16": m.MB_PREC_FP16}[a.prec]
         net = m.Net(synth.FASTMEMB, prec, 0, synth.init_params(synth.FASTMEMB, synth.FASTMEMB_WEIGHT_SEED))
     elif a.prec == "student":
         net = m.Net(synth.STUDENT, m.MB_PREC_BF16, 0, synth.init_params(synth.STUDENT, synth.STUDENT_WEIGHT_SEED))

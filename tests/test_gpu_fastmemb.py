@@ -135,13 +135,15 @@ def test_error_codes():
     n.close()
 
 
-# ---- BF16: the two 32->64 convs on the tensor cores --------------------------------------------
+# ---- BF16 and FP16: the two 32->64 convs and the head on the tensor cores -----------------------
+# (the "bf16" tests run for both 16-bit types: BF16 with split weights, FP16 without; both are held
+# to the stated BF16 tolerances)
 
-@pytest.fixture(scope="module")
-def net_bf16():
+@pytest.fixture(scope="module", params=["bf16", "fp16"])
+def net_bf16(request):
     from paper_1612_02120_gb300 import build, membrane as m
     build.build()
-    n = make_net(F, m.MB_PREC_BF16, fm_params())
+    n = make_net(F, m.MB_PREC_BF16 if request.param == "bf16" else m.MB_PREC_FP16, fm_params())
     yield n
     n.close()
 
@@ -287,12 +289,12 @@ def fm3_params():
     return synth.init_params(F3, synth.FASTMEMB_3NM_WEIGHT_SEED, center_head=True)
 
 
-@pytest.fixture(scope="module")
-def nets3():
+@pytest.fixture(scope="module", params=["bf16", "fp16"])
+def nets3(request):
     from paper_1612_02120_gb300 import build, membrane as m
     build.build()
     a = make_net(F3, m.MB_PREC_FP32, fm3_params())
-    b = make_net(F3, m.MB_PREC_BF16, fm3_params())
+    b = make_net(F3, m.MB_PREC_BF16 if request.param == "bf16" else m.MB_PREC_FP16, fm3_params())
     yield a, b
     a.close()
     b.close()

@@ -128,9 +128,9 @@ def test_fp16_timed_out_device_wait_is_reported_and_context_survives(net16, monk
     np.testing.assert_array_equal(out.cpu().numpy(), ref_m)
 
 
-def test_fp16_is_maskextend_only():
+def test_fp16_is_maskextend_and_fastmemb_only():
     from paper_1612_02120_gb300 import membrane as m
-    for layers in (synth.TEACHER, synth.STUDENT, synth.FASTMEMB, synth.FASTMEMB_3NM):
+    for layers in (synth.TEACHER, synth.STUDENT):
         with pytest.raises(m.MembraneError) as e:
             m.mb_net_create(layers, m.MB_PREC_FP16, 0)
         assert e.value.status == m.MB_ERR_UNSUPPORTED
