@@ -68,12 +68,15 @@ struct FCfg {
     // [2 chunks][N rows][16 B]. Head: the 4 row taps are stacked along N, 16 rows each (4 used),
     // one B block per (column tap, K-half): [2 chunks][64 rows][16 B]; a staged row's MMA covers
     // up to 4 output rows.
-    static constexpr int N = HEAD ? 16 : (F16 ? 64 : 128);  // accumulator width per output row
-    static constexpr int kBRows = HEAD ? 64 : N;            // B rows per block
+    // kStack: the 4 row taps stacked along N (the head, and the FP16 layers): one MMA per staged
+    // row and (column tap, K-half) into a ring of row accumulators.
+    static constexpr bool kStack = HEAD || F16;
+    static constexpr int N = HEAD ? 16 : (F16 ? 64 : 128);  // accumulator width per output row (= per row tap when stacked)
+    static constexpr int kBRows = kStack ? 4 * N : N;       // B rows per block
     static constexpr int kBlock = 2 * kBRows * 16;
-    static constexpr int kBBytes = (HEAD ? 8 : 32) * kBlock;
-    static constexpr int kAcc = HEAD ? kHAcc : kFAcc;
-    static constexpr int kTmemCols = HEAD ? 128 : kFAcc * N;
+    static constexpr int kBBytes = (kStack ? 8 : 32) * kBlock;
+    static constexpr int kAcc = kStack ? kHAcc : kFAcc;
+    static constexpr int kTmemCols = kAcc * N;
     static constexpr int oB = 0;
     static constexpr int oRing = oB + kBBytes;
     static constexpr int oBias = oRing + kFRing * kFSlot;
@@ -228,12 +231,19 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
     const uint32_t tbase = *tmem_slot;
     const uint32_t sbase = ptx::smem_u32(smem);
     const int d = p.d;
-    if constexpr (HEAD) {
-        // the head's MMAs only accumulate (a staged row adds to up to 4 rows at once): its used
+    if constexpr (C::kStack) {
+        // stacked MMAs only accumulate (a staged row adds to up to 4 rows at once): the used
         // accumulator columns start at zero, and the epilogue re-zeroes them after each drain
         if (warp >= 4 && warp < 8) {
             const uint32_t lanes = (uint32_t)(32 * (warp - 4)) << 16;
-            for (int sl = 0; sl < C::kAcc; ++sl) ptx::tmem_st4_zero(tbase + lanes + (uint32_t)C::N * sl);
+            for (int sl = 0; sl < C::kAcc; ++sl) {
+                if constexpr (HEAD) {
+                    ptx::tmem_st4_zero(tbase + lanes + (uint32_t)C::N * sl);
+                } else {
+                    ptx::tmem_st32_zero(tbase + lanes + (uint32_t)C::N * sl);
+                    ptx::tmem_st32_zero(tbase + lanes + (uint32_t)C::N * sl + 32u);
+                }
+            }
         }
         ptx::tc_fence_before();
         __syncthreads();
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                         }
                 }
             };
-            if constexpr (HEAD) {
+            if constexpr (C::kStack) {
                 // Staged row u of an item feeds output rows u - ky for ky = 0..3 (the row taps stacked
                 // along N): one MMA per (column tap, K-half) with D = the accumulators of rows u, u-1,
                 // u-2, u-3. Output row sequence q lives in ring slot K-1 - q mod K, so these rows sit in
@@ -285,8 +295,8 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                 auto slot_of = [](uint32_t q) { return (uint32_t)(K - 1) - q % (uint32_t)K; };
                 const uint64_t adesc = ptx::smem_desc(sbase + C::oRing, kFP * 16, 128);
                 const uint64_t bdesc = ptx::smem_desc(sbase + C::oB, C::kBRows * 16, 128);
-                const uint32_t idn[4] = {ptx::idesc_f32acc(kFmt, 128, 16), ptx::idesc_f32acc(kFmt, 128, 32),
-                                         ptx::idesc_f32acc(kFmt, 128, 48), ptx::idesc_f32acc(kFmt, 128, 64)};
+                const uint32_t idn[4] = {ptx::idesc_f32acc(kFmt, 128, C::N), ptx::idesc_f32acc(kFmt, 128, 2 * C::N),
+                                         ptx::idesc_f32acc(kFmt, 128, 3 * C::N), ptx::idesc_f32acc(kFmt, 128, 4 * C::N)};
                 FmCursor cur = fm_begin(p);
                 FmItem it;
                 while (fm_next(p, cur, it)) {
@@ -312,10 +322,10 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                                 for (int h = 0; h < 2; ++h) {
                                     const uint64_t ad = arow + (uint64_t)((h * 2 * kFP * 16 + d * kx * 16) >> 4);
                                     const uint64_t bg = bdesc + (uint64_t)(((kx * 2 + h) * C::kBlock) >> 4);
-                                    ptx::mma_bf16(tbase + (uint32_t)C::N * s0, ad, bg + (uint64_t)((blo * 256) >> 4),
-                                                  idn[n1 - 1], 1u);
+                                    ptx::mma_bf16(tbase + (uint32_t)C::N * s0, ad,
+                                                  bg + (uint64_t)((blo * C::N * 16) >> 4), idn[n1 - 1], 1u);
                                     if (n1 < nb)
-                                        ptx::mma_bf16(tbase, ad, bg + (uint64_t)(((blo + n1) * 256) >> 4),
+                                        ptx::mma_bf16(tbase, ad, bg + (uint64_t)(((blo + n1) * C::N * 16) >> 4),
                                                       idn[nb - n1 - 1], 1u);
                                 }
                         }
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
             const int x = it.x0 + px;
             for (int j = 0; j < it.rows; ++j) {
                 const uint32_t qa = acc_seq + j;
-                const uint32_t s = HEAD ? (uint32_t)(C::kAcc - 1) - qa % (uint32_t)C::kAcc : qa % (uint32_t)C::kAcc;
+                const uint32_t s = C::kStack ? (uint32_t)(C::kAcc - 1) - qa % (uint32_t)C::kAcc : qa % (uint32_t)C::kAcc;
                 wait_bar(&acc_full[s], (qa / C::kAcc) & 1, abort_flag, p.err, p.wait_ns);
                 ptx::tc_fence_after();
                 const uint32_t ta = tbase + lanes + (uint32_t)C::N * s;
@@ -399,6 +409,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fm_tc_conv(const __grid_constant
                         // conv channels 32 half .. 32 half + 31: column n (BF16: hi; lo in 64 + n)
                         float hi[32];
                         ptx::tmem_ld32(ta + 32u * half, hi);
+                        if constexpr (C::kStack) ptx::tmem_st32_zero(ta + 32u * half);  // accumulated into
                         if constexpr (F16) {
 #pragma unroll
                             for (int c = 0; c < 16; c += 2) {
@@ -550,10 +561,12 @@ void fm_pack(const float* W, const float* b, int channels, std::vector<uint8_t>&
                     const uint16_t whi = F16 ? f16_bits_rn(w) : bf16_bits_rn(w);
                     const uint16_t wlo =
                         F16 ? f16_bits_rn(w - f16_value(whi)) : bf16_bits_rn(w - bf16_value(whi));
-                    // layers: block (tap, K-half), rows c (hi) and 64 + c (lo); head: block (column
-                    // tap, K-half), rows 16 ky + c (hi) and 16 ky + 2 + c (lo)
-                    const int rhi = HEAD ? 16 * ky + c : c, rlo = HEAD ? 16 * ky + 2 + c : 64 + c;
-                    const int blk_i = HEAD ? kx * 2 + h : t * 2 + h;
+                    // BF16 layers: block (tap, K-half), rows c (hi) and 64 + c (lo); FP16 layers: block
+                    // (column tap, K-half), rows 64 ky + c; head: block (column tap, K-half), rows
+                    // 16 ky + c (hi) and 16 ky + 2 + c (lo)
+                    const int rhi = HEAD ? 16 * ky + c : (F16 ? 64 * ky + c : c);
+                    const int rlo = HEAD ? 16 * ky + 2 + c : 64 + c;
+                    const int blk_i = C::kStack ? kx * 2 + h : t * 2 + h;
                     uint8_t* blk = out.data() + blk_i * C::kBlock + kc * C::kBRows * 16;
                     memcpy(blk + rhi * 16 + e * 2, &whi, 2);
                     if (kLo) memcpy(blk + rlo * 16 + e * 2, &wlo, 2);
