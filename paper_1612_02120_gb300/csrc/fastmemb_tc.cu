@@ -14,15 +14,17 @@
 // Two operand types, one template: BF16 and FP16 (both kind::f16 MMAs, A and B of the same type).
 // BF16 weights are split W = W_hi + W_lo, both BF16 (W_lo = BF16(W - W_hi)), and stacked along N,
 // so each MMA applies both and the result carries BF16 activation rounding only; FP16's 11-bit
-// significand makes the split unnecessary for the layers (half the B rows, N = 64):
-//   layers: BF16 N = 128, columns n (hi) and 64 + n (lo) of conv channel n; FP16 N = 64, column n
+// significand makes the split unnecessary for the layers (64 columns per row tap):
+//   BF16 layers: N = 128 per output row, columns n (hi) and 64 + n (lo) of conv channel n
+//   FP16 layers: 64 columns per row tap ky (column n = conv channel n), the 4 row taps stacked
+//           along N (N = 256) like the head's, into a ring of 8 row accumulators of 64 columns
 //   head:   16 columns per row tap ky: 0, 1 (hi of classes 0, 1) and 2, 3 (lo); the rest zero
 //           (both types keep the split here: the head's MMAs cost the same with it).
-//           The 4 row taps are stacked along N instead of issued per output row: staged row u is
+//           Stacked row taps (head, FP16 layers) instead of MMAs per output row: staged row u is
 //           multiplied once per (kx, K-half) into the accumulators of output rows u .. u-3, a
-//           ring of 8 row accumulators (N = 16 x the taps that fall inside the item, split where
-//           the window wraps the ring); every head MMA accumulates, and the epilogue zeroes the 4
-//           used columns of a row's accumulator after draining it.
+//           ring of 8 row accumulators (N = 16 or 64 x the taps that fall inside the item, split where
+//           the window wraps the ring); every stacked MMA accumulates, and the epilogue zeroes
+//           the used columns of a row's accumulator after draining it.
 //
 // Warp roles (512 threads, 1 CTA per SM, persistent over work items):
 //   warp 0      TMEM owner; lane 0 issues the MMAs (16-bit operands -> FP32 in TMEM)
@@ -64,12 +66,11 @@ constexpr uint64_t kFWaitNs = 4000000000ull;
 
 template <bool HEAD, bool F16>
 struct FCfg {
-    // Layers: N = 128 (BF16, hi + lo) or 64 (FP16) per output row, one B block per (tap, K-half):
-    // [2 chunks][N rows][16 B]. Head: the 4 row taps are stacked along N, 16 rows each (4 used),
-    // one B block per (column tap, K-half): [2 chunks][64 rows][16 B]; a staged row's MMA covers
-    // up to 4 output rows.
-    // kStack: the 4 row taps stacked along N (the head, and the FP16 layers): one MMA per staged
-    // row and (column tap, K-half) into a ring of row accumulators.
+    // BF16 layers: N = 128 (hi + lo) per output row, one B block per (tap, K-half):
+    // [2 chunks][128 rows][16 B]. kStack (the head, and the FP16 layers): the 4 row taps stacked
+    // along N, N rows each (16 for the head, 4 used; 64 for the FP16 layers), one B block per
+    // (column tap, K-half): [2 chunks][4 N rows][16 B]; one MMA per staged row and (column tap,
+    // K-half) covers up to 4 output rows of a ring of row accumulators.
     static constexpr bool kStack = HEAD || F16;
     static constexpr int N = HEAD ? 16 : (F16 ? 64 : 128);  // accumulator width per output row (= per row tap when stacked)
     static constexpr int kBRows = kStack ? 4 * N : N;       // B rows per block
